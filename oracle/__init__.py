@@ -1,0 +1,290 @@
+"""CPU FCIQMC oracle -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, single-threaded C++ implementation of one FCIQMC iteration
+(HANDE-QMC paper, Sec. 2.1 Eq. (fciqmc), Sec. 2.4, App. A.1, App. A.2, App. B),
+loaded through ctypes.  Only tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of bench.py may import this
+package.  It shares no code with the GPU path (``paper_1811_11679_gb300``),
+and neither imports the other.
+
+Everything it needs is passed in as plain numbers and numpy arrays; seeded
+synthetic inputs come from ``paper_1811_11679_gb300.inputs``, a module that
+holds no FCIQMC arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fciqmc_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SYS_HUBBARD, SYS_UEG, SYS_MOLECULE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (g++, -O2, FMA contraction off) if it is stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _System(C.Structure):
+    _fields_ = [("kind", C.c_int), ("key_words", C.c_int), ("norb", C.c_int),
+                ("nalpha", C.c_int), ("nbeta", C.c_int), ("periodic", C.c_int),
+                ("t", C.c_double), ("U", C.c_double), ("rs", C.c_double),
+                ("h1", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)),
+                ("ecore", C.c_double)]
+
+
+class _Qmc(C.Structure):
+    _fields_ = [("tau", C.c_double), ("target_population", C.c_double),
+                ("shift_damping", C.c_double), ("spawn_cutoff", C.c_double),
+                ("init_pop", C.c_double), ("initiator_threshold", C.c_double),
+                ("p_single", C.c_double),
+                ("shift_period", C.c_int), ("initiator", C.c_int),
+                ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int),
+                ("semi_stoch_start", C.c_int),
+                ("seed", C.c_uint64), ("replica", C.c_uint64)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        u64p, i64p, dp = C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+        lib.orc_philox.argtypes = [u64p, u64p, u64p]
+        lib.orc_log.argtypes = [C.c_double]
+        lib.orc_log.restype = C.c_double
+        lib.orc_to_fixed.argtypes = [C.c_double, i64p, u64p]
+        lib.orc_create.argtypes = [C.POINTER(_System), C.POINTER(_Qmc)]
+        lib.orc_create.restype = P
+        lib.orc_destroy.argtypes = [P]
+        lib.orc_iterate.argtypes = [P, C.c_int]
+        lib.orc_nrec.argtypes = [P]
+        lib.orc_nrec.restype = C.c_int64
+        lib.orc_ndet.argtypes = [P]
+        lib.orc_ndet.restype = C.c_int64
+        lib.orc_eref.argtypes = [P]
+        lib.orc_eref.restype = C.c_double
+        lib.orc_shift.argtypes = [P]
+        lib.orc_shift.restype = C.c_double
+        lib.orc_get_walkers.argtypes = [P, u64p, i64p, dp, C.POINTER(C.c_uint8), C.c_int64]
+        lib.orc_get_walkers.restype = C.c_int64
+        lib.orc_set_walkers.argtypes = [P, u64p, i64p, C.c_int64]
+        lib.orc_set_walkers.restype = C.c_int
+        lib.orc_records.argtypes = [P, i64p, dp, i64p, i64p, dp, i64p, u64p, i64p, i64p, i64p,
+                                    i64p, C.c_int64]
+        lib.orc_records.restype = C.c_int64
+        lib.orc_reference.argtypes = [P, u64p]
+        lib.orc_hdiag.argtypes = [P, u64p]
+        lib.orc_hdiag.restype = C.c_double
+        lib.orc_hij.argtypes = [P, u64p, u64p]
+        lib.orc_hij.restype = C.c_double
+        lib.orc_generate.argtypes = [P, u64p, u64p, u64p, dp, dp]
+        lib.orc_generate.restype = C.c_int
+        lib.orc_enumerate.argtypes = [P, u64p, u64p, dp, C.c_int64]
+        lib.orc_enumerate.restype = C.c_int64
+        lib.orc_ueg_basis.argtypes = [P, C.POINTER(C.c_int), dp]
+        lib.orc_ueg_basis.restype = C.c_int
+        lib.orc_core.argtypes = [P, u64p, C.c_int64]
+        lib.orc_core.restype = C.c_int64
+        _lib = lib
+        return lib
+
+
+def _u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_uint64))
+
+
+def philox(ctr, key):
+    """Philox4x64-10 block for counter (4 words) and key (2 words)."""
+    lib = _load()
+    c, cp = _u64(ctr)
+    k, kp = _u64(key)
+    out = np.zeros(4, dtype=np.uint64)
+    lib.orc_philox(cp, kp, out.ctypes.data_as(C.POINTER(C.c_uint64)))
+    return out
+
+
+def log(x: float) -> float:
+    """The oracle's own natural logarithm (atanh series)."""
+    return _load().orc_log(float(x))
+
+
+def to_fixed(x: float) -> int:
+    """round(x * 2^16) as a Python int (the 128-bit fixed-point term)."""
+    hi, lo = C.c_int64(), C.c_uint64()
+    _load().orc_to_fixed(float(x), C.byref(hi), C.byref(lo))
+    return (hi.value << 64) | lo.value
+
+
+class Oracle:
+    """One FCIQMC run on the CPU.  ``system``/``qmc`` are plain dicts (see
+    paper_1811_11679_gb300.inputs for the keys)."""
+
+    def __init__(self, system: dict, qmc: dict):
+        lib = _load()
+        self._lib = lib
+        s = _System()
+        kind = {"hubbard": SYS_HUBBARD, "ueg": SYS_UEG, "molecule": SYS_MOLECULE}[system["kind"]]
+        s.kind = kind
+        s.key_words = int(system["key_words"])
+        s.norb = int(system["norb"])
+        s.nalpha = int(system["nalpha"])
+        s.nbeta = int(system["nbeta"])
+        s.periodic = int(system.get("periodic", 0))
+        s.t = float(system.get("t", 0.0))
+        s.U = float(system.get("U", 0.0))
+        s.rs = float(system.get("rs", 0.0))
+        s.ecore = float(system.get("ecore", 0.0))
+        self._keep = []
+        if kind == SYS_MOLECULE:
+            h1 = np.ascontiguousarray(system["h1"], dtype=np.float64)
+            eri = np.ascontiguousarray(system["eri"], dtype=np.float64)
+            self._keep += [h1, eri]
+            s.h1 = h1.ctypes.data_as(C.POINTER(C.c_double))
+            s.eri = eri.ctypes.data_as(C.POINTER(C.c_double))
+        q = _Qmc()
+        q.tau = float(qmc["tau"])
+        q.target_population = float(qmc["target_population"])
+        q.shift_damping = float(qmc.get("shift_damping", 0.05))
+        q.spawn_cutoff = float(qmc.get("spawn_cutoff", 0.0))
+        q.init_pop = float(qmc["init_pop"])
+        q.initiator_threshold = float(qmc.get("initiator_threshold", 3.0))
+        q.p_single = float(qmc.get("p_single", 0.1))
+        q.shift_period = int(qmc.get("shift_period", 1))
+        q.initiator = int(qmc.get("initiator", 0))
+        q.real_amplitudes = int(qmc.get("real_amplitudes", 0))
+        q.semi_stoch_size = int(qmc.get("semi_stoch_size", 0))
+        q.semi_stoch_start = int(qmc.get("semi_stoch_start", 0))
+        q.seed = int(qmc["seed"])
+        q.replica = int(qmc.get("replica", 0))
+        h = lib.orc_create(C.byref(s), C.byref(q))
+        if not h:
+            raise ValueError("oracle rejected the system/qmc parameters")
+        self._h = h
+        self.W = s.key_words
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    def iterate(self, n: int = 1) -> None:
+        self._lib.orc_iterate(self._h, int(n))
+
+    @property
+    def e_ref(self) -> float:
+        return self._lib.orc_eref(self._h)
+
+    @property
+    def shift(self) -> float:
+        return self._lib.orc_shift(self._h)
+
+    def reference(self) -> np.ndarray:
+        k = np.zeros(self.W, dtype=np.uint64)
+        self._lib.orc_reference(self._h, k.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return k
+
+    def walkers(self):
+        """(keys[n, W] uint64, pops int64, hdiag f64, flags u8) sorted by key."""
+        n = self._lib.orc_ndet(self._h)
+        keys = np.zeros((n, self.W), dtype=np.uint64)
+        pops = np.zeros(n, dtype=np.int64)
+        hd = np.zeros(n, dtype=np.float64)
+        fl = np.zeros(n, dtype=np.uint8)
+        got = self._lib.orc_get_walkers(self._h, keys.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                        pops.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        hd.ctypes.data_as(C.POINTER(C.c_double)),
+                                        fl.ctypes.data_as(C.POINTER(C.c_uint8)), n)
+        assert got == n
+        return keys, pops, hd, fl
+
+    def set_walkers(self, keys, pops) -> None:
+        k, kp = _u64(np.asarray(keys).reshape(-1, self.W))
+        p = np.ascontiguousarray(pops, dtype=np.int64)
+        rc = self._lib.orc_set_walkers(self._h, kp, p.ctypes.data_as(C.POINTER(C.c_int64)), len(p))
+        if rc != 0:
+            raise ValueError("walker keys must be strictly ascending")
+
+    def records(self) -> dict:
+        cols = {}
+        names = ["iter", "shift", "nw_pre", "n0", "num", "num_hi", "num_lo", "nw_post", "ndet",
+                 "natt", "nspawn"]
+        types = [np.int64, np.float64, np.int64, np.int64, np.float64, np.int64, np.uint64,
+                 np.int64, np.int64, np.int64, np.int64]
+        n = max(1, self._lib.orc_nrec(self._h))
+        arrs = [np.zeros(n, dtype=t) for t in types]
+        ptrs = []
+        for a, t in zip(arrs, types):
+            ct = {np.int64: C.c_int64, np.float64: C.c_double, np.uint64: C.c_uint64}[t]
+            ptrs.append(a.ctypes.data_as(C.POINTER(ct)))
+        got = self._lib.orc_records(self._h, *ptrs, n)
+        for name, a in zip(names, arrs):
+            cols[name] = a[:got].copy()
+        return cols
+
+    def hdiag(self, key) -> float:
+        k, kp = _u64(np.asarray(key).reshape(self.W))
+        return self._lib.orc_hdiag(self._h, kp)
+
+    def hij(self, source, target) -> float:
+        s, sp = _u64(np.asarray(source).reshape(self.W))
+        t, tp = _u64(np.asarray(target).reshape(self.W))
+        return self._lib.orc_hij(self._h, sp, tp)
+
+    def generate(self, key, words):
+        k, kp = _u64(np.asarray(key).reshape(self.W))
+        w, wp = _u64(np.asarray(words).reshape(4))
+        child = np.zeros(self.W, dtype=np.uint64)
+        pg, hv = C.c_double(), C.c_double()
+        ok = self._lib.orc_generate(self._h, kp, wp, child.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    C.byref(pg), C.byref(hv))
+        if not ok:
+            return None
+        return child, pg.value, hv.value
+
+    def enumerate(self, key):
+        """All generator selection paths from `key`: (children[m, W], probs[m]);
+        an all-zero child marks a null path."""
+        k, kp = _u64(np.asarray(key).reshape(self.W))
+        cap = 1 << 22
+        ch = np.zeros((cap, self.W), dtype=np.uint64)
+        pr = np.zeros(cap, dtype=np.float64)
+        m = self._lib.orc_enumerate(self._h, kp, ch.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    pr.ctypes.data_as(C.POINTER(C.c_double)), cap)
+        assert m >= 0
+        return ch[:m].copy(), pr[:m].copy()
+
+    def ueg_basis(self):
+        kv = np.zeros(3 * 4096, dtype=np.int32)
+        box = C.c_double()
+        n = self._lib.orc_ueg_basis(self._h, kv.ctypes.data_as(C.POINTER(C.c_int)), C.byref(box))
+        return kv[:3 * n].reshape(n, 3).copy(), box.value
+
+    def core(self) -> np.ndarray:
+        cap = 1 << 20
+        k = np.zeros((cap, self.W), dtype=np.uint64)
+        n = self._lib.orc_core(self._h, k.ctypes.data_as(C.POINTER(C.c_uint64)), cap)
+        return k[:n].copy()

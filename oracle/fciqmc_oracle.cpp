@@ -1,0 +1,1197 @@
+/*
+ * fciqmc_oracle.cpp -- plain, slow, single-threaded CPU FCIQMC.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  The GPU
+ * product path never links, imports or calls it; it shares no source, header,
+ * table builder or constant with the CUDA path.
+ *
+ * What it follows (HANDE-QMC paper, arXiv:1811.11679):
+ *   - Sec. 2.1, Eq. (fciqmc): c_i(t+dt) = c_i(t) - dt sum_j H_ij c_j(t), applied
+ *     stochastically with signed particles; shift S as a diagonal energy offset.
+ *   - Sec. 2.4: one iteration = spawning (random excitation + H_ij), death
+ *     (diagonal), annihilation (combine particles on one state).
+ *   - Sec. 2.1: initiator rule (new particles on unoccupied determinants only
+ *     from parents above a threshold); real weights; semi-stochastic exact
+ *     projection inside a deterministic space ("high" space, App. A.2).
+ *   - App. A.1: projected energy  E = E_HF + sum_{i!=0} C_i H_0i / C_0.
+ *   - App. B: sorted main list, spawned array, sort + merge annihilation.
+ *
+ * Where the paper is silent the oracle takes the readings listed in the design doc
+ * (weights as int64 fixed point with F = 2^32, counter-based Philox4x64-10
+ * keyed by (seed, replica) with counter (t, attempt, det), Slater-Condon sign
+ * convention, UEG basis ordering, heat-bath-with-rejection generator, shift
+ * update rule, exact 128-bit fixed-point accumulation of the estimator
+ * numerator and of the deterministic-space product).
+ *
+ * Parity status: Philox, the logarithm, Slater-Condon, generators and the
+ * full iteration are pinned by tests/test_oracle_*.py against numpy,
+ * brute-force second quantisation, dense exact diagonalisation and closed
+ * forms.  The large-system energies (UEG 14e/38, 28-orbital molecule) are
+ * "parity unpinned" against exact results (FCI not computable); they are
+ * pinned only through the same code paths on small instances.
+ *
+ * Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (see build.py).
+ */
+#include <stdint.h>
+#include <string.h>
+#include <math.h>
+#include <vector>
+#include <algorithm>
+#include <string>
+
+namespace {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+const int MAXW = 8;
+const uint64_t FIXED_ONE = 1ull << 32;          /* F: one walker */
+const uint64_t SENTINEL_DET = ~0ull;            /* attempt index of per-det draws */
+
+struct Det {
+    uint64_t w[MAXW];
+};
+
+/* ------------------------------------------------------------------ */
+/* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its */
+/* published definition: 10 rounds, multipliers M0, M1, Weyl key bump. */
+/* ------------------------------------------------------------------ */
+void philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint64_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        u128 p0 = (u128)M0 * c0;
+        u128 p1 = (u128)M1 * c2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ c1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ c3 ^ k1;
+        uint64_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* uniform integer in [0, n): high word of w*n (Lemire's multiply-high) */
+inline uint64_t draw_index(uint64_t w, uint64_t n) {
+    return (uint64_t)(((u128)w * n) >> 64);
+}
+/* uniform double in [0, 1) with 53 random bits */
+inline double draw_unit(uint64_t w) {
+    return (double)(w >> 11) * 0x1p-53;
+}
+
+/* SplitMix64 finaliser (Steele, Lea, Flood 2014) -- used only to fold keys
+ * wider than 128 bits into the two Philox counter words. */
+inline uint64_t mix64(uint64_t z) {
+    z ^= z >> 30; z *= 0xbf58476d1ce4e5b9ull;
+    z ^= z >> 27; z *= 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    return z;
+}
+
+/* ------------------------------------------------------------------ */
+/* Natural logarithm written from the atanh series:                    */
+/*   x = m 2^e, m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),            */
+/*   ln m = 2 s (1 + s^2/3 + s^4/5 + ... + s^22/23),  ln x = e ln2 + ln m */
+/* Every operation is one IEEE double op, so the CUDA side can produce */
+/* the same bits.  Used in the shift update (Sec. 2.1).                */
+/* ------------------------------------------------------------------ */
+double own_log(double x) {
+    if (!(x > 0.0)) return -INFINITY;          /* the shift never asks for this */
+    uint64_t bits;
+    memcpy(&bits, &x, 8);
+    int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0) {                               /* subnormal: rescale by 2^64 */
+        double y = x * 18446744073709551616.0;
+        memcpy(&bits, &y, 8);
+        e = (int)((bits >> 52) & 0x7ff) - 64;
+    }
+    e -= 1023;
+    uint64_t mbits = (bits & 0x000fffffffffffffull) | 0x3ff0000000000000ull;  /* m in [1,2) */
+    double m;
+    memcpy(&m, &mbits, 8);
+    if (m > 1.4142135623730951) {               /* fold into [sqrt(1/2), sqrt(2)) */
+        m = m * 0.5;
+        e += 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double p = 1.0 / 23.0;
+    for (int k = 10; k >= 0; --k) {
+        p = p * z;
+        p = p + 1.0 / (double)(2 * k + 1);
+    }
+    double lnm = (2.0 * s) * p;
+    return (double)e * 0.69314718055994530942 + lnm;
+}
+
+/* ------------------------------------------------------------------ */
+/* 128-bit fixed point: value * 2^16, used so that sums of FP64 terms  */
+/* are exact and independent of summation order.                       */
+/* ------------------------------------------------------------------ */
+const double FX_SCALE = 65536.0;       /* 2^16 */
+const double FX_UNSCALE = 0x1p-16;
+
+i128 to_fixed(double term) {
+    double v = term * FX_SCALE;                 /* exact: power-of-two scaling */
+    double a = fabs(v);
+    double hi = floor(a * 0x1p-64);             /* exact */
+    double rem = a - hi * 18446744073709551616.0; /* exact: low bits of a */
+    uint64_t lo = (uint64_t)rint(rem);
+    u128 u = ((u128)(uint64_t)hi << 64) | (u128)lo;
+    i128 r = (i128)u;
+    return v < 0.0 ? -r : r;
+}
+
+double from_fixed(i128 s) {
+    int64_t hi = (int64_t)(s >> 64);
+    uint64_t lo = (uint64_t)s;
+    double d = (double)hi * 18446744073709551616.0 + (double)lo;
+    return d * FX_UNSCALE;
+}
+
+/* ------------------------------------------------------------------ */
+/* Determinant helpers.  Spin orbital p = 2*spatial + spin (alpha = 0), */
+/* bit p lives in word p/64.  Keys order as unsigned big integers       */
+/* (most significant word = word W-1).                                  */
+/* ------------------------------------------------------------------ */
+struct Ctx;
+
+inline bool occ_bit(const Det& d, int p) { return (d.w[p >> 6] >> (p & 63)) & 1ull; }
+inline void flip_bit(Det& d, int p) { d.w[p >> 6] ^= 1ull << (p & 63); }
+
+int det_cmp(const Det& a, const Det& b, int W) {
+    for (int i = W - 1; i >= 0; --i) {
+        if (a.w[i] < b.w[i]) return -1;
+        if (a.w[i] > b.w[i]) return 1;
+    }
+    return 0;
+}
+
+std::vector<int> occ_list(const Det& d, int nspin) {
+    std::vector<int> o;
+    for (int p = 0; p < nspin; ++p)
+        if (occ_bit(d, p)) o.push_back(p);
+    return o;
+}
+
+/* number of occupied spin orbitals strictly between p and q */
+int count_between(const Det& d, int p, int q) {
+    int lo = p < q ? p : q, hi = p < q ? q : p;
+    int c = 0;
+    for (int r = lo + 1; r < hi; ++r) c += occ_bit(d, r);
+    return c;
+}
+
+/* ------------------------------------------------------------------ */
+/* System definitions                                                   */
+/* ------------------------------------------------------------------ */
+enum { SYS_HUBBARD = 0, SYS_UEG = 1, SYS_MOLECULE = 2 };
+
+struct HBEntry {
+    int a, b;          /* spin orbitals, a < b */
+    uint64_t cum;      /* cumulative threshold: entry chosen if w < cum (last: catch-all) */
+};
+
+struct Walker {
+    Det key;
+    int64_t pop;
+    double hdiag;      /* H_ii - E_ref */
+    int core;          /* member of the deterministic space */
+};
+
+struct Spawn {
+    Det key;
+    int64_t amount;
+    int init;          /* parent was an initiator */
+};
+
+struct Record {
+    int64_t iter;
+    double shift;
+    int64_t nw_pre, n0, nw_post, ndet, natt, nspawn;
+    int64_t num_hi;
+    uint64_t num_lo;
+    double num;
+};
+
+struct Ctx {
+    /* system */
+    int kind, W, norb, nalpha, nbeta, nel, nspin;
+    int L, periodic;
+    double t_hop, U;
+    /* UEG */
+    double rs, box, vfac, kfac;
+    std::vector<int> kvec;          /* 3 per spatial orbital */
+    int nmax, side;
+    std::vector<int> klookup;       /* cube -> spatial orbital or -1 */
+    /* molecule */
+    std::vector<double> h1, eri;
+    double ecore;
+    uint32_t psingle_thr;
+    double p_single, p_double;
+    std::vector<std::vector<HBEntry>> hb;   /* per pair index of (p<q) */
+    /* qmc */
+    double tau, target, zeta, cutoff, init_pop, n_a;
+    int period, initiator, real_amp, core_size, core_start;
+    uint64_t seed, replica;
+    int64_t target_fixed, init_thr;
+    /* state */
+    Det d0;
+    double e_ref;
+    std::vector<Walker> main;
+    double shift;
+    int vary;
+    int64_t nw_ref;
+    int64_t iter;
+    std::vector<Det> core;                 /* sorted by key */
+    std::vector<std::vector<std::pair<int, double>>> core_rows;  /* (col, H') */
+    std::vector<Record> recs;
+    std::string err;
+};
+
+/* ---------------- spin-orbital integrals (molecule) ---------------- */
+inline double mol_h(const Ctx& c, int p, int q) {
+    if ((p & 1) != (q & 1)) return 0.0;
+    return c.h1[(size_t)(p >> 1) * c.norb + (q >> 1)];
+}
+/* chemist notation (pq|rs) over spin orbitals */
+inline double mol_g(const Ctx& c, int p, int q, int r, int s) {
+    if ((p & 1) != (q & 1) || (r & 1) != (s & 1)) return 0.0;
+    size_t n = (size_t)c.norb;
+    return c.eri[(((size_t)(p >> 1) * n + (q >> 1)) * n + (r >> 1)) * n + (s >> 1)];
+}
+
+/* ---------------- UEG ---------------- */
+int ueg_orb_of(const Ctx& c, int nx, int ny, int nz) {
+    if (nx < -c.nmax || nx > c.nmax || ny < -c.nmax || ny > c.nmax || nz < -c.nmax || nz > c.nmax)
+        return -1;
+    int s = c.side;
+    return c.klookup[((size_t)(nx + c.nmax) * s + (ny + c.nmax)) * s + (nz + c.nmax)];
+}
+/* Coulomb kernel 4 pi / (Omega |q|^2) with |q|^2 = (2 pi / L)^2 m  ==  vfac / m */
+inline double ueg_v(const Ctx& c, int m) { return c.vfac / (double)m; }
+inline int ueg_dist2(const Ctx& c, int P, int Q) {
+    int dx = c.kvec[3 * P] - c.kvec[3 * Q];
+    int dy = c.kvec[3 * P + 1] - c.kvec[3 * Q + 1];
+    int dz = c.kvec[3 * P + 2] - c.kvec[3 * Q + 2];
+    return dx * dx + dy * dy + dz * dz;
+}
+inline int ueg_n2(const Ctx& c, int P) {
+    return c.kvec[3 * P] * c.kvec[3 * P] + c.kvec[3 * P + 1] * c.kvec[3 * P + 1] +
+           c.kvec[3 * P + 2] * c.kvec[3 * P + 2];
+}
+
+/* ------------------------------------------------------------------ */
+/* Hamiltonian matrix elements (Slater-Condon rules).                  */
+/*   diagonal: sum_k h_kk + sum_{k<l} [(kk|ll) - (kl|lk)]              */
+/*   single i->a: sign * (h_ia + sum_{k in D, k != i} [(ia|kk)-(ik|ka)]) */
+/*   double i<j -> a<b: sign * [(ia|jb) - (ib|ja)]                     */
+/* sign: (-1)^(occupied strictly between i and a in D), then the same  */
+/* for j->b on the updated string.  Summations run in ascending order. */
+/* ------------------------------------------------------------------ */
+double h_diag(const Ctx& c, const Det& d) {
+    std::vector<int> o = occ_list(d, c.nspin);
+    if (c.kind == SYS_HUBBARD) {
+        int dbl = 0;
+        for (int s = 0; s < c.L; ++s)
+            if (occ_bit(d, 2 * s) && occ_bit(d, 2 * s + 1)) ++dbl;
+        return c.U * (double)dbl;
+    }
+    if (c.kind == SYS_UEG) {
+        double e = 0.0;
+        for (size_t k = 0; k < o.size(); ++k) e = e + c.kfac * (double)ueg_n2(c, o[k] >> 1);
+        for (size_t k = 0; k < o.size(); ++k)
+            for (size_t l = k + 1; l < o.size(); ++l)
+                if ((o[k] & 1) == (o[l] & 1)) e = e - ueg_v(c, ueg_dist2(c, o[k] >> 1, o[l] >> 1));
+        return e;
+    }
+    double e1 = 0.0, e2 = 0.0;
+    for (size_t k = 0; k < o.size(); ++k) e1 = e1 + mol_h(c, o[k], o[k]);
+    for (size_t k = 0; k < o.size(); ++k)
+        for (size_t l = k + 1; l < o.size(); ++l) {
+            int p = o[k], q = o[l];
+            e2 = e2 + (mol_g(c, p, p, q, q) - mol_g(c, p, q, q, p));
+        }
+    return (e1 + e2) + c.ecore;
+}
+
+/* <D'|H|D> for D' = D with i->a (i occupied, a empty) */
+double h_single(const Ctx& c, const Det& d, int i, int a) {
+    Det tmp = d;
+    int sgn = (count_between(d, i, a) & 1) ? -1 : 1;
+    double v;
+    if (c.kind == SYS_HUBBARD) {
+        /* hopping -t between nearest-neighbour sites with the same spin */
+        if ((i & 1) != (a & 1)) return 0.0;
+        int si = i >> 1, sa = a >> 1;
+        int diff = si > sa ? si - sa : sa - si;
+        bool bond = (diff == 1) || (c.periodic && c.L > 2 && diff == c.L - 1);
+        if (!bond) return 0.0;
+        v = -c.t_hop;
+    } else if (c.kind == SYS_UEG) {
+        return 0.0;     /* momentum conservation forbids single excitations */
+    } else {
+        double s = 0.0;
+        for (int k = 0; k < c.nspin; ++k) {
+            if (k == i || !occ_bit(d, k)) continue;
+            s = s + (mol_g(c, i, a, k, k) - mol_g(c, i, k, k, a));
+        }
+        v = mol_h(c, i, a) + s;
+    }
+    (void)tmp;
+    return sgn < 0 ? -v : v;
+}
+
+/* <D'|H|D> for D' = D with i->a, j->b (i<j occupied, a<b empty) */
+double h_double(const Ctx& c, const Det& d, int i, int j, int a, int b) {
+    Det tmp = d;
+    int n1 = count_between(tmp, i, a);
+    flip_bit(tmp, i); flip_bit(tmp, a);
+    int n2 = count_between(tmp, j, b);
+    int sgn = ((n1 + n2) & 1) ? -1 : 1;
+    double v;
+    if (c.kind == SYS_HUBBARD) {
+        return 0.0;
+    } else if (c.kind == SYS_UEG) {
+        int I = i >> 1, J = j >> 1, A = a >> 1, B = b >> 1;
+        /* momentum conservation */
+        for (int x = 0; x < 3; ++x)
+            if (c.kvec[3 * I + x] + c.kvec[3 * J + x] != c.kvec[3 * A + x] + c.kvec[3 * B + x])
+                return 0.0;
+        double direct = 0.0, exch = 0.0;
+        if ((i & 1) == (a & 1) && (j & 1) == (b & 1)) direct = ueg_v(c, ueg_dist2(c, I, A));
+        if ((i & 1) == (b & 1) && (j & 1) == (a & 1)) exch = ueg_v(c, ueg_dist2(c, I, B));
+        v = direct - exch;
+    } else {
+        v = mol_g(c, i, a, j, b) - mol_g(c, i, b, j, a);
+    }
+    return sgn < 0 ? -v : v;
+}
+
+/* general <dt|H|ds>, ds = source (parent), dt = target */
+double h_elem(const Ctx& c, const Det& ds, const Det& dt) {
+    int nd = 0;
+    int from[2], to[2], nf = 0, nt = 0;
+    for (int wi = 0; wi < c.W; ++wi) nd += __builtin_popcountll(ds.w[wi] ^ dt.w[wi]);
+    if (nd == 0) return h_diag(c, ds);
+    if (nd != 2 && nd != 4) return 0.0;
+    for (int p = 0; p < c.nspin; ++p) {
+        bool x = occ_bit(ds, p), y = occ_bit(dt, p);
+        if (x && !y) from[nf++] = p;
+        if (!x && y) to[nt++] = p;
+    }
+    if (nd == 2) return h_single(c, ds, from[0], to[0]);
+    return h_double(c, ds, from[0], from[1], to[0], to[1]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Excitation generators.  Each consumes Philox words w[0..2] and       */
+/* returns the child determinant and its exact generation probability. */
+/* ------------------------------------------------------------------ */
+struct Excit {
+    bool null;
+    Det child;
+    double pgen;
+    double hij;
+};
+
+/* pair index -> (i, j), i < j, with P = j(j-1)/2 + i */
+void unrank_pair(uint64_t P, int& i, int& j) {
+    int jj = 1;
+    while ((uint64_t)(jj + 1) * jj / 2 <= P) ++jj;
+    j = jj;
+    i = (int)(P - (uint64_t)jj * (jj - 1) / 2);
+}
+
+Excit gen_hubbard(const Ctx& c, const Det& d, const uint64_t w[4]) {
+    Excit e;
+    e.null = true;
+    std::vector<int> o = occ_list(d, c.nspin);
+    int n = (int)o.size();
+    int p = o[draw_index(w[0], (uint64_t)n)];
+    int site = p >> 1, spin = p & 1;
+    int dir = (int)(w[1] >> 63);
+    int ns = dir == 0 ? site + 1 : site - 1;
+    if (c.periodic) {
+        ns = (ns + c.L) % c.L;
+    } else if (ns < 0 || ns >= c.L) {
+        return e;
+    }
+    int q = 2 * ns + spin;
+    if (occ_bit(d, q)) return e;
+    e.pgen = 1.0 / (2.0 * (double)n);
+    e.hij = h_single(c, d, p, q);
+    e.child = d;
+    flip_bit(e.child, p);
+    flip_bit(e.child, q);
+    e.null = false;
+    return e;
+}
+
+Excit gen_ueg(const Ctx& c, const Det& d, const uint64_t w[4]) {
+    Excit e;
+    e.null = true;
+    std::vector<int> o = occ_list(d, c.nspin);
+    int n = (int)o.size();
+    uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+    int ii, jj;
+    unrank_pair(draw_index(w[1], npairs), ii, jj);
+    int p = o[ii], q = o[jj];
+    int A = (int)draw_index(w[2], (uint64_t)c.norb);
+    int a = 2 * A + (p & 1);
+    int P = p >> 1, Q = q >> 1;
+    int B = ueg_orb_of(c, c.kvec[3 * P] + c.kvec[3 * Q] - c.kvec[3 * A],
+                       c.kvec[3 * P + 1] + c.kvec[3 * Q + 1] - c.kvec[3 * A + 1],
+                       c.kvec[3 * P + 2] + c.kvec[3 * Q + 2] - c.kvec[3 * A + 2]);
+    if (B < 0) return e;
+    int b = 2 * B + (q & 1);
+    if (a == b || occ_bit(d, a) || occ_bit(d, b)) return e;
+    double ways = ((p & 1) == (q & 1)) ? 2.0 : 1.0;
+    e.pgen = ways / ((double)npairs * (double)c.norb);
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    e.hij = h_double(c, d, p, q, lo, hi);
+    e.child = d;
+    flip_bit(e.child, p); flip_bit(e.child, q);
+    flip_bit(e.child, a); flip_bit(e.child, b);
+    e.null = false;
+    return e;
+}
+
+int pair_index(int p, int q) { return q * (q - 1) / 2 + p; }   /* p < q */
+
+Excit gen_heat_bath(const Ctx& c, const Det& d, const uint64_t w[4]) {
+    Excit e;
+    e.null = true;
+    std::vector<int> o = occ_list(d, c.nspin);
+    int n = (int)o.size();
+    if ((uint32_t)(w[0] >> 32) < c.psingle_thr) {
+        /* single: i uniform over electrons, a uniform over empty orbitals of i's spin */
+        int i = o[draw_index(w[1], (uint64_t)n)];
+        int spin = i & 1;
+        std::vector<int> empty;
+        for (int A = 0; A < c.norb; ++A)
+            if (!occ_bit(d, 2 * A + spin)) empty.push_back(2 * A + spin);
+        if (empty.empty()) return e;
+        int a = empty[draw_index(w[2], (uint64_t)empty.size())];
+        e.pgen = c.p_single / ((double)n * (double)empty.size());
+        e.hij = h_single(c, d, i, a);
+        e.child = d;
+        flip_bit(e.child, i); flip_bit(e.child, a);
+        e.null = false;
+        return e;
+    }
+    uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+    int ii, jj;
+    unrank_pair(draw_index(w[1], npairs), ii, jj);
+    int p = o[ii], q = o[jj];
+    const std::vector<HBEntry>& tab = c.hb[pair_index(p, q)];
+    if (tab.empty()) return e;
+    size_t k = 0;
+    while (k + 1 < tab.size() && !(w[2] < tab[k].cum)) ++k;
+    int a = tab[k].a, b = tab[k].b;
+    if (occ_bit(d, a) || occ_bit(d, b)) return e;
+    double pk;
+    if (tab.size() == 1) {
+        pk = 1.0;
+    } else {
+        uint64_t prev = k == 0 ? 0 : tab[k - 1].cum;
+        uint64_t width = (k + 1 == tab.size()) ? (0 - prev) : (tab[k].cum - prev);
+        pk = (double)width * 0x1p-64;
+    }
+    double pg = c.p_double / (double)npairs;
+    e.pgen = pg * pk;
+    e.hij = h_double(c, d, p, q, a, b);
+    e.child = d;
+    flip_bit(e.child, p); flip_bit(e.child, q);
+    flip_bit(e.child, a); flip_bit(e.child, b);
+    e.null = false;
+    return e;
+}
+
+Excit generate(const Ctx& c, const Det& d, const uint64_t w[4]) {
+    if (c.kind == SYS_HUBBARD) return gen_hubbard(c, d, w);
+    if (c.kind == SYS_UEG) return gen_ueg(c, d, w);
+    return gen_heat_bath(c, d, w);
+}
+
+/* Heat-bath tables: for each occupied pair (p<q), all spin-allowed (a<b)
+ * with a,b not in {p,q} and weight |(pa|qb) - (pb|qa)| > 0, in ascending
+ * (a, b) order; cum_k = floor(2^64 * S_k / S_total), forced strictly
+ * increasing, last entry catches the remainder. */
+void build_heat_bath(Ctx& c) {
+    int ns = c.nspin;
+    c.hb.assign((size_t)ns * (ns - 1) / 2, std::vector<HBEntry>());
+    for (int q = 1; q < ns; ++q)
+        for (int p = 0; p < q; ++p) {
+            std::vector<HBEntry> tab;
+            std::vector<double> wts;
+            for (int a = 0; a < ns; ++a)
+                for (int b = a + 1; b < ns; ++b) {
+                    if (a == p || a == q || b == p || b == q) continue;
+                    int sp = p & 1, sq = q & 1, sa = a & 1, sb = b & 1;
+                    if (!((sa == sp && sb == sq) || (sa == sq && sb == sp))) continue;
+                    double v = mol_g(c, p, a, q, b) - mol_g(c, p, b, q, a);
+                    double wgt = fabs(v);
+                    if (!(wgt > 0.0)) continue;
+                    HBEntry h;
+                    h.a = a; h.b = b; h.cum = 0;
+                    tab.push_back(h);
+                    wts.push_back(wgt);
+                }
+            if (!tab.empty()) {
+                std::vector<double> cs(wts.size());
+                double s = 0.0;
+                for (size_t k = 0; k < wts.size(); ++k) { s = s + wts[k]; cs[k] = s; }
+                double total = s;
+                uint64_t prev = 0;
+                for (size_t k = 0; k + 1 < tab.size(); ++k) {
+                    double r = cs[k] / total;
+                    uint64_t v = r >= 1.0 ? ~0ull : (uint64_t)(r * 18446744073709551616.0);
+                    if (v <= prev) v = prev + 1;
+                    tab[k].cum = v;
+                    prev = v;
+                }
+                tab.back().cum = ~0ull;    /* catch-all; never compared */
+            }
+            c.hb[pair_index(p, q)] = tab;
+        }
+}
+
+/* ------------------------------------------------------------------ */
+/* RNG streams: key = (seed, replica); counter = (t, attempt, h0, h1)   */
+/* with (h0, h1) the key words for W <= 2 and a SplitMix64 fold above. */
+/* ------------------------------------------------------------------ */
+void det_hash(const Ctx& c, const Det& d, uint64_t& h0, uint64_t& h1) {
+    if (c.W <= 2) {
+        h0 = d.w[0];
+        h1 = c.W == 2 ? d.w[1] : 0;
+        return;
+    }
+    uint64_t a = 0x243F6A8885A308D3ull, b = 0x13198A2E03707344ull;
+    for (int i = 0; i < c.W; ++i) {
+        a = mix64(a ^ d.w[i]);
+        b = mix64(b ^ d.w[i]);
+    }
+    h0 = a; h1 = b;
+}
+
+void draw(const Ctx& c, int64_t t, uint64_t attempt, const Det& d, uint64_t out[4]) {
+    uint64_t ctr[4], key[2];
+    uint64_t h0, h1;
+    det_hash(c, d, h0, h1);
+    ctr[0] = (uint64_t)t; ctr[1] = attempt; ctr[2] = h0; ctr[3] = h1;
+    key[0] = c.seed; key[1] = c.replica;
+    philox4x64_10(ctr, key, out);
+}
+
+/* ------------------------------------------------------------------ */
+/* One FCIQMC iteration (Sec. 2.1 / 2.4, App. B)                        */
+/* ------------------------------------------------------------------ */
+bool is_d0(const Ctx& c, const Det& d) { return det_cmp(d, c.d0, c.W) == 0; }
+
+int exc_level(const Ctx& c, const Det& a, const Det& b) {
+    int n = 0;
+    for (int i = 0; i < c.W; ++i) n += __builtin_popcountll(a.w[i] ^ b.w[i]);
+    return n / 2;
+}
+
+bool in_core(const Ctx& c, const Det& d) {
+    size_t lo = 0, hi = c.core.size();
+    while (lo < hi) {
+        size_t mid = (lo + hi) / 2;
+        int r = det_cmp(c.core[mid], d, c.W);
+        if (r == 0) return true;
+        if (r < 0) lo = mid + 1; else hi = mid;
+    }
+    return false;
+}
+
+inline int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+
+void select_core(Ctx& c);
+
+void iterate_once(Ctx& c) {
+    const int64_t t = ++c.iter;
+    Record rec;
+    memset(&rec, 0, sizeof rec);
+    rec.iter = t;
+
+    /* (1) estimators on M(t-1): N_w, N_0, numerator sum_{j != 0} N_j H_0j (App. A.1) */
+    i128 num = 0;
+    for (size_t i = 0; i < c.main.size(); ++i) {
+        const Walker& wk = c.main[i];
+        rec.nw_pre += iabs64(wk.pop);
+        if (is_d0(c, wk.key)) {
+            rec.n0 = wk.pop;
+            continue;
+        }
+        if (wk.pop == 0 || exc_level(c, c.d0, wk.key) > 2) continue;
+        double h0j = h_elem(c, wk.key, c.d0);
+        num += to_fixed((double)wk.pop * h0j);
+    }
+    rec.num_hi = (int64_t)(num >> 64);
+    rec.num_lo = (uint64_t)num;
+    rec.num = from_fixed(num);
+
+    /* (2) initiator flags (Sec. 2.1) */
+    std::vector<int> init(c.main.size(), 1);
+    if (c.initiator)
+        for (size_t i = 0; i < c.main.size(); ++i) {
+            const Walker& wk = c.main[i];
+            init[i] = (iabs64(wk.pop) > c.init_thr) || is_d0(c, wk.key) || wk.core;
+        }
+
+    /* (3) spawning from every occupied determinant (Sec. 2.4) */
+    std::vector<Spawn> spawned;
+    for (size_t i = 0; i < c.main.size(); ++i) {
+        const Walker& wk = c.main[i];
+        if (wk.pop == 0) continue;
+        uint64_t mag = (uint64_t)iabs64(wk.pop);
+        uint64_t wdet[4];
+        draw(c, t, SENTINEL_DET, wk.key, wdet);
+        uint64_t natt = mag >> 32;
+        if (c.real_amp) {
+            uint64_t frac = mag & 0xffffffffull;
+            if ((wdet[0] >> 32) < frac) natt += 1;
+        }
+        rec.natt += (int64_t)natt;
+        int psign = wk.pop < 0 ? -1 : 1;
+        for (uint64_t a = 0; a < natt; ++a) {
+            uint64_t w[4];
+            draw(c, t, a, wk.key, w);
+            Excit ex = generate(c, wk.key, w);
+            if (ex.null) continue;
+            if (ex.hij == 0.0) continue;
+            if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
+            double m = (c.tau * fabs(ex.hij)) / ex.pgen;
+            int64_t q;
+            if (!c.real_amp) {
+                double fl = floor(m);
+                double k = fl;
+                if (draw_unit(w[3]) < m - fl) k = k + 1.0;
+                if (k == 0.0) continue;
+                q = (int64_t)k * (int64_t)FIXED_ONE;
+            } else {
+                if (m < c.cutoff) {
+                    if (draw_unit(w[3]) < m / c.cutoff) m = c.cutoff;
+                    else continue;
+                }
+                q = llrint(m * 4294967296.0);
+                if (q == 0) continue;
+            }
+            int hs = ex.hij < 0.0 ? -1 : 1;
+            Spawn s;
+            s.key = ex.child;
+            s.amount = (-hs * psign) < 0 ? -q : q;
+            s.init = init[i];
+            spawned.push_back(s);
+        }
+    }
+    rec.nspawn = (int64_t)spawned.size();
+
+    /* (4) death / cloning for determinants outside the core, from N(t-1) */
+    std::vector<int64_t> newpop(c.main.size());
+    for (size_t i = 0; i < c.main.size(); ++i) {
+        const Walker& wk = c.main[i];
+        newpop[i] = wk.pop;
+        if (wk.core || wk.pop == 0) continue;
+        double d = c.tau * (wk.hdiag - c.shift);
+        if (c.real_amp) {
+            double x = d * (double)wk.pop;
+            newpop[i] = wk.pop - llrint(x);
+        } else {
+            uint64_t wdet[4];
+            draw(c, t, SENTINEL_DET, wk.key, wdet);
+            int64_t n = iabs64(wk.pop) >> 32;
+            double x = fabs(d) * (double)n;
+            double fl = floor(x);
+            int64_t k = (int64_t)fl;
+            if (draw_unit(wdet[1]) < x - fl) k += 1;
+            int64_t nn = d > 0.0 ? n - k : n + k;
+            newpop[i] = (wk.pop < 0 ? -nn : nn) * (int64_t)FIXED_ONE;
+        }
+    }
+
+    /* (5) semi-stochastic: exact projection inside the core (App. A.2) */
+    if (!c.core.empty()) {
+        std::vector<size_t> pos(c.core.size());
+        for (size_t r = 0; r < c.core.size(); ++r) {
+            size_t lo = 0, hi = c.main.size();
+            while (lo < hi) {
+                size_t mid = (lo + hi) / 2;
+                if (det_cmp(c.main[mid].key, c.core[r], c.W) < 0) lo = mid + 1; else hi = mid;
+            }
+            pos[r] = lo;
+        }
+        for (size_t r = 0; r < c.core.size(); ++r) {
+            i128 acc = 0;
+            for (size_t k = 0; k < c.core_rows[r].size(); ++k) {
+                int col = c.core_rows[r][k].first;
+                double h = c.core_rows[r][k].second;
+                acc += to_fixed((double)c.main[pos[col]].pop * h);
+            }
+            double y = from_fixed(acc);
+            int64_t pr = c.main[pos[r]].pop;
+            double v = y - c.shift * (double)pr;
+            double x = c.tau * v;
+            newpop[pos[r]] = pr - llrint(x);
+        }
+    }
+
+    /* (6) annihilation: sort the spawned array, combine equal keys, merge
+     *     into the sorted main list; initiator rule for new determinants. */
+    const int W = c.W;
+    std::sort(spawned.begin(), spawned.end(), [W](const Spawn& x, const Spawn& y) {
+        return det_cmp(x.key, y.key, W) < 0;
+    });
+    std::vector<Spawn> merged;
+    for (size_t k = 0; k < spawned.size(); ++k) {
+        if (!merged.empty() && det_cmp(merged.back().key, spawned[k].key, W) == 0) {
+            merged.back().amount += spawned[k].amount;
+            merged.back().init |= spawned[k].init;
+        } else {
+            merged.push_back(spawned[k]);
+        }
+    }
+    std::vector<Walker> out;
+    out.reserve(c.main.size() + merged.size());
+    size_t im = 0, is = 0;
+    while (im < c.main.size() || is < merged.size()) {
+        int r;
+        if (im == c.main.size()) r = 1;
+        else if (is == merged.size()) r = -1;
+        else r = det_cmp(c.main[im].key, merged[is].key, W);
+        Walker nw;
+        if (r < 0) {
+            nw = c.main[im];
+            nw.pop = newpop[im];
+            ++im;
+        } else if (r == 0) {
+            nw = c.main[im];
+            nw.pop = newpop[im] + merged[is].amount;
+            ++im; ++is;
+        } else {
+            const Spawn& s = merged[is];
+            ++is;
+            if (c.initiator && !s.init) continue;
+            if (s.amount == 0) continue;
+            nw.key = s.key;
+            nw.pop = s.amount;
+            nw.hdiag = h_diag(c, s.key) - c.e_ref;
+            nw.core = 0;
+        }
+        bool keep_always = nw.core || is_d0(c, nw.key);
+        if (!keep_always && c.real_amp) {
+            int64_t mag = iabs64(nw.pop);
+            if (mag > 0 && mag < (int64_t)FIXED_ONE) {
+                uint64_t wdet[4];
+                draw(c, t, SENTINEL_DET, nw.key, wdet);
+                int64_t rounded = ((wdet[2] >> 32) < (uint64_t)mag) ? (int64_t)FIXED_ONE : 0;
+                nw.pop = nw.pop < 0 ? -rounded : rounded;
+            }
+        }
+        if (nw.pop == 0 && !keep_always) continue;
+        out.push_back(nw);
+    }
+    c.main.swap(out);
+
+    /* (7) shift update (Sec. 2.1): S <- S - zeta/(A tau) ln(N_w(t)/N_w(t-A)) */
+    int64_t nw_post = 0;
+    for (size_t i = 0; i < c.main.size(); ++i) nw_post += iabs64(c.main[i].pop);
+    if (c.vary) {
+        if (t % c.period == 0) {
+            double ratio = (double)nw_post / (double)c.nw_ref;
+            double coef = c.zeta / ((double)c.period * c.tau);
+            c.shift = c.shift - coef * own_log(ratio);
+            c.nw_ref = nw_post;
+        }
+    } else if (nw_post > c.target_fixed) {
+        c.vary = 1;
+        c.nw_ref = nw_post;
+    }
+    rec.shift = c.shift;
+    rec.nw_post = nw_post;
+    rec.ndet = (int64_t)c.main.size();
+    c.recs.push_back(rec);
+
+    /* (8) deterministic space "high": chosen once, at start_iteration */
+    if (c.core_size > 0 && t == c.core_start) select_core(c);
+}
+
+/* core = D0 plus the (size-1) other determinants of largest |N|, ties by key */
+void select_core(Ctx& c) {
+    std::vector<size_t> idx;
+    for (size_t i = 0; i < c.main.size(); ++i)
+        if (!is_d0(c, c.main[i].key)) idx.push_back(i);
+    const Ctx& cc = c;
+    std::stable_sort(idx.begin(), idx.end(), [&cc](size_t x, size_t y) {
+        int64_t ax = iabs64(cc.main[x].pop), ay = iabs64(cc.main[y].pop);
+        if (ax != ay) return ax > ay;
+        return det_cmp(cc.main[x].key, cc.main[y].key, cc.W) < 0;
+    });
+    size_t ntake = (size_t)c.core_size - 1;
+    if (ntake > idx.size()) ntake = idx.size();
+    c.core.clear();
+    c.core.push_back(c.d0);
+    for (size_t k = 0; k < ntake; ++k) c.core.push_back(c.main[idx[k]].key);
+    const int W = c.W;
+    std::sort(c.core.begin(), c.core.end(), [W](const Det& x, const Det& y) { return det_cmp(x, y, W) < 0; });
+    for (size_t i = 0; i < c.main.size(); ++i) c.main[i].core = in_core(c, c.main[i].key) ? 1 : 0;
+    /* H' = H - E_ref on the diagonal; rows and columns in key order */
+    c.core_rows.assign(c.core.size(), std::vector<std::pair<int, double>>());
+    for (size_t r = 0; r < c.core.size(); ++r)
+        for (size_t k = 0; k < c.core.size(); ++k) {
+            if (exc_level(c, c.core[r], c.core[k]) > 2) continue;
+            double h;
+            if (r == k) h = h_diag(c, c.core[r]) - c.e_ref;
+            else h = h_elem(c, c.core[k], c.core[r]);
+            if (h == 0.0) continue;                 /* zero elements add nothing */
+            c.core_rows[r].push_back(std::make_pair((int)k, h));
+        }
+}
+
+}  /* namespace */
+
+/* ======================= C interface for the tests ======================= */
+extern "C" {
+
+typedef struct {
+    int kind, key_words, norb, nalpha, nbeta, periodic;
+    double t, U, rs;
+    const double* h1;
+    const double* eri;
+    double ecore;
+} orc_system;
+
+typedef struct {
+    double tau, target_population, shift_damping, spawn_cutoff, init_pop, initiator_threshold;
+    double p_single;
+    int shift_period, initiator, real_amplitudes, semi_stoch_size, semi_stoch_start;
+    uint64_t seed, replica;
+} orc_qmc;
+
+void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
+double orc_log(double x) { return own_log(x); }
+void orc_to_fixed(double x, int64_t* hi, uint64_t* lo) {
+    i128 v = to_fixed(x);
+    *hi = (int64_t)(v >> 64);
+    *lo = (uint64_t)v;
+}
+
+static bool setup_ueg(Ctx& c) {
+    const double PI = 3.14159265358979323846;
+    /* basis: plane waves k = 2 pi n / L sorted by (|n|^2, nx, ny, nz) */
+    int R = 1;
+    for (;;) {
+        int cnt = 0;
+        for (int x = -R; x <= R; ++x)
+            for (int y = -R; y <= R; ++y)
+                for (int z = -R; z <= R; ++z)
+                    if (x * x + y * y + z * z <= R * R) ++cnt;
+        if (cnt > c.norb) break;
+        ++R;
+    }
+    std::vector<std::vector<int>> pts;
+    for (int x = -R; x <= R; ++x)
+        for (int y = -R; y <= R; ++y)
+            for (int z = -R; z <= R; ++z)
+                if (x * x + y * y + z * z <= R * R) pts.push_back({x * x + y * y + z * z, x, y, z});
+    std::sort(pts.begin(), pts.end());
+    c.kvec.clear();
+    c.nmax = 0;
+    for (int i = 0; i < c.norb; ++i) {
+        for (int k = 1; k <= 3; ++k) {
+            c.kvec.push_back(pts[i][k]);
+            int a = pts[i][k] < 0 ? -pts[i][k] : pts[i][k];
+            if (a > c.nmax) c.nmax = a;
+        }
+    }
+    c.side = 2 * c.nmax + 1;
+    c.klookup.assign((size_t)c.side * c.side * c.side, -1);
+    for (int i = 0; i < c.norb; ++i)
+        c.klookup[((size_t)(c.kvec[3 * i] + c.nmax) * c.side + (c.kvec[3 * i + 1] + c.nmax)) * c.side +
+                  (c.kvec[3 * i + 2] + c.nmax)] = i;
+    /* Wigner-Seitz radius: Omega = (4 pi / 3) r_s^3 N, L = Omega^(1/3) */
+    c.box = c.rs * cbrt(4.0 * PI * (double)c.nel / 3.0);
+    c.vfac = 1.0 / (PI * c.box);                     /* 4pi/(Omega (2pi/L)^2) */
+    double kf = 2.0 * PI / c.box;
+    c.kfac = 0.5 * (kf * kf);                         /* |k|^2/2 = kfac |n|^2 */
+    return true;
+}
+
+void* orc_create(const orc_system* s, const orc_qmc* q) {
+    Ctx* c = new Ctx();
+    c->kind = s->kind;
+    c->W = s->key_words;
+    c->norb = s->norb;
+    c->nalpha = s->nalpha;
+    c->nbeta = s->nbeta;
+    c->nel = s->nalpha + s->nbeta;
+    c->nspin = 2 * s->norb;
+    c->L = s->norb;
+    c->periodic = s->periodic;
+    c->t_hop = s->t;
+    c->U = s->U;
+    c->rs = s->rs;
+    c->ecore = s->ecore;
+    if (c->W < 1 || c->W > MAXW || c->nspin > 64 * c->W) { delete c; return nullptr; }
+    if (c->kind == SYS_HUBBARD && c->periodic && c->L < 3) { delete c; return nullptr; }
+    if (c->kind == SYS_MOLECULE) {
+        size_t n = (size_t)c->norb;
+        c->h1.assign(s->h1, s->h1 + n * n);
+        c->eri.assign(s->eri, s->eri + n * n * n * n);
+    }
+    c->tau = q->tau;
+    c->target = q->target_population;
+    c->zeta = q->shift_damping;
+    c->cutoff = q->spawn_cutoff;
+    c->init_pop = q->init_pop;
+    c->n_a = q->initiator_threshold;
+    c->period = q->shift_period > 0 ? q->shift_period : 1;
+    c->initiator = q->initiator;
+    c->real_amp = q->real_amplitudes;
+    c->core_size = q->semi_stoch_size;
+    c->core_start = q->semi_stoch_start;
+    c->seed = q->seed;
+    c->replica = q->replica;
+    /* thresholds in fixed point, saturated at the int64 range */
+    c->target_fixed = c->target * 4294967296.0 >= 9223372036854775807.0
+                          ? INT64_MAX : llrint(c->target * 4294967296.0);
+    c->init_thr = c->n_a * 4294967296.0 >= 9223372036854775807.0
+                      ? INT64_MAX : llrint(c->n_a * 4294967296.0);
+    /* p_single as an exact dyadic: threshold on the top 32 bits of a word */
+    c->psingle_thr = (uint32_t)llrint(q->p_single * 4294967296.0);
+    c->p_single = (double)c->psingle_thr * 0x1p-32;
+    c->p_double = (double)(4294967296ull - c->psingle_thr) * 0x1p-32;
+
+    memset(&c->d0, 0, sizeof c->d0);
+    if (c->kind == SYS_HUBBARD) {
+        /* Neel reference: alpha on even sites, beta on odd sites */
+        if (c->nalpha > (c->L + 1) / 2 || c->nbeta > c->L / 2) { delete c; return nullptr; }
+        for (int k = 0; k < c->nalpha; ++k) flip_bit(c->d0, 2 * (2 * k) + 0);
+        for (int k = 0; k < c->nbeta; ++k) flip_bit(c->d0, 2 * (2 * k + 1) + 1);
+    } else {
+        if (c->kind == SYS_UEG) setup_ueg(*c);
+        for (int k = 0; k < c->nalpha; ++k) flip_bit(c->d0, 2 * k);
+        for (int k = 0; k < c->nbeta; ++k) flip_bit(c->d0, 2 * k + 1);
+        if (c->kind == SYS_MOLECULE) build_heat_bath(*c);
+    }
+    c->e_ref = h_diag(*c, c->d0);
+    Walker w0;
+    w0.key = c->d0;
+    w0.pop = llrint(c->init_pop * 4294967296.0);
+    w0.hdiag = 0.0;
+    w0.core = 0;
+    c->main.push_back(w0);
+    c->shift = 0.0;
+    c->vary = 0;
+    c->nw_ref = 0;
+    c->iter = 0;
+    return c;
+}
+
+void orc_destroy(void* h) { delete (Ctx*)h; }
+
+void orc_iterate(void* h, int n) {
+    Ctx* c = (Ctx*)h;
+    for (int i = 0; i < n; ++i) iterate_once(*c);
+}
+
+int64_t orc_nrec(void* h) { return (int64_t)((Ctx*)h)->recs.size(); }
+int64_t orc_ndet(void* h) { return (int64_t)((Ctx*)h)->main.size(); }
+double orc_eref(void* h) { return ((Ctx*)h)->e_ref; }
+double orc_shift(void* h) { return ((Ctx*)h)->shift; }
+
+/* keys: W words per walker (word 0 first); flags bit0 = core */
+int64_t orc_get_walkers(void* h, uint64_t* keys, int64_t* pops, double* hdiag, uint8_t* flags, int64_t cap) {
+    Ctx* c = (Ctx*)h;
+    int64_t n = (int64_t)c->main.size();
+    if (n > cap) return -n;
+    for (int64_t i = 0; i < n; ++i) {
+        const Walker& wk = c->main[(size_t)i];
+        for (int k = 0; k < c->W; ++k) keys[i * c->W + k] = wk.key.w[k];
+        pops[i] = wk.pop;
+        hdiag[i] = wk.hdiag;
+        flags[i] = (uint8_t)(wk.core ? 1 : 0);
+    }
+    return n;
+}
+
+/* replace the walker list (sorted by key is required) -- test hook */
+int orc_set_walkers(void* h, const uint64_t* keys, const int64_t* pops, int64_t n) {
+    Ctx* c = (Ctx*)h;
+    c->main.clear();
+    for (int64_t i = 0; i < n; ++i) {
+        Walker wk;
+        memset(&wk.key, 0, sizeof wk.key);
+        for (int k = 0; k < c->W; ++k) wk.key.w[k] = keys[i * c->W + k];
+        wk.pop = pops[i];
+        wk.hdiag = h_diag(*c, wk.key) - c->e_ref;
+        wk.core = 0;
+        if (!c->main.empty() && det_cmp(c->main.back().key, wk.key, c->W) >= 0) return -1;
+        c->main.push_back(wk);
+    }
+    /* start_iteration 0: the deterministic space is taken from the list as given */
+    if (c->core_size > 0 && c->core_start == 0 && c->iter == 0) select_core(*c);
+    return 0;
+}
+
+/* records: 11 int64/double slots per iteration, see Record */
+int64_t orc_records(void* h, int64_t* iter, double* shift, int64_t* nw_pre, int64_t* n0, double* num,
+                    int64_t* num_hi, uint64_t* num_lo, int64_t* nw_post, int64_t* ndet, int64_t* natt,
+                    int64_t* nspawn, int64_t cap) {
+    Ctx* c = (Ctx*)h;
+    int64_t n = (int64_t)c->recs.size();
+    if (n > cap) n = cap;
+    for (int64_t i = 0; i < n; ++i) {
+        const Record& r = c->recs[(size_t)i];
+        iter[i] = r.iter; shift[i] = r.shift; nw_pre[i] = r.nw_pre; n0[i] = r.n0;
+        num[i] = r.num; num_hi[i] = r.num_hi; num_lo[i] = r.num_lo; nw_post[i] = r.nw_post;
+        ndet[i] = r.ndet; natt[i] = r.natt; nspawn[i] = r.nspawn;
+    }
+    return n;
+}
+
+void orc_reference(void* h, uint64_t* key) {
+    Ctx* c = (Ctx*)h;
+    for (int k = 0; k < c->W; ++k) key[k] = c->d0.w[k];
+}
+
+double orc_hdiag(void* h, const uint64_t* key) {
+    Ctx* c = (Ctx*)h;
+    Det d;
+    memset(&d, 0, sizeof d);
+    for (int k = 0; k < c->W; ++k) d.w[k] = key[k];
+    return h_diag(*c, d);
+}
+
+/* <target|H|source> */
+double orc_hij(void* h, const uint64_t* source, const uint64_t* target) {
+    Ctx* c = (Ctx*)h;
+    Det s, t;
+    memset(&s, 0, sizeof s);
+    memset(&t, 0, sizeof t);
+    for (int k = 0; k < c->W; ++k) { s.w[k] = source[k]; t.w[k] = target[k]; }
+    return h_elem(*c, s, t);
+}
+
+/* one excitation from the Philox words w[4]; returns 0 if null */
+int orc_generate(void* h, const uint64_t* key, const uint64_t* w, uint64_t* child, double* pgen, double* hij) {
+    Ctx* c = (Ctx*)h;
+    Det d;
+    memset(&d, 0, sizeof d);
+    for (int k = 0; k < c->W; ++k) d.w[k] = key[k];
+    Excit e = generate(*c, d, w);
+    if (e.null) return 0;
+    for (int k = 0; k < c->W; ++k) child[k] = e.child.w[k];
+    *pgen = e.pgen;
+    *hij = e.hij;
+    return 1;
+}
+
+/* Every selection path of the generator from `key` with its probability.
+ * Returns the number of paths (children[k] all-zero words = null path). */
+int64_t orc_enumerate(void* h, const uint64_t* key, uint64_t* children, double* probs, int64_t cap) {
+    Ctx* c = (Ctx*)h;
+    Det d;
+    memset(&d, 0, sizeof d);
+    for (int k = 0; k < c->W; ++k) d.w[k] = key[k];
+    std::vector<int> o = occ_list(d, c->nspin);
+    int n = (int)o.size();
+    std::vector<std::pair<Det, double>> paths;
+    Det zero;
+    memset(&zero, 0, sizeof zero);
+    auto add = [&](const Det* ch, double p) { paths.push_back(std::make_pair(ch ? *ch : zero, p)); };
+    if (c->kind == SYS_HUBBARD) {
+        for (int k = 0; k < n; ++k)
+            for (int dir = 0; dir < 2; ++dir) {
+                uint64_t w[4] = {0, 0, 0, 0};
+                /* smallest word mapping to electron k */
+                w[0] = (uint64_t)((((u128)k << 64) + (uint64_t)n - 1) / (uint64_t)n);
+                w[1] = dir ? (1ull << 63) : 0;
+                Excit e = generate(*c, d, w);
+                add(e.null ? nullptr : &e.child, 1.0 / (2.0 * n));
+            }
+    } else if (c->kind == SYS_UEG) {
+        uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+        for (uint64_t P = 0; P < npairs; ++P)
+            for (int A = 0; A < c->norb; ++A) {
+                uint64_t w[4] = {0, 0, 0, 0};
+                w[1] = (uint64_t)((((u128)P << 64) + npairs - 1) / npairs);
+                w[2] = (uint64_t)((((u128)(uint64_t)A << 64) + (uint64_t)c->norb - 1) / (uint64_t)c->norb);
+                Excit e = generate(*c, d, w);
+                add(e.null ? nullptr : &e.child, 1.0 / ((double)npairs * c->norb));
+            }
+    } else {
+        for (int k = 0; k < n; ++k) {
+            int i = o[k];
+            int spin = i & 1;
+            std::vector<int> empty;
+            for (int A = 0; A < c->norb; ++A)
+                if (!occ_bit(d, 2 * A + spin)) empty.push_back(2 * A + spin);
+            for (size_t r = 0; r < empty.size(); ++r) {
+                Det ch = d;
+                flip_bit(ch, i); flip_bit(ch, empty[r]);
+                add(&ch, c->p_single / ((double)n * (double)empty.size()));
+            }
+        }
+        uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+        for (uint64_t P = 0; P < npairs; ++P) {
+            int ii, jj;
+            unrank_pair(P, ii, jj);
+            int p = o[ii], q = o[jj];
+            const std::vector<HBEntry>& tab = c->hb[pair_index(p, q)];
+            if (tab.empty()) { add(nullptr, c->p_double / (double)npairs); continue; }
+            uint64_t prev = 0;
+            for (size_t k = 0; k < tab.size(); ++k) {
+                double pk;
+                if (tab.size() == 1) pk = 1.0;
+                else if (k + 1 == tab.size()) pk = (double)(0 - prev) * 0x1p-64;
+                else pk = (double)(tab[k].cum - prev) * 0x1p-64;
+                prev = tab[k].cum;
+                double pp = (c->p_double / (double)npairs) * pk;
+                if (occ_bit(d, tab[k].a) || occ_bit(d, tab[k].b)) { add(nullptr, pp); continue; }
+                Det ch = d;
+                flip_bit(ch, p); flip_bit(ch, q); flip_bit(ch, tab[k].a); flip_bit(ch, tab[k].b);
+                add(&ch, pp);
+            }
+        }
+    }
+    int64_t m = (int64_t)paths.size();
+    if (m > cap) return -m;
+    for (int64_t i = 0; i < m; ++i) {
+        for (int k = 0; k < c->W; ++k) children[i * c->W + k] = paths[(size_t)i].first.w[k];
+        probs[i] = paths[(size_t)i].second;
+    }
+    return m;
+}
+
+/* UEG basis vectors (3 ints per spatial orbital) and box length */
+int orc_ueg_basis(void* h, int* kvec, double* box) {
+    Ctx* c = (Ctx*)h;
+    if (c->kind != SYS_UEG) return -1;
+    for (int i = 0; i < 3 * c->norb; ++i) kvec[i] = c->kvec[(size_t)i];
+    *box = c->box;
+    return c->norb;
+}
+
+int64_t orc_core(void* h, uint64_t* keys, int64_t cap) {
+    Ctx* c = (Ctx*)h;
+    int64_t n = (int64_t)c->core.size();
+    if (n > cap) return -n;
+    for (int64_t i = 0; i < n; ++i)
+        for (int k = 0; k < c->W; ++k) keys[i * c->W + k] = c->core[(size_t)i].w[k];
+    return n;
+}
+
+}  /* extern "C" */
