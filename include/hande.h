@@ -1,0 +1,181 @@
+/*
+ * hande.h -- C ABI of the GPU FCIQMC engine (libhande.so, one NVIDIA GB300, sm_103a).
+ *
+ * The engine advances the walker population dynamics of full configuration
+ * interaction quantum Monte Carlo as described in the HANDE-QMC paper
+ * (arXiv:1811.11679):
+ *   Sec. 2.1, Eq. (fciqmc)   c_i(t+dt) = c_i(t) - dt sum_j H_ij c_j(t), applied
+ *                            stochastically with signed (real-weight) particles,
+ *                            shift S as a diagonal energy offset, initiator
+ *                            approximation, semi-stochastic propagation;
+ *   Sec. 2.4                 one iteration = spawning, death, annihilation;
+ *   App. A.1                 projected energy E = E_HF + sum_{i!=0} C_i H_0i / C_0,
+ *                            numerator and denominator reported separately;
+ *   App. A.2                 deterministic space "high" of size `semi_stoch_size`
+ *                            chosen at iteration `semi_stoch_start`;
+ *   App. B                   sorted main list + spawned array, annihilation by
+ *                            sorting the spawns and merging them into the list.
+ * The run parameters mirror the paper's `qmc` / `semi_stoch` input tables
+ * (Supplementary tutorial: tau, rng_seed, init_pop, target_population,
+ * initiator, real_amplitudes, spawn_cutoff, state_size, spawned_state_size).
+ *
+ * Conventions
+ *   - Determinants are bit strings over spin orbitals p = 2*spatial + spin
+ *     (alpha = 0), stored as `key_words` 64-bit words; bit p is in word p/64.
+ *     Keys order as unsigned big integers with word key_words-1 most significant.
+ *   - Populations are int64 fixed point: one walker = 2^32 (HANDE_ONE_WALKER).
+ *   - All pointers in this header are HOST pointers unless stated otherwise;
+ *     inputs are copied, the library never keeps a caller pointer.  The
+ *     library owns all device memory of a context (allocated through the
+ *     optional allocator, else cudaMalloc) and frees it in hande_destroy.
+ *   - Every call returns a hande_status; nothing aborts or prints.  Device-side
+ *     errors (capacity, overflow, bounded-wait timeout) are latched on the
+ *     device and reported by the next synchronising call (hande_estimators,
+ *     hande_get_walkers, hande_synchronize); afterwards the context only
+ *     accepts hande_destroy / hande_last_error.
+ *   - hande_iterate is asynchronous and stream-ordered on the context's stream.
+ */
+#ifndef HANDE_H
+#define HANDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HANDE_ONE_WALKER ((int64_t)1 << 32)
+
+typedef enum {
+  HANDE_OK = 0,
+  HANDE_ERR_INVALID = -1,   /* bad argument or system/run parameter */
+  HANDE_ERR_NOMEM = -2,     /* device allocation failed */
+  HANDE_ERR_CAPACITY = -3,  /* walker, spawn or annihilation-tile capacity exceeded */
+  HANDE_ERR_OVERFLOW = -4,  /* a population reached 2^62 in fixed point */
+  HANDE_ERR_CUDA = -5,      /* a CUDA runtime call failed */
+  HANDE_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up */
+  HANDE_ERR_STATE = -7      /* context unusable after an earlier error */
+} hande_status;
+
+typedef enum { HANDE_HUBBARD = 0, HANDE_UEG = 1, HANDE_MOLECULE = 2 } hande_system_kind;
+
+/* The Hamiltonian (the paper's `sys` table).
+ *   HUBBARD   real-space 1D chain/ring of `norb` sites, hopping -t between
+ *             neighbours, on-site U; periodic needs norb >= 3.  Reference
+ *             determinant: alpha on even sites, beta on odd sites.
+ *   UEG       3D uniform electron gas in the `norb` plane waves of lowest
+ *             |n|^2 (ties by (nx, ny, nz)), box from the Wigner-Seitz radius
+ *             rs, Coulomb kernel 4 pi / (Omega |q|^2), q = 0 and Madelung terms
+ *             omitted.  Reference: aufbau.
+ *   MOLECULE  one- and two-electron integrals h1[norb*norb] (row-major,
+ *             symmetric) and eri[norb^4] (chemist order (pq|rs), exactly
+ *             8-fold symmetric), core energy ecore.  Reference: aufbau.
+ *             Host pointers, copied at init. */
+typedef struct {
+  int kind;          /* hande_system_kind */
+  int key_words;     /* 1, 2 or 8; 2*norb must fit in 64*key_words bits */
+  int norb;          /* spatial orbitals (Hubbard: sites) */
+  int nalpha, nbeta; /* electrons per spin */
+  int periodic;      /* Hubbard only */
+  double t, U;       /* Hubbard only */
+  double rs;         /* UEG only */
+  const double* h1;  /* MOLECULE only */
+  const double* eri; /* MOLECULE only */
+  double ecore;      /* MOLECULE only */
+} hande_system;
+
+/* Run parameters (the paper's `qmc` and `semi_stoch` tables). */
+typedef struct {
+  double tau;                 /* time step */
+  double target_population;   /* walkers at which the shift starts to vary */
+  double shift_damping;       /* zeta in S <- S - zeta/(A tau) ln(N_w(t)/N_w(t-A)) */
+  double spawn_cutoff;        /* real weights: smaller spawns are rounded stochastically */
+  double init_pop;            /* walkers placed on the reference at start */
+  double initiator_threshold; /* n_a: a parent is an initiator if |N| > n_a */
+  double p_single;            /* MOLECULE: probability of a single excitation */
+  int shift_period;           /* A: iterations between shift updates (>= 1) */
+  int initiator;              /* 1 = initiator approximation */
+  int real_amplitudes;        /* 1 = real weights, 0 = integer walkers */
+  int semi_stoch_size;        /* deterministic space size, 0 = off (needs real weights) */
+  int semi_stoch_start;       /* iteration at whose end the space is chosen; 0 = at start */
+  uint64_t seed;              /* rng_seed: Philox4x64-10 key word 0 */
+  uint64_t replica;           /* Philox key word 1 (independent replicas) */
+  int64_t state_capacity;     /* max determinants in the main list (0 = default) */
+  int64_t spawn_capacity;     /* max spawns per iteration (0 = default) */
+  int record_capacity;        /* estimator records kept on the device (0 = default) */
+} hande_qmc;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  `alloc`
+ * returns a device pointer aligned to 256 bytes or NULL; `free` releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, size_t bytes, void* user);
+  void* user;
+} hande_allocator;
+
+/* One iteration's estimators (App. A.1), evaluated on the list at the start
+ * of the iteration, plus population and throughput counters. */
+typedef struct {
+  int64_t iter;        /* iteration number t >= 1 */
+  double shift;        /* S after the update at the end of iteration t */
+  int64_t nw_pre;      /* sum |N_i| at the start of t (fixed point) */
+  int64_t n0;          /* N on the reference determinant (fixed point) */
+  int64_t num_hi;      /* numerator sum_{j!=0} N_j H_0j * 2^16, exact 128-bit (hi word) */
+  uint64_t num_lo;     /*   ... (lo word) */
+  double num;          /* the same numerator as a double, in fixed-point population units */
+  int64_t nw_post;     /* sum |N_i| after annihilation */
+  int64_t ndet;        /* occupied determinants after annihilation */
+  int64_t natt;        /* spawning attempts */
+  int64_t nspawn;      /* nonzero spawns */
+} hande_estimate;
+
+typedef struct hande_ctx hande_ctx;
+
+/* Build the system tables, the reference determinant with `init_pop` walkers
+ * and the device buffers on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  `allocator` may be NULL.  On success *out owns the context. */
+hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, const hande_allocator* allocator,
+                               void* cuda_stream, hande_ctx** out);
+
+/* Advance n >= 0 iterations (asynchronous; one CUDA-graph launch per iteration). */
+hande_status hande_iterate(hande_ctx* ctx, int n);
+
+/* Wait for the stream and report latched device errors. */
+hande_status hande_synchronize(hande_ctx* ctx);
+
+/* Copy the records not yet fetched (oldest first, at most `max`) to `out`;
+ * *n_out = records written.  Synchronises.  HANDE_ERR_CAPACITY if records
+ * were overwritten before being fetched (record_capacity too small). */
+hande_status hande_estimators(hande_ctx* ctx, hande_estimate* out, int max, int* n_out);
+
+/* Copy the current walker list, sorted by key: keys[n*key_words] (word 0
+ * first per walker), pops[n], hdiag[n] (H_ii - E_ref, may be NULL), flags[n]
+ * (bit0 = in the deterministic space, may be NULL).  HANDE_ERR_CAPACITY with
+ * *n set if cap is too small.  Synchronises. */
+hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, double* hdiag, uint8_t* flags,
+                               int64_t cap, int64_t* n);
+
+/* Replace the walker list with n entries (keys strictly ascending, the
+ * reference determinant must be present).  hdiag may be NULL, in which case
+ * H_ii - E_ref is evaluated on the device.  With semi_stoch_start == 0 the
+ * deterministic space is chosen from this list.  Synchronises. */
+hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
+                               int64_t n);
+
+/* E_ref = H_00 of the reference determinant, and its key (key_words words). */
+hande_status hande_reference(hande_ctx* ctx, double* e_ref, uint64_t* key);
+
+/* Completed iterations. */
+int64_t hande_iterations(const hande_ctx* ctx);
+
+/* Free all device memory and the context (safe on NULL). */
+void hande_destroy(hande_ctx* ctx);
+
+/* Last error message of the context ("" if none); static text for NULL. */
+const char* hande_last_error(const hande_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HANDE_H */

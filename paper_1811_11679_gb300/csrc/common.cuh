@@ -1,0 +1,252 @@
+// common.cuh -- device-side building blocks of the GPU FCIQMC iteration.
+//
+// Arithmetic that decides the walker list is exact and order-independent:
+// populations are int64 fixed point (one walker = 2^32), sums of FP64 terms
+// are accumulated exactly in 128-bit fixed point (2^-16 resolution), and
+// every FP64 expression is written with explicit round-to-nearest intrinsics
+// (__dadd_rn, __dmul_rn, ...) so the compiler cannot contract or reorder it.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hande {
+
+constexpr int64_t kOne = int64_t(1) << 32;            // one walker
+constexpr uint64_t kDetDraw = ~0ull;                   // attempt index of per-determinant draws
+
+// error bits (reported through the C ABI as hande_status codes)
+enum : unsigned {
+  ERR_SPAWN_CAPACITY = 1u,
+  ERR_STATE_CAPACITY = 2u,
+  ERR_OVERFLOW = 4u,
+  ERR_TIMEOUT = 8u,
+  ERR_TILE_CAPACITY = 16u,
+  ERR_BUCKET_CAPACITY = 32u,
+};
+
+// ------------------------------------------------------------------ keys
+// A determinant: W 64-bit words, bit p = spin orbital p (p = 2*spatial + spin).
+// Order: unsigned big integer, word W-1 most significant.
+template <int W>
+struct Key {
+  uint64_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ bool key_lt(const Key<W>& a, const Key<W>& b) {
+#pragma unroll
+  for (int i = W - 1; i >= 0; --i) {
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+  }
+  return false;
+}
+template <int W>
+__device__ __forceinline__ bool key_eq(const Key<W>& a, const Key<W>& b) {
+  bool e = true;
+#pragma unroll
+  for (int i = 0; i < W; ++i) e &= (a.w[i] == b.w[i]);
+  return e;
+}
+template <int W>
+__device__ __forceinline__ bool key_le(const Key<W>& a, const Key<W>& b) {
+  return !key_lt<W>(b, a);
+}
+// load / store from a structure-of-arrays key block: word k of entry i at p[k*stride + i]
+template <int W>
+__device__ __forceinline__ Key<W> load_key(const uint64_t* __restrict__ p, int64_t stride, int64_t i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = p[j * stride + i];
+  return k;
+}
+template <int W>
+__device__ __forceinline__ void store_key(uint64_t* __restrict__ p, int64_t stride, int64_t i, const Key<W>& k) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) p[j * stride + i] = k.w[j];
+}
+template <int W>
+__device__ __forceinline__ int key_popc_xor(const Key<W>& a, const Key<W>& b) {
+  int n = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) n += __popcll(a.w[j] ^ b.w[j]);
+  return n;
+}
+template <int W>
+__device__ __forceinline__ bool key_bit(const Key<W>& k, int p) {
+  return (k.w[p >> 6] >> (p & 63)) & 1ull;
+}
+template <int W>
+__device__ __forceinline__ void key_flip(Key<W>& k, int p) {
+  k.w[p >> 6] ^= 1ull << (p & 63);
+}
+// number of set bits strictly between spin orbitals p and q (fermionic sign)
+template <int W>
+__device__ __forceinline__ int key_between(const Key<W>& k, int p, int q) {
+  int lo = p < q ? p : q, hi = p < q ? q : p;
+  int n = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    int b0 = j * 64;
+    // bits (lo, hi) restricted to this word
+    int s = lo + 1 - b0, e = hi - b0;  // [s, e)
+    if (s < 0) s = 0;
+    if (e > 64) e = 64;
+    if (e > s) {
+      uint64_t m = (e == 64 ? ~0ull : ((1ull << e) - 1)) & ~((s == 0) ? 0ull : ((1ull << s) - 1));
+      n += __popcll(k.w[j] & m);
+    }
+  }
+  return n;
+}
+// position of the r-th (0-based) set bit of a 64-bit word
+__device__ __forceinline__ int select64(uint64_t x, int r) {
+  unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
+  int c = __popc(lo);
+  if (r < c) return __fns(lo, 0, r + 1);
+  return 32 + __fns(hi, 0, r - c + 1);
+}
+// position of the r-th set bit of a multiword mask
+template <int W>
+__device__ __forceinline__ int select_bit(const Key<W>& k, int r) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    int c = __popcll(k.w[j]);
+    if (r < c) return j * 64 + select64(k.w[j], r);
+    r -= c;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Counter-based generator of Salmon et al. (SC'11): 10 rounds of two 64x64->128
+// multiplies with Weyl key increments.
+struct Words4 {
+  uint64_t x, y, z, w;
+};
+__device__ __forceinline__ Words4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                                uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B97F4A7C15ull;
+      k1 += 0xBB67AE8584CAA73Bull;
+    }
+    uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
+    uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  return {c0, c1, c2, c3};
+}
+__device__ __forceinline__ uint64_t splitmix_fold(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xbf58476d1ce4e5b9ull;
+  z ^= z >> 27;
+  z *= 0x94d049bb133111ebull;
+  z ^= z >> 31;
+  return z;
+}
+// stream of determinant D at iteration t, attempt a: counter (t, a, h0(D), h1(D)),
+// key (seed, replica); h = the key words for W <= 2, a SplitMix64 fold above.
+template <int W>
+__device__ __forceinline__ Words4 draw(uint64_t seed, uint64_t replica, int64_t t, uint64_t a, const Key<W>& d) {
+  uint64_t h0, h1;
+  if (W <= 2) {
+    h0 = d.w[0];
+    h1 = (W == 2) ? d.w[W - 1] : 0ull;
+  } else {
+    uint64_t p = 0x243F6A8885A308D3ull, q = 0x13198A2E03707344ull;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      p = splitmix_fold(p ^ d.w[j]);
+      q = splitmix_fold(q ^ d.w[j]);
+    }
+    h0 = p;
+    h1 = q;
+  }
+  return philox4x64_10((uint64_t)t, a, h0, h1, seed, replica);
+}
+__device__ __forceinline__ uint64_t draw_index(uint64_t w, uint64_t n) { return __umul64hi(w, n); }
+__device__ __forceinline__ double draw_unit(uint64_t w) { return __dmul_rn((double)(w >> 11), 0x1p-53); }
+
+// ------------------------------------------------------------------ natural log
+// atanh series: x = m 2^e with m in [sqrt(1/2), sqrt(2)), s = (m-1)/(m+1),
+// ln x = e ln2 + 2 s sum_{k=0..11} s^(2k) / (2k+1); Horner in s^2.
+__device__ __forceinline__ double log_series(double x) {
+  if (!(x > 0.0)) return __longlong_as_double((long long)0xfff0000000000000ull);  // -inf
+  uint64_t bits = (uint64_t)__double_as_longlong(x);
+  int e = (int)((bits >> 52) & 0x7ff);
+  if (e == 0) {
+    double y = __dmul_rn(x, 18446744073709551616.0);
+    bits = (uint64_t)__double_as_longlong(y);
+    e = (int)((bits >> 52) & 0x7ff) - 64;
+  }
+  e -= 1023;
+  double m = __longlong_as_double((long long)((bits & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+  if (m > 1.4142135623730951) {
+    m = __dmul_rn(m, 0.5);
+    e += 1;
+  }
+  double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+  double z = __dmul_rn(s, s);
+  double p = __ddiv_rn(1.0, 23.0);
+  for (int k = 10; k >= 0; --k) {
+    p = __dmul_rn(p, z);
+    p = __dadd_rn(p, __ddiv_rn(1.0, (double)(2 * k + 1)));
+  }
+  double lnm = __dmul_rn(__dmul_rn(2.0, s), p);
+  return __dadd_rn(__dmul_rn((double)e, 0.69314718055994530942), lnm);
+}
+
+// ------------------------------------------------------------------ exact sums
+// term -> round_half_even(term * 2^16) as a signed 128-bit integer (lo, hi words)
+struct I128 {
+  uint64_t lo;
+  int64_t hi;
+};
+__device__ __forceinline__ I128 fixed_from_double(double term) {
+  double v = __dmul_rn(term, 65536.0);
+  double a = fabs(v);
+  double h = floor(__dmul_rn(a, 0x1p-64));
+  double rem = __dsub_rn(a, __dmul_rn(h, 18446744073709551616.0));
+  uint64_t lo = __double2ull_rn(rem);
+  uint64_t hi = (uint64_t)h;
+  if (v < 0.0) {  // two's complement negate
+    lo = ~lo;
+    hi = ~hi;
+    lo += 1;
+    if (lo == 0) hi += 1;
+  }
+  return {lo, (int64_t)hi};
+}
+__device__ __forceinline__ void i128_add(I128& a, const I128& b) {
+  uint64_t lo = a.lo + b.lo;
+  uint64_t c = lo < a.lo ? 1 : 0;
+  a.hi = (int64_t)((uint64_t)a.hi + (uint64_t)b.hi + c);
+  a.lo = lo;
+}
+__device__ __forceinline__ double fixed_to_double(I128 s) {
+  double d = __dadd_rn(__dmul_rn((double)s.hi, 18446744073709551616.0), __ull2double_rn(s.lo));
+  return __dmul_rn(d, 0x1p-16);
+}
+__device__ __forceinline__ I128 shfl_xor_i128(I128 v, int m) {
+  I128 r;
+  r.lo = __shfl_xor_sync(0xffffffffu, v.lo, m);
+  r.hi = __shfl_xor_sync(0xffffffffu, v.hi, m);
+  return r;
+}
+__device__ __forceinline__ void atomic_add_i128(unsigned long long* lo_hi, I128 v) {
+  unsigned long long old = atomicAdd(lo_hi, (unsigned long long)v.lo);
+  unsigned long long c = (old + v.lo < old) ? 1ull : 0ull;
+  atomicAdd(lo_hi + 1, (unsigned long long)v.hi + c);
+}
+
+// ------------------------------------------------------------------ misc
+__device__ __forceinline__ int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
+__device__ __forceinline__ unsigned warp_lane() { return threadIdx.x & 31u; }
+
+}  // namespace hande

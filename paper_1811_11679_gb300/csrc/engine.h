@@ -1,0 +1,64 @@
+// engine.h -- host-side state of one FCIQMC context and the per-key-width
+// kernel launchers (implemented in inst_w*.cu, dispatched from host.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hande.h"
+#include "kernels.cuh"
+
+namespace hande {
+
+struct Engine;
+
+// launchers for one (key width, system kind) pair
+struct Ops {
+  void (*iteration)(Engine& E, int cur, bool core, cudaStream_t s);
+  void (*hdiag)(Engine& E, int cur, int64_t n, cudaStream_t s);
+  void (*eref)(Engine& E, cudaStream_t s);
+  void (*csr_count)(Engine& E, int32_t* rowcnt, cudaStream_t s);
+  void (*csr_fill)(Engine& E, cudaStream_t s);
+  void (*sel_gather)(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s);
+  void (*sel_hist)(Engine& E, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist,
+                   cudaStream_t s);
+  void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);
+  size_t (*merge_smem)(int tc, int sm);
+  const void* merge_kernel;
+};
+
+Ops ops_w1(int kind);
+Ops ops_w2(int kind);
+Ops ops_w8(int kind);
+
+struct Engine {
+  Params P{};            // device pointers and run constants (kernel argument)
+  Ops ops{};
+  int W = 1, kind = 0, nalpha = 0, nbeta = 0;
+  cudaStream_t stream = nullptr;      // caller's stream
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  hande_allocator alloc{};
+  bool has_alloc = false;
+  std::vector<std::pair<void*, size_t>> blocks;
+  int merge_grid = 0;
+  size_t merge_smem_bytes = 0;
+  int attempt_grid = 0;
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int cur = 0;
+  int64_t host_iter = 0;
+  int64_t fetched = 0;
+  bool core_active = false;
+  int core_size = 0, core_start = 0;
+  // core storage (device)
+  uint64_t* core_key = nullptr;
+  int64_t* core_rowptr = nullptr;
+  int32_t* core_col = nullptr;
+  double* core_val = nullptr;
+  int64_t nnz_cap = 0, ncore_cap = 0;
+  double e_ref = 0.0;
+  bool failed = false;
+  std::string err;
+};
+
+}  // namespace hande

@@ -1,0 +1,751 @@
+// host.cu -- the C ABI (include/hande.h): context set-up, system tables, device
+// memory, CUDA-graph capture of one iteration, deterministic-space selection,
+// estimator records and walker-list transfer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+using namespace hande;
+
+struct hande_ctx {
+  Engine E;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+struct CudaError {
+  cudaError_t e;
+  const char* what;
+};
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t _e = (call);                          \
+    if (_e != cudaSuccess) throw CudaError{_e, #call}; \
+  } while (0)
+
+struct Fail {
+  hande_status code;
+  std::string msg;
+};
+
+void* dev_alloc(Engine& E, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (E.has_alloc) {
+    p = E.alloc.alloc(bytes, E.alloc.user);
+    if (!p) throw Fail{HANDE_ERR_NOMEM, "device allocation failed (" + std::to_string(bytes) + " bytes)"};
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{HANDE_ERR_NOMEM, "cudaMalloc failed (" + std::to_string(bytes) + " bytes)"};
+    }
+  }
+  E.blocks.push_back({p, bytes});
+  return p;
+}
+template <typename T>
+T* dalloc(Engine& E, size_t count) {
+  return static_cast<T*>(dev_alloc(E, count * sizeof(T)));
+}
+
+void release_all(Engine& E) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b)
+      if (E.graph[a][b]) {
+        cudaGraphExecDestroy(E.graph[a][b]);
+        E.graph[a][b] = nullptr;
+      }
+  cudaStreamSynchronize(E.stream);
+  for (auto& blk : E.blocks) {
+    if (E.has_alloc) E.alloc.free(blk.first, blk.second, E.alloc.user);
+    else cudaFree(blk.first);
+  }
+  E.blocks.clear();
+  if (E.cap_stream) {
+    cudaStreamDestroy(E.cap_stream);
+    E.cap_stream = nullptr;
+  }
+}
+
+// ---------------------------------------------------------------- system tables
+struct HostTables {
+  std::vector<int4> kvec;
+  std::vector<int16_t> klookup;
+  std::vector<double> h1, eri_packed;
+  std::vector<int> hb_start, hb_len;
+  std::vector<uint16_t> hb_ab;
+  std::vector<uint64_t> hb_cum;
+};
+
+inline size_t tri_h(size_t p, size_t q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
+
+// plane waves n in Z^3 ordered by (|n|^2, nx, ny, nz); the first norb are the basis
+void build_ueg(const hande_system& s, SysDev& sd, HostTables& T) {
+  struct PW {
+    int n2, x, y, z;
+  };
+  int R = 1;
+  std::vector<PW> pts;
+  for (;;) {
+    pts.clear();
+    for (int x = -R; x <= R; ++x)
+      for (int y = -R; y <= R; ++y)
+        for (int z = -R; z <= R; ++z) {
+          int n2 = x * x + y * y + z * z;
+          if (n2 <= R * R) pts.push_back({n2, x, y, z});
+        }
+    if ((int)pts.size() > s.norb) break;
+    ++R;
+  }
+  std::sort(pts.begin(), pts.end(), [](const PW& a, const PW& b) {
+    if (a.n2 != b.n2) return a.n2 < b.n2;
+    if (a.x != b.x) return a.x < b.x;
+    if (a.y != b.y) return a.y < b.y;
+    return a.z < b.z;
+  });
+  int nmax = 0;
+  T.kvec.resize(s.norb);
+  for (int i = 0; i < s.norb; ++i) {
+    T.kvec[i] = make_int4(pts[i].x, pts[i].y, pts[i].z, pts[i].n2);
+    nmax = std::max(nmax, std::max(std::abs(pts[i].x), std::max(std::abs(pts[i].y), std::abs(pts[i].z))));
+  }
+  int side = 2 * nmax + 1;
+  T.klookup.assign((size_t)side * side * side, (int16_t)-1);
+  for (int i = 0; i < s.norb; ++i)
+    T.klookup[((size_t)(T.kvec[i].x + nmax) * side + (T.kvec[i].y + nmax)) * side + (T.kvec[i].z + nmax)] = (int16_t)i;
+  sd.nmax = nmax;
+  sd.side = side;
+  // Omega = (4 pi / 3) rs^3 N, L = Omega^(1/3); 4 pi / (Omega (2 pi / L)^2 m) = 1 / (pi L m)
+  const int nel = s.nalpha + s.nbeta;
+  double box = s.rs * cbrt(4.0 * kPi * (double)nel / 3.0);
+  sd.vfac = 1.0 / (kPi * box);
+  double kf = 2.0 * kPi / box;
+  sd.kfac = 0.5 * (kf * kf);
+}
+
+double g_so(const std::vector<double>& eri, int n, int p, int q, int r, int t) {
+  if (((p ^ q) & 1) || ((r ^ t) & 1)) return 0.0;
+  size_t N = (size_t)n;
+  return eri[(((size_t)(p >> 1) * N + (q >> 1)) * N + (r >> 1)) * N + (t >> 1)];
+}
+
+void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostTables& T) {
+  const int n = s.norb;
+  const size_t N = (size_t)n;
+  T.h1.assign(s.h1, s.h1 + N * N);
+  std::vector<double> eri(s.eri, s.eri + N * N * N * N);
+  for (int p = 0; p < n; ++p)
+    for (int r = 0; r < n; ++r)
+      if (T.h1[p * N + r] != T.h1[r * N + p]) throw Fail{HANDE_ERR_INVALID, "h1 is not symmetric"};
+  size_t npair = N * (N + 1) / 2;
+  T.eri_packed.assign(npair * (npair + 1) / 2, 0.0);
+  auto at = [&](size_t a, size_t b, size_t c, size_t d) { return eri[((a * N + b) * N + c) * N + d]; };
+  for (size_t a = 0; a < N; ++a)
+    for (size_t b = 0; b < N; ++b)
+      for (size_t c = 0; c < N; ++c)
+        for (size_t d = 0; d < N; ++d) {
+          double v = at(a, b, c, d);
+          if (v != at(b, a, c, d) || v != at(a, b, d, c) || v != at(c, d, a, b))
+            throw Fail{HANDE_ERR_INVALID, "eri is not 8-fold symmetric"};
+          T.eri_packed[tri_h(tri_h(a, b), tri_h(c, d))] = v;
+        }
+  sd.ecore = s.ecore;
+  // heat-bath tables: for each occupied pair p<q (index q(q-1)/2 + p), every
+  // spin-allowed target pair a<b outside {p, q} with |<pq||ab>| > 0, in ascending
+  // (a, b) order, as cumulative thresholds floor(2^64 S_k / S_total) made strictly
+  // increasing; the last entry takes the remainder.
+  const int ns = 2 * n;
+  T.hb_start.assign((size_t)ns * (ns - 1) / 2, 0);
+  T.hb_len.assign((size_t)ns * (ns - 1) / 2, 0);
+  for (int qq = 1; qq < ns; ++qq) {
+    for (int pp = 0; pp < qq; ++pp) {
+      const int idx = qq * (qq - 1) / 2 + pp;
+      const int start = (int)T.hb_ab.size();
+      std::vector<double> wts;
+      for (int a = 0; a < ns; ++a) {
+        for (int b = a + 1; b < ns; ++b) {
+          if (a == pp || a == qq || b == pp || b == qq) continue;
+          const bool direct = ((a & 1) == (pp & 1)) && ((b & 1) == (qq & 1));
+          const bool swapped = ((a & 1) == (qq & 1)) && ((b & 1) == (pp & 1));
+          if (!direct && !swapped) continue;
+          double v = g_so(eri, n, pp, a, qq, b) - g_so(eri, n, pp, b, qq, a);
+          double w = std::fabs(v);
+          if (!(w > 0.0)) continue;
+          T.hb_ab.push_back((uint16_t)(a | (b << 8)));
+          T.hb_cum.push_back(0);
+          wts.push_back(w);
+        }
+      }
+      const int len = (int)wts.size();
+      T.hb_start[idx] = start;
+      T.hb_len[idx] = len;
+      if (len > 0) {
+        std::vector<double> run(len);
+        double acc = 0.0;
+        for (int k = 0; k < len; ++k) {
+          acc = acc + wts[k];
+          run[k] = acc;
+        }
+        uint64_t last = 0;
+        for (int k = 0; k + 1 < len; ++k) {
+          double frac = run[k] / acc;
+          uint64_t c = frac >= 1.0 ? ~0ull : (uint64_t)(frac * 18446744073709551616.0);
+          if (c <= last) c = last + 1;
+          T.hb_cum[start + k] = c;
+          last = c;
+        }
+        T.hb_cum[start + len - 1] = ~0ull;
+      }
+    }
+  }
+  sd.psingle_thr = (uint32_t)llrint(q.p_single * 4294967296.0);
+  sd.p_single = (double)sd.psingle_thr * 0x1p-32;
+  sd.p_double = (double)(4294967296ull - sd.psingle_thr) * 0x1p-32;
+}
+
+template <typename T>
+T* upload(Engine& E, const std::vector<T>& v) {
+  if (v.empty()) return nullptr;
+  T* d = dalloc<T>(E, v.size());
+  CK(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, E.stream));
+  return d;
+}
+
+unsigned read_error(Engine& E) {
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, (char*)E.P.st + offsetof(DevState, error), sizeof(e), cudaMemcpyDeviceToHost, E.stream));
+  CK(cudaStreamSynchronize(E.stream));
+  return e;
+}
+
+hande_status map_error(Engine& E, unsigned e) {
+  if (!e) return HANDE_OK;
+  E.failed = true;
+  if (e & ERR_OVERFLOW) {
+    E.err = "population overflow (|N| reached 2^62 in fixed point)";
+    return HANDE_ERR_OVERFLOW;
+  }
+  if (e & ERR_TIMEOUT) {
+    E.err = "bounded device wait timed out (annihilation look-back)";
+    return HANDE_ERR_TIMEOUT;
+  }
+  if (e & ERR_SPAWN_CAPACITY) E.err = "spawn capacity exceeded (raise spawn_capacity)";
+  else if (e & ERR_STATE_CAPACITY) E.err = "walker-list capacity exceeded (raise state_capacity)";
+  else if (e & ERR_TILE_CAPACITY) E.err = "annihilation tile capacity exceeded (too many distinct new determinants in one key range)";
+  else E.err = "bucket capacity exceeded";
+  return HANDE_ERR_CAPACITY;
+}
+
+void ensure_graph(Engine& E, int cur, int core) {
+  if (E.graph[cur][core]) return;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(E.cap_stream, cudaStreamCaptureModeThreadLocal));
+  E.ops.iteration(E, cur, core != 0, E.cap_stream);
+  cudaError_t launch_err = cudaGetLastError();
+  CK(cudaStreamEndCapture(E.cap_stream, &g));
+  if (launch_err != cudaSuccess) {
+    cudaGraphDestroy(g);
+    throw CudaError{launch_err, "kernel launch during capture"};
+  }
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  CK(ie);
+  E.graph[cur][core] = ex;
+}
+
+void drop_graphs(Engine& E, int core) {
+  for (int c = 0; c < 2; ++c)
+    if (E.graph[c][core]) {
+      cudaGraphExecDestroy(E.graph[c][core]);
+      E.graph[c][core] = nullptr;
+    }
+}
+
+// run the int64 scan machinery on natt[0..ndet[cur]) -> att_begin, total -> scan_total
+void scan_natt(Engine& E, int cur) {
+  Params& P = E.P;
+  int64_t* n = st_field_i64(P.st, offsetof(DevState, ndet) + 8 * cur);
+  k_scan_reduce<int64_t><<<kScanBlocks, kScanThreads, 0, E.stream>>>(P.natt, n, P.part, P.st);
+  k_scan_partials_i64<<<1, 1024, 0, E.stream>>>(P.part, kScanBlocks, st_field_i64(P.st, offsetof(DevState, scan_total)),
+                                                 P.st);
+  k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, E.stream>>>(P.natt, P.att_begin, n, P.part, P.st);
+  CK(cudaGetLastError());
+}
+
+int64_t read_i64(Engine& E, size_t off) {
+  int64_t v = 0;
+  CK(cudaMemcpyAsync(&v, (char*)E.P.st + off, 8, cudaMemcpyDeviceToHost, E.stream));
+  CK(cudaStreamSynchronize(E.stream));
+  return v;
+}
+
+// Deterministic space "high": the reference plus the (size - 1) other
+// determinants of largest |N| (ties by ascending key), then H' in CSR.
+void select_core(Engine& E) {
+  Params& P = E.P;
+  const int cur = E.cur;
+  const int64_t n = read_i64(E, offsetof(DevState, ndet) + 8 * cur);
+  const int64_t want = (int64_t)E.core_size - 1;
+  unsigned long long* hist = dalloc<unsigned long long>(E, 256);
+  uint64_t vstar = 0;
+  int64_t need_eq = INT64_MAX;
+  if (want < n - 1) {  // otherwise every determinant is taken
+    uint64_t mask = 0, prefix = 0;
+    int64_t remaining = want;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), E.stream));
+      E.ops.sel_hist(E, cur, shift, mask, prefix, hist, E.stream);
+      unsigned long long h[256];
+      CK(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, E.stream));
+      CK(cudaStreamSynchronize(E.stream));
+      int d = 255;
+      for (; d >= 0; --d) {
+        if ((int64_t)h[d] >= remaining) break;
+        remaining -= (int64_t)h[d];
+      }
+      if (d < 0) d = 0;
+      prefix |= (uint64_t)d << shift;
+      mask |= (uint64_t)255 << shift;
+    }
+    vstar = prefix;
+    need_eq = remaining;
+    if (want <= 0) {
+      vstar = ~0ull;
+      need_eq = 0;
+    }
+    E.ops.sel_flags(E, cur, vstar, need_eq, 0, E.stream);
+    scan_natt(E, cur);
+  }
+  E.ops.sel_flags(E, cur, vstar, need_eq, 1, E.stream);
+  scan_natt(E, cur);
+  const int64_t ncore = read_i64(E, offsetof(DevState, scan_total));
+  if (ncore > E.ncore_cap) {
+    E.core_key = dalloc<uint64_t>(E, (size_t)ncore * E.W);
+    E.ncore_cap = ncore;
+    P.core_pos = dalloc<int64_t>(E, ncore);
+    P.core_delta = dalloc<int64_t>(E, ncore);
+    E.core_rowptr = dalloc<int64_t>(E, ncore + 1);
+  }
+  E.ops.sel_gather(E, cur, E.core_key, ncore, E.stream);
+  P.ncore = (int)ncore;
+  P.core_key = E.core_key;
+  // CSR of H' restricted to the core
+  int32_t* rowcnt = dalloc<int32_t>(E, ncore);
+  E.ops.csr_count(E, rowcnt, E.stream);
+  k_scan_small<<<1, 1024, 0, E.stream>>>(rowcnt, E.core_rowptr, (int)ncore);
+  CK(cudaGetLastError());
+  int64_t nnz = 0;
+  CK(cudaMemcpyAsync(&nnz, E.core_rowptr + ncore, 8, cudaMemcpyDeviceToHost, E.stream));
+  CK(cudaStreamSynchronize(E.stream));
+  if (nnz > E.nnz_cap) {
+    E.core_col = dalloc<int32_t>(E, nnz);
+    E.core_val = dalloc<double>(E, nnz);
+    E.nnz_cap = nnz;
+  }
+  P.core_rowptr = E.core_rowptr;
+  P.core_col = E.core_col;
+  P.core_val = E.core_val;
+  E.ops.csr_fill(E, E.stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(E.stream));
+  drop_graphs(E, 1);
+  E.core_active = true;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+namespace {
+hande_status run_guarded(Engine* E, const std::function<hande_status()>& body) {
+  try {
+    return body();
+  } catch (const Fail& f) {
+    if (E) {
+      E->err = f.msg;
+      if (f.code != HANDE_ERR_INVALID && f.code != HANDE_ERR_CAPACITY) E->failed = true;
+    }
+    return f.code;
+  } catch (const CudaError& c) {
+    if (E) {
+      E->err = std::string(c.what) + ": " + cudaGetErrorString(c.e);
+      E->failed = true;
+    }
+    return HANDE_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    if (E) E->err = "host allocation failed";
+    return HANDE_ERR_NOMEM;
+  }
+}
+}  // namespace
+
+extern "C" {
+
+hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, const hande_allocator* allocator,
+                               void* cuda_stream, hande_ctx** out) {
+  if (!sys || !qmc || !out) return HANDE_ERR_INVALID;
+  *out = nullptr;
+  hande_ctx* ctx = new (std::nothrow) hande_ctx();
+  if (!ctx) return HANDE_ERR_NOMEM;
+  Engine& E = ctx->E;
+  hande_status st = run_guarded(&E, [&]() -> hande_status {
+    const hande_system& s = *sys;
+    const hande_qmc& q = *qmc;
+    // ---- validation
+    if (s.key_words != 1 && s.key_words != 2 && s.key_words != 8) throw Fail{HANDE_ERR_INVALID, "key_words must be 1, 2 or 8"};
+    if (s.kind < 0 || s.kind > 2) throw Fail{HANDE_ERR_INVALID, "unknown system kind"};
+    if (s.norb < 1 || 2 * s.norb > 64 * s.key_words) throw Fail{HANDE_ERR_INVALID, "2*norb must fit in the key"};
+    if (s.nalpha < 0 || s.nbeta < 0 || s.nalpha > s.norb || s.nbeta > s.norb || s.nalpha + s.nbeta < 2)
+      throw Fail{HANDE_ERR_INVALID, "bad electron numbers"};
+    if (s.kind == HANDE_HUBBARD) {
+      if (s.periodic && s.norb < 3) throw Fail{HANDE_ERR_INVALID, "periodic Hubbard needs at least 3 sites"};
+      if (s.nalpha > (s.norb + 1) / 2 || s.nbeta > s.norb / 2)
+        throw Fail{HANDE_ERR_INVALID, "Hubbard reference needs nalpha <= ceil(L/2), nbeta <= floor(L/2)"};
+    }
+    if (s.kind == HANDE_MOLECULE && (!s.h1 || !s.eri || 2 * s.norb > 255))
+      throw Fail{HANDE_ERR_INVALID, "molecule needs h1, eri and at most 127 orbitals"};
+    if (s.kind == HANDE_UEG && !(s.rs > 0.0)) throw Fail{HANDE_ERR_INVALID, "UEG needs rs > 0"};
+    if (!(q.tau > 0.0) || !(q.init_pop > 0.0)) throw Fail{HANDE_ERR_INVALID, "tau and init_pop must be positive"};
+    if (q.semi_stoch_size > 0 && !q.real_amplitudes)
+      throw Fail{HANDE_ERR_INVALID, "semi-stochastic propagation needs real amplitudes"};
+    if (q.semi_stoch_size < 0 || q.semi_stoch_start < 0) throw Fail{HANDE_ERR_INVALID, "bad semi_stoch parameters"};
+    if (q.real_amplitudes && !(q.spawn_cutoff >= 0.0)) throw Fail{HANDE_ERR_INVALID, "bad spawn_cutoff"};
+    if (s.kind == HANDE_MOLECULE && !(q.p_single >= 0.0 && q.p_single < 1.0))
+      throw Fail{HANDE_ERR_INVALID, "p_single must be in [0, 1)"};
+
+    E.W = s.key_words;
+    E.kind = s.kind;
+    E.nalpha = s.nalpha;
+    E.nbeta = s.nbeta;
+    E.stream = (cudaStream_t)cuda_stream;
+    if (allocator && allocator->alloc && allocator->free) {
+      E.alloc = *allocator;
+      E.has_alloc = true;
+    }
+    E.ops = E.W == 1 ? ops_w1(s.kind) : (E.W == 2 ? ops_w2(s.kind) : ops_w8(s.kind));
+    CK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
+
+    Params& P = E.P;
+    P.W = E.W;
+    P.tau = q.tau;
+    P.cutoff = q.spawn_cutoff;
+    P.zeta = q.shift_damping;
+    P.real_amp = q.real_amplitudes ? 1 : 0;
+    P.initiator = q.initiator ? 1 : 0;
+    P.period = q.shift_period > 0 ? q.shift_period : 1;
+    P.target_fixed = q.target_population * 4294967296.0 >= 9223372036854775807.0
+                         ? INT64_MAX
+                         : llrint(q.target_population * 4294967296.0);
+    P.init_thr = q.initiator_threshold * 4294967296.0 >= 9223372036854775807.0
+                     ? INT64_MAX
+                     : llrint(q.initiator_threshold * 4294967296.0);
+    P.seed = q.seed;
+    P.replica = q.replica;
+    P.cap = q.state_capacity > 0 ? q.state_capacity : (int64_t)1 << 20;
+    P.scap = q.spawn_capacity > 0 ? q.spawn_capacity : (int64_t)1 << 21;
+    if (P.scap >= ((int64_t)1 << 31)) throw Fail{HANDE_ERR_INVALID, "spawn_capacity must be below 2^31"};
+    P.rec_cap = q.record_capacity > 0 ? q.record_capacity : 1 << 16;
+    P.tile_cap = E.W == 1 ? 2048 : (E.W == 2 ? 2048 : 1024);
+    P.seg_max = P.tile_cap / 2;
+    E.core_size = q.semi_stoch_size;
+    E.core_start = q.semi_stoch_start;
+
+    // ---- reference determinant
+    std::memset(P.d0, 0, sizeof P.d0);
+    auto setbit = [&](int p) { P.d0[p >> 6] |= 1ull << (p & 63); };
+    if (s.kind == HANDE_HUBBARD) {
+      for (int k = 0; k < s.nalpha; ++k) setbit(2 * (2 * k));
+      for (int k = 0; k < s.nbeta; ++k) setbit(2 * (2 * k + 1) + 1);
+    } else {
+      for (int k = 0; k < s.nalpha; ++k) setbit(2 * k);
+      for (int k = 0; k < s.nbeta; ++k) setbit(2 * k + 1);
+    }
+
+    // ---- system tables
+    SysDev& sd = P.sys;
+    std::memset(&sd, 0, sizeof sd);
+    sd.norb = s.norb;
+    sd.nspin = 2 * s.norb;
+    sd.nel = s.nalpha + s.nbeta;
+    sd.L = s.norb;
+    sd.periodic = s.periodic;
+    sd.t = s.t;
+    sd.U = s.U;
+    HostTables T;
+    if (s.kind == HANDE_UEG) build_ueg(s, sd, T);
+    if (s.kind == HANDE_MOLECULE) build_molecule(s, q, sd, T);
+    sd.kvec = upload(E, T.kvec);
+    sd.klookup = upload(E, T.klookup);
+    sd.h1 = upload(E, T.h1);
+    sd.eri = upload(E, T.eri_packed);
+    sd.hb_start = upload(E, T.hb_start);
+    sd.hb_len = upload(E, T.hb_len);
+    sd.hb_ab = upload(E, T.hb_ab);
+    sd.hb_cum = upload(E, T.hb_cum);
+
+    // ---- device buffers
+    const int64_t cap = P.cap, scap = P.scap;
+    for (int b = 0; b < 2; ++b) {
+      P.key[b] = dalloc<uint64_t>(E, (size_t)cap * E.W);
+      P.pop[b] = dalloc<int64_t>(E, cap);
+      P.hdiag[b] = dalloc<double>(E, cap);
+      P.flags[b] = dalloc<uint8_t>(E, cap);
+    }
+    P.natt = dalloc<int64_t>(E, cap);
+    P.att_begin = dalloc<int64_t>(E, cap);
+    P.part = dalloc<int64_t>(E, kScanBlocks + 1);
+    P.s_key = dalloc<uint64_t>(E, (size_t)scap * E.W);
+    P.s_amt = dalloc<int64_t>(E, scap);
+    P.s_meta = dalloc<uint64_t>(E, scap);
+    P.b_key = dalloc<uint64_t>(E, (size_t)scap * E.W);
+    P.b_amt = dalloc<int64_t>(E, scap);
+    P.b_flag = dalloc<uint8_t>(E, scap);
+    P.bcount = dalloc<uint32_t>(E, cap);
+    P.boff = dalloc<uint32_t>(E, cap);
+    P.tile_state = dalloc<unsigned long long>(E, cap);
+    P.split_key = dalloc<uint64_t>(E, (size_t)cap * E.W);
+    P.st = dalloc<DevState>(E, 1);
+    P.rec = dalloc<Record>(E, P.rec_cap);
+    P.ncore = 0;
+
+    // ---- launch geometry
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    E.merge_smem_bytes = E.ops.merge_smem(P.tile_cap, P.seg_max);
+    CK(cudaFuncSetAttribute(E.ops.merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)E.merge_smem_bytes));
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, E.ops.merge_kernel, 512, E.merge_smem_bytes));
+    if (per_sm < 1) throw Fail{HANDE_ERR_CUDA, "annihilation kernel does not fit on an SM"};
+    E.merge_grid = per_sm * nsm;
+    E.attempt_grid = 8 * nsm;
+
+    // ---- initial state: init_pop walkers on the reference
+    DevState hs;
+    std::memset(&hs, 0, sizeof hs);
+    hs.ndet[0] = 1;
+    CK(cudaMemcpyAsync(P.st, &hs, sizeof hs, cudaMemcpyHostToDevice, E.stream));
+    E.ops.eref(E, E.stream);
+    for (int j = 0; j < E.W; ++j)
+      CK(cudaMemcpyAsync(P.key[0] + (size_t)j * cap, &P.d0[j], 8, cudaMemcpyHostToDevice, E.stream));
+    int64_t p0 = llrint(q.init_pop * 4294967296.0);
+    double h0 = 0.0;
+    uint8_t f0 = 0;
+    CK(cudaMemcpyAsync(P.pop[0], &p0, 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync(P.hdiag[0], &h0, 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync(P.flags[0], &f0, 1, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaGetLastError());
+    E.e_ref = 0.0;
+    CK(cudaMemcpyAsync(&E.e_ref, (char*)P.st + offsetof(DevState, e_ref), 8, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    E.cur = 0;
+    if (E.core_size > 0 && E.core_start == 0) select_core(E);
+    return HANDE_OK;
+  });
+  if (st != HANDE_OK) {
+    release_all(E);
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return HANDE_OK;
+}
+
+hande_status hande_iterate(hande_ctx* ctx, int n) {
+  if (!ctx || n < 0) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    for (int k = 0; k < n; ++k) {
+      int core = E.core_active ? 1 : 0;
+      ensure_graph(E, E.cur, core);
+      CK(cudaGraphLaunch(E.graph[E.cur][core], E.stream));
+      E.cur ^= 1;
+      E.host_iter += 1;
+      if (E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start) {
+        hande_status es = map_error(E, read_error(E));
+        if (es != HANDE_OK) return es;
+        select_core(E);
+      }
+    }
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_synchronize(hande_ctx* ctx) {
+  if (!ctx) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status { return map_error(E, read_error(E)); });
+}
+
+hande_status hande_estimators(hande_ctx* ctx, hande_estimate* out, int max, int* n_out) {
+  if (!ctx || (max > 0 && !out)) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (n_out) *n_out = 0;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    hande_status es = map_error(E, read_error(E));
+    if (es != HANDE_OK) return es;
+    bool lost = false;
+    if (E.host_iter - E.fetched > E.P.rec_cap) {
+      E.fetched = E.host_iter - E.P.rec_cap;
+      lost = true;
+    }
+    int64_t avail = E.host_iter - E.fetched;
+    int64_t m = std::min<int64_t>(avail, max);
+    std::vector<Record> tmp((size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+      int64_t slot = (E.fetched + i) % E.P.rec_cap;
+      CK(cudaMemcpyAsync(&tmp[(size_t)i], E.P.rec + slot, sizeof(Record), cudaMemcpyDeviceToHost, E.stream));
+    }
+    CK(cudaStreamSynchronize(E.stream));
+    for (int64_t i = 0; i < m; ++i) {
+      const Record& r = tmp[(size_t)i];
+      hande_estimate& o = out[i];
+      o.iter = r.iter;
+      o.shift = r.shift;
+      o.nw_pre = r.nw_pre;
+      o.n0 = r.n0;
+      o.num_hi = r.num_hi;
+      o.num_lo = r.num_lo;
+      o.num = r.num;
+      o.nw_post = r.nw_post;
+      o.ndet = r.ndet;
+      o.natt = r.natt;
+      o.nspawn = r.nspawn;
+    }
+    E.fetched += m;
+    if (n_out) *n_out = (int)m;
+    if (lost) {
+      E.err = "estimator records were overwritten before being fetched";
+      return HANDE_ERR_CAPACITY;
+    }
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, double* hdiag, uint8_t* flags,
+                               int64_t cap, int64_t* n) {
+  if (!ctx || !n) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    hande_status es = map_error(E, read_error(E));
+    if (es != HANDE_OK) return es;
+    const int cur = E.cur;
+    int64_t nd = read_i64(E, offsetof(DevState, ndet) + 8 * cur);
+    *n = nd;
+    if (nd > cap) return HANDE_ERR_CAPACITY;
+    if (nd == 0) return HANDE_OK;
+    if (!keys || !pops) return HANDE_ERR_INVALID;
+    const int W = E.W;
+    std::vector<uint64_t> soa((size_t)nd * W);
+    for (int j = 0; j < W; ++j)
+      CK(cudaMemcpyAsync(soa.data() + (size_t)j * nd, E.P.key[cur] + (size_t)j * E.P.cap, nd * 8,
+                         cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaMemcpyAsync(pops, E.P.pop[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
+    if (hdiag) CK(cudaMemcpyAsync(hdiag, E.P.hdiag[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
+    if (flags) CK(cudaMemcpyAsync(flags, E.P.flags[cur], nd, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    for (int64_t i = 0; i < nd; ++i)
+      for (int j = 0; j < W; ++j) keys[i * W + j] = soa[(size_t)j * nd + i];
+    if (flags)
+      for (int64_t i = 0; i < nd; ++i) flags[i] &= F_CORE;
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
+                               int64_t n) {
+  if (!ctx || n < 1 || !keys || !pops) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    const int W = E.W;
+    if (n > E.P.cap) throw Fail{HANDE_ERR_CAPACITY, "more walkers than state_capacity"};
+    bool has_ref = false;
+    const int nspin = E.P.sys.nspin;
+    for (int64_t i = 0; i < n; ++i) {
+      int na = 0, nb = 0;
+      for (int j = 0; j < W; ++j) {
+        uint64_t w = keys[i * W + j];
+        int lo = 64 * j;
+        if (nspin - lo < 64 && (nspin - lo <= 0 ? w != 0 : (w >> (nspin - lo)) != 0))
+          throw Fail{HANDE_ERR_INVALID, "a key has bits beyond the spin orbitals"};
+        na += __builtin_popcountll(w & 0x5555555555555555ull);
+        nb += __builtin_popcountll(w & 0xAAAAAAAAAAAAAAAAull);
+      }
+      if (na != E.nalpha || nb != E.nbeta) throw Fail{HANDE_ERR_INVALID, "a key has the wrong electron numbers"};
+      bool eq = true;
+      for (int j = 0; j < W; ++j) eq &= keys[i * W + j] == E.P.d0[j];
+      has_ref |= eq;
+      if (i > 0) {
+        int c = 0;
+        for (int j = W - 1; j >= 0 && c == 0; --j) {
+          uint64_t a = keys[(i - 1) * W + j], b = keys[i * W + j];
+          c = a < b ? -1 : (a > b ? 1 : 0);
+        }
+        if (c >= 0) throw Fail{HANDE_ERR_INVALID, "keys must be strictly ascending"};
+      }
+    }
+    if (!has_ref) throw Fail{HANDE_ERR_INVALID, "the reference determinant must be in the list"};
+    const int cur = E.cur;
+    std::vector<uint64_t> soa((size_t)n * W);
+    for (int64_t i = 0; i < n; ++i)
+      for (int j = 0; j < W; ++j) soa[(size_t)j * n + i] = keys[i * W + j];
+    for (int j = 0; j < W; ++j)
+      CK(cudaMemcpyAsync(E.P.key[cur] + (size_t)j * E.P.cap, soa.data() + (size_t)j * n, n * 8,
+                         cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync(E.P.pop[cur], pops, n * 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemsetAsync(E.P.flags[cur], 0, n, E.stream));
+    CK(cudaMemcpyAsync((char*)E.P.st + offsetof(DevState, ndet) + 8 * cur, &n, 8, cudaMemcpyHostToDevice, E.stream));
+    if (hdiag) CK(cudaMemcpyAsync(E.P.hdiag[cur], hdiag, n * 8, cudaMemcpyHostToDevice, E.stream));
+    else E.ops.hdiag(E, cur, n, E.stream);
+    CK(cudaGetLastError());
+    // the deterministic space refers to the old list
+    E.core_active = false;
+    E.P.ncore = 0;
+    drop_graphs(E, 1);
+    if (E.core_size > 0 && E.core_start == 0) select_core(E);
+    CK(cudaStreamSynchronize(E.stream));
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_reference(hande_ctx* ctx, double* e_ref, uint64_t* key) {
+  if (!ctx) return HANDE_ERR_INVALID;
+  if (e_ref) *e_ref = ctx->E.e_ref;
+  if (key)
+    for (int j = 0; j < ctx->E.W; ++j) key[j] = ctx->E.P.d0[j];
+  return HANDE_OK;
+}
+
+int64_t hande_iterations(const hande_ctx* ctx) { return ctx ? ctx->E.host_iter : 0; }
+
+void hande_destroy(hande_ctx* ctx) {
+  if (!ctx) return;
+  release_all(ctx->E);
+  delete ctx;
+}
+
+const char* hande_last_error(const hande_ctx* ctx) {
+  if (!ctx) return "no context";
+  return ctx->E.err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,981 @@
+// kernels.cuh -- one FCIQMC iteration as a fixed sequence of kernels
+// (HANDE-QMC paper, Sec. 2.1 Eq. (fciqmc) and Sec. 2.4; annihilation as in App. B:
+// sort the spawned array and merge it into the sorted main list).
+//
+//   det_pass      per determinant: projected-energy terms (App. A.1), initiator
+//                 flag (Sec. 2.1), spawning-attempt count, death/cloning
+//   scan          exclusive scan of attempt counts (attempt space)
+//   split         bucket geometry + splitter keys taken from the sorted main list
+//   core_*        semi-stochastic exact projection inside the deterministic space
+//   attempt       per attempt: Philox draw, excitation, H_ij, spawn amount, bucket id
+//   scan          exclusive scan of bucket counts
+//   scatter       spawns -> bucket-contiguous layout (one read + one write)
+//   merge         per bucket: on-chip sort + reduce of its spawns, merge with the
+//                 bucket's main-list segment, initiator rule, real-weight rounding,
+//                 new diagonal elements, decoupled look-back compaction
+//   finalize      shift update (Sec. 2.1) and the per-iteration estimator record
+#pragma once
+#include "system.cuh"
+
+namespace hande {
+
+constexpr int kMaxW = 8;
+constexpr int kScanBlocks = 608;      // 4 x 152 SMs
+constexpr int kScanThreads = 256;
+
+// flags byte of a main-list entry
+enum : uint8_t { F_CORE = 1, F_INIT = 2, F_NEG = 4, F_REF = 8 };
+
+struct Record {
+  int64_t iter;
+  double shift;
+  int64_t nw_pre, n0, nw_post, ndet, natt, nspawn;
+  int64_t num_hi;
+  uint64_t num_lo;
+  double num;
+};
+
+struct DevState {
+  int64_t iter;
+  int64_t ndet[2];
+  int64_t natt;
+  int64_t nspawn;
+  int64_t nbuckets;
+  int64_t sb;
+  int64_t nw_pre;
+  int64_t n0;
+  unsigned long long num[2];   // int128 lo, hi
+  int64_t nw_post;
+  double shift;
+  int64_t nw_ref;
+  double e_ref;
+  int vary;
+  int64_t scan_total;
+  unsigned error;
+  unsigned merge_ticket;
+};
+
+struct Params {
+  // run
+  double tau, cutoff, zeta;
+  int real_amp, initiator, period, W;
+  int64_t init_thr, target_fixed;
+  uint64_t seed, replica;
+  uint64_t d0[kMaxW];
+  // capacities
+  int64_t cap, scap;
+  int tile_cap, seg_max, rec_cap;
+  // main list (two buffers)
+  uint64_t* key[2];
+  int64_t* pop[2];
+  double* hdiag[2];
+  uint8_t* flags[2];
+  // attempt space
+  int64_t* natt;
+  int64_t* att_begin;
+  int64_t* part;         // scan partials, kScanBlocks + 1
+  // spawns
+  uint64_t* s_key;
+  int64_t* s_amt;
+  uint64_t* s_meta;
+  uint64_t* b_key;
+  int64_t* b_amt;
+  uint8_t* b_flag;
+  uint32_t* bcount;
+  uint32_t* boff;
+  unsigned long long* tile_state;
+  uint64_t* split_key;
+  // deterministic space
+  int ncore;
+  const uint64_t* core_key;
+  int64_t* core_pos;
+  const int64_t* core_rowptr;
+  const int32_t* core_col;
+  const double* core_val;
+  int64_t* core_delta;
+  // state
+  DevState* st;
+  Record* rec;
+  SysDev sys;
+};
+
+template <int W>
+__device__ __forceinline__ Key<W> ref_key(const Params& P) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = P.d0[j];
+  return k;
+}
+
+// ------------------------------------------------------------------ block helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T r = 0;
+  if (wid == 0) {
+    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;  // valid in thread 0
+}
+static __device__ I128 block_sum_i128(I128 v, I128* sh) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    I128 x = shfl_xor_i128(v, o);
+    i128_add(v, x);
+  }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  I128 r{0, 0};
+  if (wid == 0) {
+    if (lane < (int)(blockDim.x >> 5)) r = sh[lane];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      I128 x = shfl_xor_i128(r, o);
+      i128_add(r, x);
+    }
+  }
+  return r;
+}
+// exclusive scan over a shared array a[0..n) in place; returns the total (all threads)
+template <typename T>
+__device__ T block_scan_excl(T* a, int n, T* wsum) {
+  const int T_ = blockDim.x;
+  const int per = (n + T_ - 1) / T_;
+  const int beg = threadIdx.x * per;
+  const int end = min(beg + per, n);
+  T s = 0;
+  for (int i = beg; i < end; ++i) s += a[i];
+  // warp inclusive scan of s
+  T x = s;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  __syncthreads();
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = T_ >> 5;
+    T v = lane < nw ? wsum[lane] : T(0);
+    T inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < nw) wsum[lane] = inc - v;  // exclusive warp offsets
+    if (lane == nw - 1) wsum[32] = inc;   // total
+  }
+  __syncthreads();
+  T run = wsum[wid] + x - s;
+  for (int i = beg; i < end; ++i) {
+    T v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  T total = wsum[32];
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ void set_error(DevState* st, unsigned bit) { atomicOr(&st->error, bit); }
+
+// chunk of a block-partitioned range [0, n)
+__device__ __forceinline__ void block_chunk(int64_t n, int64_t& beg, int64_t& end) {
+  int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  beg = (int64_t)blockIdx.x * per;
+  end = beg + per < n ? beg + per : n;
+  if (beg > n) beg = n;
+}
+
+// ------------------------------------------------------------------ det pass
+template <int W, int SYS>
+__global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  __shared__ int64_t sh64[32];
+  __shared__ I128 sh128[32];
+  const int64_t n = st->ndet[cur];
+  const int64_t t = st->iter + 1;
+  const double S = st->shift;
+  const Key<W> d0 = ref_key<W>(P);
+  int64_t beg, end;
+  block_chunk(n, beg, end);
+  uint64_t* key = P.key[cur];
+  int64_t* pop = P.pop[cur];
+  const double* hd = P.hdiag[cur];
+  uint8_t* fl = P.flags[cur];
+  int64_t nw = 0, attsum = 0;
+  I128 num{0, 0};
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    Key<W> k = load_key<W>(key, P.cap, i);
+    int64_t p = pop[i];
+    uint8_t f = fl[i] & F_CORE;
+    bool core = f != 0;
+    bool is0 = key_eq<W>(k, d0);
+    int64_t mag = iabs64(p);
+    nw += mag;
+    if (is0) {
+      st->n0 = p;
+    } else if (p != 0 && key_popc_xor<W>(k, d0) <= 4) {
+      double h0j = h_elem<W, SYS>(P.sys, k, d0);
+      i128_add(num, fixed_from_double(__dmul_rn((double)p, h0j)));
+    }
+    bool init = !P.initiator || mag > P.init_thr || is0 || core;
+    int64_t na = 0;
+    int64_t np = p;
+    if (p != 0) {
+      Words4 w = draw<W>(P.seed, P.replica, t, kDetDraw, k);
+      na = (int64_t)((uint64_t)mag >> 32);
+      if (P.real_amp && (w.x >> 32) < ((uint64_t)mag & 0xffffffffull)) na += 1;
+      if (!core) {
+        double d = __dmul_rn(P.tau, __dsub_rn(__ldg(&hd[i]), S));
+        if (P.real_amp) {
+          np = p - __double2ll_rn(__dmul_rn(d, (double)p));
+        } else {
+          int64_t nwk = mag >> 32;
+          double x = __dmul_rn(fabs(d), (double)nwk);
+          double flo = floor(x);
+          int64_t kk = (int64_t)flo;
+          if (draw_unit(w.y) < __dsub_rn(x, flo)) kk += 1;
+          int64_t nn = d > 0.0 ? nwk - kk : nwk + kk;
+          np = (p < 0 ? -nn : nn) * kOne;
+        }
+        if (iabs64(np) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+        if (np != p) pop[i] = np;
+      }
+    }
+    fl[i] = f | (init ? F_INIT : 0) | (p < 0 ? F_NEG : 0) | (is0 ? F_REF : 0);
+    P.natt[i] = na;
+    attsum += na;
+  }
+  int64_t a = block_sum<int64_t>(attsum, sh64);
+  if (threadIdx.x == 0) P.part[blockIdx.x] = a;
+  int64_t b = block_sum<int64_t>(nw, sh64);
+  if (threadIdx.x == 0 && b) atomicAdd((unsigned long long*)&st->nw_pre, (unsigned long long)b);
+  I128 c = block_sum_i128(num, sh128);
+  if (threadIdx.x == 0 && (c.lo | (uint64_t)c.hi)) atomic_add_i128(st->num, c);
+}
+
+// ------------------------------------------------------------------ generic scans
+// partials scanned by one block; total written to *total
+static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* total, DevState* st) {
+  if (st->error) return;
+  __shared__ int64_t buf[kScanBlocks];
+  __shared__ int64_t wsum[33];
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) buf[i] = part[i];
+  __syncthreads();
+  int64_t tot = block_scan_excl<int64_t>(buf, nparts, wsum);
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) part[i] = buf[i];
+  if (threadIdx.x == 0) *total = tot;
+}
+// out[i] = exclusive prefix of in over the block's chunk + part[block]
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,
+                                                             const int64_t* part, DevState* st) {
+  if (st->error) return;
+  __shared__ T tile[kScanThreads];
+  __shared__ T wsum[33];
+  int64_t beg, end;
+  block_chunk(*n_ptr, beg, end);
+  T carry = (T)part[blockIdx.x];
+  for (int64_t base = beg; base < end; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    tile[threadIdx.x] = i < end ? in[i] : T(0);
+    __syncthreads();
+    T tot = block_scan_excl<T>(tile, blockDim.x, wsum);
+    if (i < end) out[i] = carry + tile[threadIdx.x];
+    carry += tot;
+    __syncthreads();
+  }
+}
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const int64_t* n_ptr, int64_t* part,
+                                                              DevState* st) {
+  if (st->error) return;
+  __shared__ int64_t sh[32];
+  int64_t beg, end;
+  block_chunk(*n_ptr, beg, end);
+  int64_t s = 0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += (int64_t)in[i];
+  s = block_sum<int64_t>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ buckets
+// Bucket b holds the main-list segment [b*sb, (b+1)*sb) and every spawn whose key
+// lies in [key[b*sb], key[(b+1)*sb]); sb is chosen so a bucket expects at most
+// a quarter tile of spawns.
+template <int W>
+__global__ void k_split(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  const int64_t n = st->ndet[cur];
+  const int64_t na = st->natt;
+  int64_t sb = (int64_t)P.seg_max;
+  int64_t half = P.tile_cap / 4;   // expected spawns per bucket: a quarter tile
+  if (na > 0) {
+    int64_t want = (int64_t)(((double)half * (double)n) / (double)na);
+    if (want < sb) sb = want;
+  }
+  if (sb < 1) sb = 1;
+  int64_t nb = (n + sb - 1) / sb;
+  if (nb < 1) nb = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->nbuckets = nb;
+    st->sb = sb;
+    st->nspawn = 0;
+    st->merge_ticket = 0;
+    if (nb > P.cap) set_error(st, ERR_BUCKET_CAPACITY);
+  }
+  if (nb > P.cap) return;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+    P.bcount[b] = 0;
+    P.tile_state[b] = 0ull;
+    int64_t src = b * sb;
+#pragma unroll
+    for (int j = 0; j < W; ++j) P.split_key[j * P.cap + b] = src < n ? P.key[cur][j * P.cap + src] : 0ull;
+  }
+}
+
+// ------------------------------------------------------------------ deterministic space
+template <int W>
+__device__ __forceinline__ int64_t lower_bound_main(const uint64_t* key, int64_t stride, int64_t n, const Key<W>& k) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    Key<W> m = load_key<W>(key, stride, mid);
+    if (key_lt<W>(m, k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+template <int W>
+__device__ __forceinline__ bool in_core(const Params& P, const Key<W>& k) {
+  int lo = 0, hi = P.ncore;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    Key<W> m = load_key<W>(P.core_key, P.ncore, mid);
+    if (key_lt<W>(m, k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo < P.ncore && key_eq<W>(load_key<W>(P.core_key, P.ncore, lo), k);
+}
+template <int W>
+__global__ void k_core_locate(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.ncore) return;
+  Key<W> k = load_key<W>(P.core_key, P.ncore, r);
+  const int64_t n = st->ndet[cur];
+  int64_t pos = lower_bound_main<W>(P.key[cur], P.cap, n, k);
+  if (pos >= n || !key_eq<W>(load_key<W>(P.key[cur], P.cap, pos), k)) {
+    set_error(st, ERR_STATE_CAPACITY);   // a deterministic-space determinant left the list
+    pos = 0;
+  }
+  P.core_pos[r] = pos;
+}
+// one warp per core row: y_r = sum_c H'_rc N_c exactly, dN_r = -rint(tau (y_r - S N_r))
+static __global__ void k_core_spmv(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= P.ncore) return;
+  const int64_t* pop = P.pop[cur];
+  I128 acc{0, 0};
+  for (int64_t e = P.core_rowptr[r] + lane; e < P.core_rowptr[r + 1]; e += 32) {
+    int64_t pc = pop[P.core_pos[P.core_col[e]]];
+    i128_add(acc, fixed_from_double(__dmul_rn((double)pc, P.core_val[e])));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    I128 x = shfl_xor_i128(acc, o);
+    i128_add(acc, x);
+  }
+  if (lane == 0) {
+    double y = fixed_to_double(acc);
+    int64_t pr = pop[P.core_pos[r]];
+    double v = __dsub_rn(y, __dmul_rn(st->shift, (double)pr));
+    double x = __dmul_rn(P.tau, v);
+    P.core_delta[r] = -__double2ll_rn(x);
+  }
+}
+static __global__ void k_core_apply(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.ncore) return;
+  P.pop[cur][P.core_pos[r]] += P.core_delta[r];
+}
+
+// ------------------------------------------------------------------ attempts
+template <int W, int SYS>
+__global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  const int64_t natt = st->natt;
+  const int64_t n = st->ndet[cur];
+  const int64_t nb = st->nbuckets;
+  const int64_t t = st->iter + 1;
+  const uint64_t* key = P.key[cur];
+  const uint8_t* fl = P.flags[cur];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < natt; g0 += stride) {
+    int64_t g = g0 + threadIdx.x;
+    bool have = false;
+    Key<W> child;
+    int64_t amt = 0;
+    uint32_t bkt = 0;
+    uint8_t initf = 0;
+    if (g < natt) {
+      // parent: last i with att_begin[i] <= g
+      int64_t lo = 0, hi = n - 1;
+      while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (P.att_begin[mid] <= g) lo = mid;
+        else hi = mid - 1;
+      }
+      const int64_t i = lo;
+      const uint64_t a = (uint64_t)(g - P.att_begin[i]);
+      Key<W> k = load_key<W>(key, P.cap, i);
+      const uint8_t f = fl[i];
+      Words4 w = draw<W>(P.seed, P.replica, t, a, k);
+      Excitation<W> ex = generate<W, SYS>(P.sys, k, w);
+      if (ex.ok && ex.hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
+        double m = __ddiv_rn(__dmul_rn(P.tau, fabs(ex.hij)), ex.pgen);
+        int64_t q = 0;
+        if (!P.real_amp) {
+          double flo = floor(m);
+          double kk = flo;
+          if (draw_unit(w.w) < __dsub_rn(m, flo)) kk = __dadd_rn(kk, 1.0);
+          if (kk != 0.0) q = (int64_t)kk * kOne;
+        } else {
+          bool keep = true;
+          if (m < P.cutoff) {
+            if (draw_unit(w.w) < __ddiv_rn(m, P.cutoff)) m = P.cutoff;
+            else keep = false;
+          }
+          if (keep) q = __double2ll_rn(__dmul_rn(m, 4294967296.0));
+        }
+        if (q != 0) {
+          int hs = ex.hij < 0.0 ? -1 : 1;
+          int ps = (f & F_NEG) ? -1 : 1;
+          amt = (-hs * ps) < 0 ? -q : q;
+          child = ex.child;
+          initf = (f & F_INIT) ? 1 : 0;
+          // bucket = number of splitters s_j (j >= 1) with s_j <= child
+          int64_t blo = 1, bhi = nb;
+          while (blo < bhi) {
+            int64_t mid = (blo + bhi) >> 1;
+            Key<W> sk = load_key<W>(P.split_key, P.cap, mid);
+            if (key_le<W>(sk, child)) blo = mid + 1;
+            else bhi = mid;
+          }
+          bkt = (uint32_t)(blo - 1);
+          have = true;
+        }
+      }
+    }
+    // warp-aggregated slot allocation
+    unsigned act = __activemask();
+    unsigned want = __ballot_sync(act, have);
+    int64_t base = 0;
+    int leader = want ? __ffs(want) - 1 : 0;
+    if (want && (int)warp_lane() == leader)
+      base = (int64_t)atomicAdd((unsigned long long*)&st->nspawn, (unsigned long long)__popc(want));
+    base = __shfl_sync(act, base, leader);
+    if (have) {
+      int64_t slot = base + __popc(want & ((1u << warp_lane()) - 1u));
+      uint32_t rank = atomicAdd(&P.bcount[bkt], 1u);
+      if (slot < P.scap) {
+        store_key<W>(P.s_key, P.scap, slot, child);
+        P.s_amt[slot] = amt;
+        P.s_meta[slot] = ((uint64_t)bkt << 32) | ((uint64_t)rank << 1) | initf;
+      } else {
+        set_error(st, ERR_SPAWN_CAPACITY);
+      }
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_scatter(Params P) {
+  DevState* st = P.st;
+  if (st->error) return;
+  const int64_t ns = st->nspawn < P.scap ? st->nspawn : P.scap;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t m = P.s_meta[s];
+    uint32_t b = (uint32_t)(m >> 32);
+    uint32_t rank = (uint32_t)(m & 0xffffffffu) >> 1;
+    int64_t dst = (int64_t)P.boff[b] + rank;
+    Key<W> k = load_key<W>(P.s_key, P.scap, s);
+    store_key<W>(P.b_key, P.scap, dst, k);
+    P.b_amt[dst] = P.s_amt[s];
+    P.b_flag[dst] = (uint8_t)(m & 1u);
+  }
+}
+
+// ------------------------------------------------------------------ merge (annihilation)
+template <int W>
+struct MergeSmem {
+  // tile arrays are carved from dynamic shared memory
+  uint64_t* skey;    // [W][TC]
+  int64_t* samt;     // [TC]
+  uint32_t* sflg;    // [TC]   bit0 initiator parent, bit31 padding
+  int32_t* uid;      // [TC]
+  int64_t* uamt;     // [TC]
+  uint32_t* uflg;    // [TC]
+  uint64_t* mkey;    // [W][SM]
+  int32_t* mmatch;   // [SM]   unique index matching main entry, or -1
+  int32_t* mlb;      // [SM]   number of unique keys below main key
+  int32_t* ulb;      // [TC]   number of main keys below unique key (or -1 if matched)
+  uint32_t* mscan;   // [TC+1] exclusive prefix of matched flags over unique list
+  uint32_t* keep;    // [TC+SM] keep flag by merged rank, scanned in place
+};
+
+template <int W>
+__host__ __device__ inline size_t merge_smem_bytes(int TC, int SM) {
+  return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4) +
+         (size_t)(TC + SM) * 4 + 512;
+}
+
+template <int W>
+__device__ __forceinline__ Key<W> skey_at(const MergeSmem<W>& m, int TC, int i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = m.skey[j * TC + i];
+  return k;
+}
+template <int W>
+__device__ __forceinline__ Key<W> mkey_at(const MergeSmem<W>& m, int SM, int i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = m.mkey[j * SM + i];
+  return k;
+}
+template <int W>
+__device__ __forceinline__ bool rec_lt(const MergeSmem<W>& m, int TC, int a, int b) {
+  bool pa = m.sflg[a] >> 31, pb = m.sflg[b] >> 31;
+  if (pa != pb) return pb;
+  if (pa) return false;
+  return key_lt<W>(skey_at<W>(m, TC, a), skey_at<W>(m, TC, b));
+}
+template <int W>
+__device__ __forceinline__ void rec_swap(MergeSmem<W>& m, int TC, int a, int b) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    uint64_t x = m.skey[j * TC + a];
+    m.skey[j * TC + a] = m.skey[j * TC + b];
+    m.skey[j * TC + b] = x;
+  }
+  int64_t y = m.samt[a];
+  m.samt[a] = m.samt[b];
+  m.samt[b] = y;
+  uint32_t z = m.sflg[a];
+  m.sflg[a] = m.sflg[b];
+  m.sflg[b] = z;
+}
+
+// sort records [0, n) in place (padding to a power of two), then combine equal
+// keys: on return records [0, u) are the sorted unique keys with summed amounts
+// and OR-ed initiator bits.  Returns u.
+template <int W>
+__device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
+  int n2 = 1;
+  while (n2 < n) n2 <<= 1;
+  for (int i = n + threadIdx.x; i < n2; i += blockDim.x) m.sflg[i] = 0x80000000u;
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          bool sw = up ? rec_lt<W>(m, TC, l, i) : rec_lt<W>(m, TC, i, l);
+          if (sw) rec_swap<W>(m, TC, i, l);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // heads and unique ids
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    bool head = (i == 0) || !key_eq<W>(skey_at<W>(m, TC, i), skey_at<W>(m, TC, i - 1));
+    m.uid[i] = head ? 1 : 0;
+    m.uamt[i] = 0;
+    m.uflg[i] = 0;
+  }
+  __syncthreads();
+  // inclusive scan of heads -> unique id + 1
+  uint32_t* u32 = reinterpret_cast<uint32_t*>(m.uid);
+  uint32_t total = block_scan_excl<uint32_t>(u32, n, wsum);
+  // u32 now holds exclusive prefix; unique id of element i = prefix + head - 1
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    bool head = (i == 0) || !key_eq<W>(skey_at<W>(m, TC, i), skey_at<W>(m, TC, i - 1));
+    int id = (int)u32[i] + (head ? 1 : 0) - 1;
+    atomicAdd((unsigned long long*)&m.uamt[id], (unsigned long long)m.samt[i]);
+    if (m.sflg[i] & 1u) atomicOr(&m.uflg[id], 1u);
+    m.uid[i] = head ? id : -1;
+  }
+  __syncthreads();
+  // compact heads forward in rounds (a head at i moves to id <= i)
+  for (int base = 0; base < n; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int id = -1;
+    Key<W> k;
+    if (i < n) {
+      id = m.uid[i];
+      if (id >= 0) k = skey_at<W>(m, TC, i);
+    }
+    __syncthreads();
+    if (id >= 0) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) m.skey[j * TC + id] = k.w[j];
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < (int)total; i += blockDim.x) {
+    m.samt[i] = m.uamt[i];
+    m.sflg[i] = m.uflg[i];
+  }
+  __syncthreads();
+  return (int)total;
+}
+
+template <int W>
+__device__ __forceinline__ int lb_smem_main(const MergeSmem<W>& m, int SM, int nm, const Key<W>& k) {
+  int lo = 0, hi = nm;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (key_lt<W>(mkey_at<W>(m, SM, mid), k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+template <int W>
+__device__ __forceinline__ int lb_smem_uniq(const MergeSmem<W>& m, int TC, int nu, const Key<W>& k) {
+  int lo = 0, hi = nu;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (key_lt<W>(skey_at<W>(m, TC, mid), k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The decision for one merged candidate.  Main entries keep their list slot if
+// core or reference, otherwise they survive with a nonzero population after the
+// real-weight occupation rounding.  New determinants need an initiator parent
+// (Sec. 2.1) and a nonzero amount.
+template <int W>
+__device__ __forceinline__ int64_t round_small(const Params& P, int64_t t, const Key<W>& k, int64_t p) {
+  int64_t mag = iabs64(p);
+  if (P.real_amp && mag > 0 && mag < kOne) {
+    Words4 w = draw<W>(P.seed, P.replica, t, kDetDraw, k);
+    int64_t r = ((w.z >> 32) < (uint64_t)mag) ? kOne : 0;
+    return p < 0 ? -r : r;
+  }
+  return p;
+}
+
+template <int W, int SYS>
+__global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
+  DevState* st = P.st;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t wsum[33];
+  __shared__ int64_t sh64[32];
+  __shared__ int tile_id;
+  __shared__ unsigned long long s_base;
+  __shared__ int s_abort;
+  const int TC = P.tile_cap, SM = P.seg_max;
+  MergeSmem<W> m;
+  {
+    unsigned char* p = smem_raw;
+    auto carve = [&](size_t bytes) {
+      unsigned char* r = p;
+      p += (bytes + 15) & ~size_t(15);
+      return r;
+    };
+    m.skey = (uint64_t*)carve(sizeof(uint64_t) * W * TC);
+    m.samt = (int64_t*)carve(sizeof(int64_t) * TC);
+    m.uamt = (int64_t*)carve(sizeof(int64_t) * TC);
+    m.mkey = (uint64_t*)carve(sizeof(uint64_t) * W * SM);
+    m.sflg = (uint32_t*)carve(4 * TC);
+    m.uid = (int32_t*)carve(4 * TC);
+    m.uflg = (uint32_t*)carve(4 * TC);
+    m.ulb = (int32_t*)carve(4 * TC);
+    m.mscan = (uint32_t*)carve(4 * (TC + 1));
+    m.mmatch = (int32_t*)carve(4 * SM);
+    m.mlb = (int32_t*)carve(4 * SM);
+    m.keep = (uint32_t*)carve(4 * (TC + SM));
+  }
+  const int64_t n = st->ndet[cur];
+  const int64_t nb = st->nbuckets;
+  const int64_t sb = st->sb;
+  const int64_t t = st->iter + 1;
+  const int nxt = cur ^ 1;
+  const uint64_t* key = P.key[cur];
+  const int64_t* pop = P.pop[cur];
+  const double* hd = P.hdiag[cur];
+  const uint8_t* fl = P.flags[cur];
+  int64_t nwsum = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      tile_id = st->error ? -1 : (int)atomicAdd(&st->merge_ticket, 1u);
+      s_abort = 0;
+    }
+    __syncthreads();
+    const int64_t b = tile_id;
+    if (b < 0 || b >= nb) break;
+    const int64_t s0 = P.boff[b];
+    const int64_t ns = P.bcount[b];
+    const int64_t m0 = b * sb;
+    const int nm = (int)((m0 + sb < n ? m0 + sb : n) - m0);
+    // ---- spawns of this bucket: chunked sort + reduce (duplicates collapse)
+    int nu = 0;
+    for (int64_t pos = 0; pos < ns;) {
+      int take = TC - nu;
+      if (take <= 0) {
+        if (threadIdx.x == 0) {
+          set_error(st, ERR_TILE_CAPACITY);
+          s_abort = 1;
+        }
+        break;
+      }
+      if ((int64_t)take > ns - pos) take = (int)(ns - pos);
+      for (int i = threadIdx.x; i < take; i += blockDim.x) {
+        int64_t src = s0 + pos + i;
+#pragma unroll
+        for (int j = 0; j < W; ++j) m.skey[j * TC + nu + i] = P.b_key[j * P.scap + src];
+        m.samt[nu + i] = P.b_amt[src];
+        m.sflg[nu + i] = P.b_flag[src];
+      }
+      __syncthreads();
+      nu = sort_reduce<W>(m, TC, nu + take, wsum);
+      pos += take;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // ---- main segment keys
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) m.mkey[j * SM + i] = key[j * P.cap + m0 + i];
+    }
+    __syncthreads();
+    // ---- match unique spawns against the segment
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+      Key<W> k = skey_at<W>(m, TC, j);
+      int lb = lb_smem_main<W>(m, SM, nm, k);
+      bool match = lb < nm && key_eq<W>(mkey_at<W>(m, SM, lb), k);
+      m.ulb[j] = match ? -1 : lb;
+      m.mscan[j] = match ? 1u : 0u;
+    }
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+      Key<W> k = mkey_at<W>(m, SM, i);
+      int lb = lb_smem_uniq<W>(m, TC, nu, k);
+      m.mlb[i] = lb;
+      m.mmatch[i] = (lb < nu && key_eq<W>(skey_at<W>(m, TC, lb), k)) ? lb : -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) m.mscan[nu] = 0;
+    __syncthreads();
+    uint32_t nmatched = block_scan_excl<uint32_t>(m.mscan, nu + 1, wsum);
+    const int nc = nm + nu - (int)nmatched;
+    // ---- pass A: keep flags by merged rank
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+      int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
+      int64_t p = pop[m0 + i];
+      if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
+      uint8_t f = fl[m0 + i];
+      bool always = (f & (F_CORE | F_REF)) != 0;
+      if (!always) p = round_small<W>(P, t, mkey_at<W>(m, SM, i), p);
+      m.keep[rank] = (always || p != 0) ? 1u : 0u;
+    }
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+      int lb = m.ulb[j];
+      if (lb < 0) continue;
+      int rank = lb + (j - (int)m.mscan[j]);
+      int64_t p = m.samt[j];
+      bool ok = (!P.initiator || (m.sflg[j] & 1u)) && p != 0;
+      if (ok) p = round_small<W>(P, t, skey_at<W>(m, TC, j), p);
+      m.keep[rank] = (ok && p != 0) ? 1u : 0u;
+    }
+    __syncthreads();
+    uint32_t nkeep = block_scan_excl<uint32_t>(m.keep, nc, wsum);
+    // ---- decoupled look-back for the output offset of this bucket
+    if (threadIdx.x == 0) {
+      const unsigned long long AGG = 1ull << 62, INC = 2ull << 62, MASK = (1ull << 62) - 1;
+      unsigned long long excl = 0;
+      if (b == 0) {
+        atomicExch(&P.tile_state[0], INC | (unsigned long long)nkeep);
+      } else {
+        atomicExch(&P.tile_state[b], AGG | (unsigned long long)nkeep);
+        int64_t p = b - 1;
+        long long spins = 0;
+        while (p >= 0) {
+          unsigned long long v = atomicAdd(&P.tile_state[p], 0ull);
+          unsigned long long s = v & ~MASK;
+          if (s == 0) {
+            ++spins;
+            if (spins > (1ll << 22) || ((spins & 1023) == 0 && *(volatile unsigned*)&st->error)) {
+              set_error(st, ERR_TIMEOUT);
+              s_abort = 1;
+              break;
+            }
+            continue;
+          }
+          excl += v & MASK;
+          if (s == INC) break;
+          --p;
+        }
+        if (!s_abort) atomicExch(&P.tile_state[b], INC | (excl + nkeep));
+      }
+      s_base = excl;
+      if (b == nb - 1) st->ndet[nxt] = (int64_t)(excl + nkeep);
+      if ((int64_t)(excl + nkeep) > P.cap) {
+        set_error(st, ERR_STATE_CAPACITY);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const int64_t base = (int64_t)s_base;
+    uint64_t* okey = P.key[nxt];
+    int64_t* opop = P.pop[nxt];
+    double* ohd = P.hdiag[nxt];
+    uint8_t* ofl = P.flags[nxt];
+    // ---- pass B: write the surviving entries
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+      int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
+      uint32_t pos = m.keep[rank];
+      uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+      if (nx == pos) continue;
+      int64_t p = pop[m0 + i];
+      if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
+      uint8_t f = fl[m0 + i];
+      Key<W> k = mkey_at<W>(m, SM, i);
+      bool always = (f & (F_CORE | F_REF)) != 0;
+      if (!always) p = round_small<W>(P, t, k, p);
+      if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+      int64_t o = base + pos;
+      store_key<W>(okey, P.cap, o, k);
+      opop[o] = p;
+      ohd[o] = hd[m0 + i];
+      ofl[o] = f & F_CORE;
+      nwsum += iabs64(p);
+    }
+    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+      int lb = m.ulb[j];
+      if (lb < 0) continue;
+      int rank = lb + (j - (int)m.mscan[j]);
+      uint32_t pos = m.keep[rank];
+      uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+      if (nx == pos) continue;
+      Key<W> k = skey_at<W>(m, TC, j);
+      int64_t p = round_small<W>(P, t, k, m.samt[j]);
+      if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+      int64_t o = base + pos;
+      store_key<W>(okey, P.cap, o, k);
+      opop[o] = p;
+      ohd[o] = __dsub_rn(h_diag<W, SYS>(P.sys, k), st->e_ref);
+      ofl[o] = 0;
+      nwsum += iabs64(p);
+    }
+    __syncthreads();
+  }
+  int64_t tot = block_sum<int64_t>(nwsum, sh64);
+  if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)tot);
+}
+
+// ------------------------------------------------------------------ finalize
+static __global__ void k_finalize(Params P, int cur) {
+  DevState* st = P.st;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (st->error) return;
+  const int64_t t = st->iter + 1;
+  const int64_t nw = st->nw_post;
+  if (st->vary) {
+    if (t % P.period == 0) {
+      double ratio = __ddiv_rn((double)nw, (double)st->nw_ref);
+      double coef = __ddiv_rn(P.zeta, __dmul_rn((double)P.period, P.tau));
+      st->shift = __dsub_rn(st->shift, __dmul_rn(coef, log_series(ratio)));
+      st->nw_ref = nw;
+    }
+  } else if (nw > P.target_fixed) {
+    st->vary = 1;
+    st->nw_ref = nw;
+  }
+  Record r;
+  r.iter = t;
+  r.shift = st->shift;
+  r.nw_pre = st->nw_pre;
+  r.n0 = st->n0;
+  r.nw_post = nw;
+  r.ndet = st->ndet[cur ^ 1];
+  r.natt = st->natt;
+  r.nspawn = st->nspawn;
+  I128 num{(uint64_t)st->num[0], (int64_t)st->num[1]};
+  r.num_lo = num.lo;
+  r.num_hi = num.hi;
+  r.num = fixed_to_double(num);
+  P.rec[(t - 1) % P.rec_cap] = r;
+  st->iter = t;
+  st->nw_pre = 0;
+  st->n0 = 0;
+  st->num[0] = 0;
+  st->num[1] = 0;
+  st->nw_post = 0;
+}
+
+// ------------------------------------------------------------------ utilities
+inline int64_t* st_field_i64(DevState* st, size_t off) { return (int64_t*)((char*)st + off); }
+
+// single-block exclusive scan of int32 counts into int64 offsets (n+1 entries)
+static __global__ void k_scan_small(const int32_t* in, int64_t* out, int n) {
+  __shared__ int64_t tile[1024];
+  __shared__ int64_t wsum[33];
+  int64_t carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    tile[threadIdx.x] = i < n ? in[i] : 0;
+    __syncthreads();
+    int64_t tot = block_scan_excl<int64_t>(tile, blockDim.x, wsum);
+    if (i < n) out[i] = carry + tile[threadIdx.x];
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+
+template <int W, int SYS>
+__global__ void k_hdiag(Params P, int cur, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Key<W> k = load_key<W>(P.key[cur], P.cap, i);
+    P.hdiag[cur][i] = __dsub_rn(h_diag<W, SYS>(P.sys, k), P.st->e_ref);
+  }
+}
+template <int W, int SYS>
+__global__ void k_eref(Params P) {
+  if (threadIdx.x || blockIdx.x) return;
+  P.st->e_ref = h_diag<W, SYS>(P.sys, ref_key<W>(P));
+}
+
+}  // namespace hande

@@ -1,0 +1,201 @@
+// launch.cuh -- per-(key width, system) launchers: the iteration sequence, the
+// deterministic-space selection ("high" space, HANDE-QMC paper App. A.2) and
+// the CSR build of the deterministic-space Hamiltonian.  Included once per key
+// width by inst_w{1,2,8}.cu so the three widths compile in parallel.
+#pragma once
+#include <cstddef>
+
+#include "engine.h"
+
+namespace hande {
+
+// ------------------------------------------------------------------ CSR of H' inside the core
+// H'_rc = <D_r|H|D_c> off the diagonal, H_rr - E_ref on it; zero elements omitted.
+template <int W, int SYS>
+__device__ __forceinline__ double core_elem(const Params& P, int r, int c, const Key<W>& kr, const Key<W>& kc) {
+  if (key_popc_xor<W>(kr, kc) > 4) return 0.0;
+  if (r == c) return __dsub_rn(h_diag<W, SYS>(P.sys, kr), P.st->e_ref);
+  return h_elem<W, SYS>(P.sys, kc, kr);
+}
+template <int W, int SYS>
+__global__ void k_csr_count(Params P, int32_t* rowcnt) {
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= P.ncore) return;
+  Key<W> kr = load_key<W>(P.core_key, P.ncore, r);
+  int cnt = 0;
+  for (int c0 = 0; c0 < P.ncore; c0 += 32) {
+    int c = c0 + lane;
+    bool nz = false;
+    if (c < P.ncore) {
+      Key<W> kc = load_key<W>(P.core_key, P.ncore, c);
+      nz = core_elem<W, SYS>(P, r, c, kr, kc) != 0.0;
+    }
+    cnt += __popc(__ballot_sync(0xffffffffu, nz));
+  }
+  if (lane == 0) rowcnt[r] = cnt;
+}
+template <int W, int SYS>
+__global__ void k_csr_fill(Params P, int64_t* rowptr, int32_t* col, double* val) {
+  int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (r >= P.ncore) return;
+  Key<W> kr = load_key<W>(P.core_key, P.ncore, r);
+  int64_t o = rowptr[r];
+  for (int c0 = 0; c0 < P.ncore; c0 += 32) {
+    int c = c0 + lane;
+    double h = 0.0;
+    if (c < P.ncore) {
+      Key<W> kc = load_key<W>(P.core_key, P.ncore, c);
+      h = core_elem<W, SYS>(P, r, c, kr, kc);
+    }
+    unsigned nzm = __ballot_sync(0xffffffffu, h != 0.0);
+    if (h != 0.0) {
+      int64_t e = o + __popc(nzm & ((1u << lane) - 1u));
+      col[e] = c;
+      val[e] = h;
+    }
+    o += __popc(nzm);
+  }
+}
+// ------------------------------------------------------------------ selection of the core
+template <int W>
+__global__ void k_sel_hist(Params P, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist) {
+  __shared__ unsigned h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t n = P.st->ndet[cur];
+  const Key<W> d0 = ref_key<W>(P);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Key<W> k = load_key<W>(P.key[cur], P.cap, i);
+    if (key_eq<W>(k, d0)) continue;
+    uint64_t v = (uint64_t)iabs64(P.pop[cur][i]);
+    if ((v & mask) == prefix) atomicAdd(&h[(v >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], (unsigned long long)h[i]);
+}
+// stage 0: natt[i] = 1 for non-reference entries with |N| == vstar
+// stage 1: natt[i] = 1 for the selected entries (att_begin holds the tie ranks)
+template <int W>
+__global__ void k_sel_flags(Params P, int cur, uint64_t vstar, int64_t need_eq, int stage) {
+  const int64_t n = P.st->ndet[cur];
+  const Key<W> d0 = ref_key<W>(P);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Key<W> k = load_key<W>(P.key[cur], P.cap, i);
+    bool is0 = key_eq<W>(k, d0);
+    uint64_t v = (uint64_t)iabs64(P.pop[cur][i]);
+    int64_t r;
+    if (stage == 0) {
+      r = (!is0 && v == vstar) ? 1 : 0;
+    } else {
+      r = is0 || v > vstar || (v == vstar && P.att_begin[i] < need_eq);
+    }
+    P.natt[i] = r;
+  }
+}
+template <int W>
+__global__ void k_sel_gather(Params P, int cur, uint64_t* core_key, int64_t ncore) {
+  const int64_t n = P.st->ndet[cur];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t f = P.flags[cur][i] & (uint8_t)~F_CORE;
+    if (P.natt[i]) {
+      Key<W> k = load_key<W>(P.key[cur], P.cap, i);
+      store_key<W>(core_key, ncore, P.att_begin[i], k);
+      f |= F_CORE;
+    }
+    P.flags[cur][i] = f;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+template <int W, int SYS>
+void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s) {
+  Params& P = E.P;
+  DevState* st = P.st;
+  k_det_pass<W, SYS><<<kScanBlocks, kScanThreads, 0, s>>>(P, cur);
+  k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, natt)), st);
+  k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, s>>>(
+      P.natt, P.att_begin, st_field_i64(st, offsetof(DevState, ndet) + 8 * cur), P.part, st);
+  k_split<W><<<kScanBlocks, 256, 0, s>>>(P, cur);
+  if (core && P.ncore > 0) {
+    int nb = (P.ncore + 255) / 256;
+    k_core_locate<W><<<nb, 256, 0, s>>>(P, cur);
+    k_core_spmv<<<(int)(((int64_t)P.ncore * 32 + 255) / 256), 256, 0, s>>>(P, cur);
+    k_core_apply<<<nb, 256, 0, s>>>(P, cur);
+  }
+  k_attempt<W, SYS><<<E.attempt_grid, 256, 0, s>>>(P, cur);
+  int64_t* nbk = st_field_i64(st, offsetof(DevState, nbuckets));
+  k_scan_reduce<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, nbk, P.part, st);
+  k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, scan_total)), st);
+  k_scan_apply<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, P.boff, nbk, P.part, st);
+  k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
+  k_merge<W, SYS><<<E.merge_grid, 512, E.merge_smem_bytes, s>>>(P, cur);
+  k_finalize<<<1, 32, 0, s>>>(P, cur);
+}
+
+template <int W, int SYS>
+void enqueue_hdiag(Engine& E, int cur, int64_t n, cudaStream_t s) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_hdiag<W, SYS><<<blocks, 256, 0, s>>>(E.P, cur, n);
+}
+template <int W, int SYS>
+void enqueue_eref(Engine& E, cudaStream_t s) {
+  k_eref<W, SYS><<<1, 32, 0, s>>>(E.P);
+}
+template <int W, int SYS>
+void enqueue_csr_count(Engine& E, int32_t* rowcnt, cudaStream_t s) {
+  int blocks = (int)(((int64_t)E.P.ncore * 32 + 255) / 256);
+  k_csr_count<W, SYS><<<blocks, 256, 0, s>>>(E.P, rowcnt);
+}
+template <int W, int SYS>
+void enqueue_csr_fill(Engine& E, cudaStream_t s) {
+  int blocks = (int)(((int64_t)E.P.ncore * 32 + 255) / 256);
+  k_csr_fill<W, SYS><<<blocks, 256, 0, s>>>(E.P, E.core_rowptr, E.core_col, E.core_val);
+}
+template <int W>
+void enqueue_sel_hist(Engine& E, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist,
+                      cudaStream_t s) {
+  k_sel_hist<W><<<4 * 152, 256, 0, s>>>(E.P, cur, shift, mask, prefix, hist);
+}
+template <int W>
+void enqueue_sel_flags(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s) {
+  k_sel_flags<W><<<4 * 152, 256, 0, s>>>(E.P, cur, vstar, need_eq, stage);
+}
+template <int W>
+void enqueue_sel_gather(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s) {
+  k_sel_gather<W><<<4 * 152, 256, 0, s>>>(E.P, cur, core_key, ncore);
+}
+
+template <int W>
+size_t merge_smem_w(int tc, int sm) {
+  return merge_smem_bytes<W>(tc, sm);
+}
+
+template <int W, int SYS>
+Ops make_ops() {
+  Ops o;
+  o.iteration = &enqueue_iteration<W, SYS>;
+  o.hdiag = &enqueue_hdiag<W, SYS>;
+  o.eref = &enqueue_eref<W, SYS>;
+  o.csr_count = &enqueue_csr_count<W, SYS>;
+  o.csr_fill = &enqueue_csr_fill<W, SYS>;
+  o.sel_gather = &enqueue_sel_gather<W>;
+  o.sel_hist = &enqueue_sel_hist<W>;
+  o.sel_flags = &enqueue_sel_flags<W>;
+  o.merge_smem = &merge_smem_w<W>;
+  o.merge_kernel = (const void*)&k_merge<W, SYS>;
+  return o;
+}
+
+template <int W>
+Ops ops_for(int kind) {
+  if (kind == SYS_HUBBARD) return make_ops<W, SYS_HUBBARD>();
+  if (kind == SYS_UEG) return make_ops<W, SYS_UEG>();
+  return make_ops<W, SYS_MOLECULE>();
+}
+
+}  // namespace hande

@@ -1,0 +1,260 @@
+"""Python binding of libhande.so (include/hande.h), argument marshalling only.
+
+Every step of an FCIQMC iteration runs in the library's CUDA kernels; this
+module converts dicts and numpy arrays to the C structs, passes PyTorch's
+current CUDA stream and routes the library's device allocations through
+PyTorch's caching allocator.  There is no CPU fallback: if the shared library
+is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ONE_WALKER = 1 << 32
+_KIND = {"hubbard": 0, "ueg": 1, "molecule": 2}
+
+STATUS = {0: "HANDE_OK", -1: "HANDE_ERR_INVALID", -2: "HANDE_ERR_NOMEM", -3: "HANDE_ERR_CAPACITY",
+          -4: "HANDE_ERR_OVERFLOW", -5: "HANDE_ERR_CUDA", -6: "HANDE_ERR_TIMEOUT", -7: "HANDE_ERR_STATE"}
+
+
+class HandeError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _System(C.Structure):
+    _fields_ = [("kind", C.c_int), ("key_words", C.c_int), ("norb", C.c_int), ("nalpha", C.c_int),
+                ("nbeta", C.c_int), ("periodic", C.c_int), ("t", C.c_double), ("U", C.c_double),
+                ("rs", C.c_double), ("h1", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)),
+                ("ecore", C.c_double)]
+
+
+class _Qmc(C.Structure):
+    _fields_ = [("tau", C.c_double), ("target_population", C.c_double), ("shift_damping", C.c_double),
+                ("spawn_cutoff", C.c_double), ("init_pop", C.c_double), ("initiator_threshold", C.c_double),
+                ("p_single", C.c_double), ("shift_period", C.c_int), ("initiator", C.c_int),
+                ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int), ("semi_stoch_start", C.c_int),
+                ("seed", C.c_uint64), ("replica", C.c_uint64), ("state_capacity", C.c_int64),
+                ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int)]
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
+
+
+class _Allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+class _Estimate(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_pre", C.c_int64), ("n0", C.c_int64),
+                ("num_hi", C.c_int64), ("num_lo", C.c_uint64), ("num", C.c_double), ("nw_post", C.c_int64),
+                ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64)]
+
+
+# names declared in include/hande.h, in order
+EXPORTS = ["hande_init_system", "hande_iterate", "hande_synchronize", "hande_estimators", "hande_get_walkers",
+           "hande_set_walkers", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libhande.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_needed:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build the CUDA extension first")
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        u64p, i64p, dp = C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.POINTER(C.c_double)
+        lib.hande_init_system.argtypes = [C.POINTER(_System), C.POINTER(_Qmc), C.POINTER(_Allocator), P,
+                                          C.POINTER(P)]
+        lib.hande_iterate.argtypes = [P, C.c_int]
+        lib.hande_synchronize.argtypes = [P]
+        lib.hande_estimators.argtypes = [P, C.POINTER(_Estimate), C.c_int, C.POINTER(C.c_int)]
+        lib.hande_get_walkers.argtypes = [P, u64p, i64p, dp, C.POINTER(C.c_uint8), C.c_int64, i64p]
+        lib.hande_set_walkers.argtypes = [P, u64p, i64p, dp, C.c_int64]
+        lib.hande_reference.argtypes = [P, dp, u64p]
+        lib.hande_iterations.argtypes = [P]
+        lib.hande_iterations.restype = C.c_int64
+        lib.hande_destroy.argtypes = [P]
+        lib.hande_destroy.restype = None
+        lib.hande_last_error.argtypes = [P]
+        lib.hande_last_error.restype = C.c_char_p
+        for name in EXPORTS[:7]:
+            getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _torch_allocator(device):
+    import torch
+
+    stream = torch.cuda.current_stream(device)
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+        except Exception:  # out of memory: the library reports HANDE_ERR_NOMEM
+            return None
+
+    def free(ptr, nbytes, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _ALLOC_FN(alloc), _FREE_FN(free)
+
+
+class Hande:
+    """One FCIQMC run on the current CUDA device (see include/hande.h)."""
+
+    def __init__(self, system: dict, qmc: dict, stream: int | None = None, torch_memory: bool = True):
+        lib = load()
+        self._lib = lib
+        self._h = C.c_void_p()
+        s = _System()
+        s.kind = _KIND[system["kind"]]
+        s.key_words = int(system["key_words"])
+        s.norb = int(system["norb"])
+        s.nalpha = int(system["nalpha"])
+        s.nbeta = int(system["nbeta"])
+        s.periodic = int(system.get("periodic", 0))
+        s.t = float(system.get("t", 0.0))
+        s.U = float(system.get("U", 0.0))
+        s.rs = float(system.get("rs", 0.0))
+        s.ecore = float(system.get("ecore", 0.0))
+        self._keep = []
+        if s.kind == 2:
+            h1 = np.ascontiguousarray(system["h1"], dtype=np.float64)
+            eri = np.ascontiguousarray(system["eri"], dtype=np.float64)
+            self._keep += [h1, eri]
+            s.h1 = h1.ctypes.data_as(C.POINTER(C.c_double))
+            s.eri = eri.ctypes.data_as(C.POINTER(C.c_double))
+        q = _Qmc()
+        q.tau = float(qmc["tau"])
+        q.target_population = float(qmc["target_population"])
+        q.shift_damping = float(qmc.get("shift_damping", 0.05))
+        q.spawn_cutoff = float(qmc.get("spawn_cutoff", 0.0))
+        q.init_pop = float(qmc["init_pop"])
+        q.initiator_threshold = float(qmc.get("initiator_threshold", 3.0))
+        q.p_single = float(qmc.get("p_single", 0.1))
+        q.shift_period = int(qmc.get("shift_period", 1))
+        q.initiator = int(qmc.get("initiator", 0))
+        q.real_amplitudes = int(qmc.get("real_amplitudes", 0))
+        q.semi_stoch_size = int(qmc.get("semi_stoch_size", 0))
+        q.semi_stoch_start = int(qmc.get("semi_stoch_start", 0))
+        q.seed = int(qmc["seed"])
+        q.replica = int(qmc.get("replica", 0))
+        q.state_capacity = int(qmc.get("state_capacity", 0))
+        q.spawn_capacity = int(qmc.get("spawn_capacity", 0))
+        q.record_capacity = int(qmc.get("record_capacity", 0))
+        self.W = s.key_words
+        alloc_p = None
+        if stream is None or torch_memory:
+            import torch
+            dev = torch.cuda.current_device()
+            if stream is None:
+                stream = torch.cuda.current_stream(dev).cuda_stream
+            if torch_memory:
+                fa, ff = _torch_allocator(dev)
+                self._alloc = _Allocator(fa, ff, None)
+                self._alloc_fns = (fa, ff)
+                alloc_p = C.byref(self._alloc)
+        self.stream = int(stream)
+        rc = lib.hande_init_system(C.byref(s), C.byref(q), alloc_p, C.c_void_p(self.stream), C.byref(self._h))
+        if rc != 0:
+            raise HandeError(rc, "hande_init_system failed")
+
+    # ------------------------------------------------------------------ calls
+    def _check(self, rc: int, what: str):
+        if rc != 0:
+            msg = self._lib.hande_last_error(self._h).decode()
+            raise HandeError(rc, f"{what}: {msg}")
+
+    def iterate(self, n: int = 1) -> None:
+        self._check(self._lib.hande_iterate(self._h, int(n)), "hande_iterate")
+
+    def synchronize(self) -> None:
+        self._check(self._lib.hande_synchronize(self._h), "hande_synchronize")
+
+    @property
+    def iterations(self) -> int:
+        return int(self._lib.hande_iterations(self._h))
+
+    def reference(self):
+        e = C.c_double()
+        k = np.zeros(self.W, dtype=np.uint64)
+        self._check(self._lib.hande_reference(self._h, C.byref(e), k.ctypes.data_as(C.POINTER(C.c_uint64))),
+                    "hande_reference")
+        return e.value, k
+
+    def estimators(self, max_records: int = 1 << 20) -> dict:
+        buf = (_Estimate * max_records)()
+        n = C.c_int()
+        self._check(self._lib.hande_estimators(self._h, buf, max_records, C.byref(n)), "hande_estimators")
+        arr = np.ctypeslib.as_array(buf)[: n.value]
+        return {name: np.array(arr[name]) for name, _ in _Estimate._fields_}
+
+    def walkers(self):
+        n = C.c_int64()
+        rc = self._lib.hande_get_walkers(self._h, None, None, None, None, 0, C.byref(n))
+        if rc not in (0, -3):
+            self._check(rc, "hande_get_walkers")
+        cap = n.value
+        keys = np.zeros((cap, self.W), dtype=np.uint64)
+        pops = np.zeros(cap, dtype=np.int64)
+        hd = np.zeros(cap, dtype=np.float64)
+        fl = np.zeros(cap, dtype=np.uint8)
+        self._check(self._lib.hande_get_walkers(self._h, keys.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                pops.ctypes.data_as(C.POINTER(C.c_int64)),
+                                                hd.ctypes.data_as(C.POINTER(C.c_double)),
+                                                fl.ctypes.data_as(C.POINTER(C.c_uint8)), cap, C.byref(n)),
+                    "hande_get_walkers")
+        m = n.value
+        return keys[:m], pops[:m], hd[:m], fl[:m]
+
+    def set_walkers(self, keys, pops, hdiag=None) -> None:
+        k = np.ascontiguousarray(np.asarray(keys, dtype=np.uint64).reshape(-1, self.W))
+        p = np.ascontiguousarray(pops, dtype=np.int64)
+        hp = None
+        if hdiag is not None:
+            h = np.ascontiguousarray(hdiag, dtype=np.float64)
+            self._hd_keep = h
+            hp = h.ctypes.data_as(C.POINTER(C.c_double))
+        self._check(self._lib.hande_set_walkers(self._h, k.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                                p.ctypes.data_as(C.POINTER(C.c_int64)), hp, len(p)),
+                    "hande_set_walkers")
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.hande_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,59 @@
+"""The C-ABI library loads and exports every entry point include/hande.h
+declares; argument validation runs without a GPU."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1811_11679_gb300 import hande, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "hande.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hande_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hande.load()
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(hande.EXPORTS) == names
+
+
+def test_invalid_arguments_rejected_before_any_device_call():
+    lib = hande.load()
+    out = C.c_void_p()
+    assert lib.hande_init_system(None, None, None, None, C.byref(out)) == -1
+    s = hande._System()
+    q = hande._Qmc()
+    s.kind, s.key_words, s.norb, s.nalpha, s.nbeta = 1, 3, 19, 7, 7   # key_words must be 1, 2 or 8
+    q.tau, q.init_pop = 0.01, 10.0
+    assert lib.hande_init_system(C.byref(s), C.byref(q), None, None, C.byref(out)) == -1
+    s.key_words, s.rs = 1, 1.0
+    q.tau = -1.0
+    assert lib.hande_init_system(C.byref(s), C.byref(q), None, None, C.byref(out)) == -1
+    q.tau = 0.01
+    q.semi_stoch_size, q.real_amplitudes = 10, 0   # semi-stochastic needs real weights
+    assert lib.hande_init_system(C.byref(s), C.byref(q), None, None, C.byref(out)) == -1
+    s.kind, s.norb, s.nalpha, s.nbeta, s.periodic = 0, 2, 1, 1, 1   # periodic 2-site ring
+    q.semi_stoch_size = 0
+    assert lib.hande_init_system(C.byref(s), C.byref(q), None, None, C.byref(out)) == -1
+    assert lib.hande_iterate(None, 1) == -1
+    assert lib.hande_last_error(None) == b"no context"
+    lib.hande_destroy(None)
+
+
+def test_python_binding_has_no_cpu_fallback(monkeypatch, tmp_path):
+    """With the shared library missing, the binding raises instead of computing."""
+    monkeypatch.setattr(hande, "_lib", None)
+    monkeypatch.setattr(hande._build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        hande.load(build_if_needed=False)
