@@ -1,0 +1,319 @@
+"""Benchmark: FCIQMC iterations at 1e7 walkers on one GB300 (spawn attempts/s).
+
+Workload: the synthetic 28-orbital molecule (56 spin orbitals, 64-bit keys,
+8 up + 7 down electrons, seeded integrals from paper_1811_11679_gb300.inputs),
+heat-bath excitation generator, initiator rule (n_a = 3), real weights
+(spawn_cutoff 0.1), tau = 0.01, target population 1e7, semi-stochastic core of
+1e4 determinants chosen at iteration 2000 ("high" space).  The run grows on the
+device from 500 walkers on the reference determinant; the timed steps start
+after iteration 2000 + warm-up.  One step = one full FCIQMC iteration (every
+phase on the GPU).  The walker and spawn arrays exceed the 129 MB L2, so no
+flush is needed between steps.
+
+Arms
+  default           the CUDA engine through its C ABI (CUDA-graph launches)
+  --impl reference  the CPU oracle (oracle/), timed on the host cores on a
+                    1/10-scale run of the same workload (1e6 walkers, core 1e3)
+
+Output: one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FCIQMC spawn attempts/s at 1e7 walkers"
+UNIT = "attempts/s"
+WORKLOAD = "molecule28"
+N_WALKERS = 1e7
+CORE = 10_000
+CORE_START = 2000
+
+
+def _workload_desc():
+    return ("synthetic molecule, 28 spatial orbitals (56 spin orbitals, 64-bit keys), 8a+7b electrons, "
+            "heat-bath generator, initiator n_a=3, real weights, tau=0.01, target 1e7 walkers, "
+            "semi-stochastic core 1e4 chosen at iteration 2000; grown on the device from 500 walkers")
+
+
+def _system_and_qmc(scale: float = 1.0):
+    from paper_1811_11679_gb300 import inputs
+    core = int(CORE * scale) if scale < 1 else CORE
+    sysd, q = inputs.workload(WORKLOAD, target_population=N_WALKERS * scale, semi_stoch_size=core,
+                              semi_stoch_start=CORE_START, state_capacity=int(16_000_000 * max(scale, 0.1)),
+                              spawn_capacity=int(32_000_000 * max(scale, 0.1)))
+    return sysd, q
+
+
+def _grow(step, iterations, until):
+    """Advance in blocks until `until` iterations are done."""
+    while iterations() < until:
+        step(min(250, until - iterations()))
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _phase_bytes(rec, W):
+    """Algorithmic bytes per launch of the HBM-bound phases."""
+    K = 8 * W
+    ns, nd_pre, nd_post = float(rec["nspawn"]), float(rec["ndet_pre"]), float(rec["ndet"])
+    return {
+        # bucketed spawns read once, main list read once, new list written once
+        "merge": ns * (K + 9) + nd_pre * (K + 17) + nd_post * (K + 17),
+        # staged spawns read (key, amount, bucket/rank word), bucketed spawns written
+        "scatter": ns * (K + 16) + ns * (K + 9),
+        # main list read, populations/flags/attempt counts written
+        "det_pass": nd_pre * (K + 17) + nd_pre * (8 + 1 + 8),
+    }
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1811_11679_gb300 import hande
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dev = torch.cuda.current_device()
+    sysd, q = _system_and_qmc()
+    q["replica"] = rank
+    W = sysd["key_words"]
+    eng = hande.Hande(sysd, q)
+    t_grow = time.perf_counter()
+    _grow(eng.iterate, lambda: eng.iterations, CORE_START + 50)
+    eng.iterate(args.warmup)
+    eng.synchronize()
+    t_grow = time.perf_counter() - t_grow
+    eng.estimators()
+    stream = torch.cuda.current_stream(dev)
+    assert stream.cuda_stream == eng.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        e0.record(stream)
+        eng.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    rec = eng.estimators()
+    attempts = float(rec["natt"].sum())
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms, attempts], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        t_max, attempts = float(tmax[0]), float(t[1])
+    value = attempts / (t_max / 1e3)
+
+    # per-phase device time (kernel-by-kernel launches with events), same stream
+    ph = eng.iterate_timed(args.steps)
+    rec2 = eng.estimators()
+    nd_prev = np.concatenate([[rec["ndet"][-1]], rec2["ndet"][:-1]])
+    per = {"nspawn": rec2["nspawn"].mean(), "ndet_pre": nd_prev.mean(), "ndet": rec2["ndet"].mean()}
+    total = sum(ph.values())
+    share = {k: v / total for k, v in ph.items()}
+    dominant = max(ph, key=ph.get)
+    peak, peak_kind = _peaks()
+    byt = _phase_bytes(per, W)
+    roof = {}
+    for k in ("merge", "scatter", "det_pass"):
+        t_s = ph[k] / args.steps / 1e3
+        ach = byt[k] / t_s / 1e9
+        roof[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                   "frac": round(ach / peak, 4), "traffic": None, "bytes_per_launch": int(byt[k]),
+                   "ms_per_launch": round(ph[k] / args.steps, 4), "peak_source": peak_kind}
+
+    # end to end through the C ABI with host buffers: upload, iterate, download
+    e2e_steps = min(args.steps, 3)
+    k_h, p_h, h_h, _ = eng.walkers()
+    h2d = d2h = 0
+    att_e2e = 0.0
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        eng.set_walkers(k_h, p_h, h_h)
+        h2d += k_h.nbytes + p_h.nbytes + h_h.nbytes
+        eng.iterate(1)
+        k_h, p_h, h_h, f_h = eng.walkers()
+        r = eng.estimators()
+        d2h += k_h.nbytes + p_h.nbytes + h_h.nbytes + f_h.nbytes + 88 * len(r["iter"])
+        att_e2e += float(r["natt"].sum())
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": att_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
+           "d2h_bytes_per_step": int(d2h / e2e_steps),
+           "step": "set_walkers(host list) + iterate(1) + get_walkers + estimators"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+        "config": {"workload": _workload_desc(), "walkers_target": N_WALKERS,
+                   "mean_walkers": float(rec["nw_post"].mean()) / 2 ** 32,
+                   "mean_determinants": float(rec["ndet"].mean()),
+                   "mean_attempts_per_step": attempts / args.steps / world,
+                   "mean_spawns_per_step": float(rec["nspawn"].mean()),
+                   "first_timed_iteration": int(rec["iter"][0]), "grow_seconds": round(t_grow, 2),
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": f"independent replicas x{world}"},
+        "roofline": dict(roof["merge"], kernel="k_merge (annihilation: tile sort + merge)"),
+        "roofline_phases": roof,
+        "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in ph.items()},
+        "phase_share": {k: round(v, 4) for k, v in share.items()},
+        "dominant_phase": dominant,
+        "e2e": e2e,
+        "gpu_launches": int(args.steps * 15),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        k_h, p_h, _, _ = eng.walkers()
+        out["cpu_baseline"] = cpu_baseline(sysd, q, k_h, p_h)
+    eng.close()
+    return out
+
+
+def cpu_baseline(sysd, q, keys, pops):
+    """The oracle as it stands, single-threaded: one iteration on the device's
+    current 1e7-walker list (its deterministic space re-chosen from that list)."""
+    import oracle
+    o = oracle.Oracle(sysd, dict(q, semi_stoch_start=0))
+    o.set_walkers(keys, pops)
+    t0 = time.perf_counter()
+    o.iterate(1)
+    dt = time.perf_counter() - t0
+    r = o.records()
+    return {"value": float(r["natt"][-1]) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "one oracle iteration on the GPU run's steady-state list (1e7 walkers)",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    """The oracle arm: the same workload at 1/10 scale (1e6 walkers, core 1e3 at
+    iteration 2000), grown on the CPU; each step is one oracle iteration."""
+    import oracle
+    sysd, q = _system_and_qmc(scale=0.1)
+    o = oracle.Oracle(sysd, q)
+    t_grow = time.perf_counter()
+    done = 0
+    while done < CORE_START + 50 + args.warmup:
+        n = min(250, CORE_START + 50 + args.warmup - done)
+        o.iterate(n)
+        done += n
+    t_grow = time.perf_counter() - t_grow
+    n0 = len(o.records()["iter"])
+    t0 = time.perf_counter()
+    o.iterate(args.steps)
+    dt = time.perf_counter() - t0
+    r = o.records()
+    att = float(r["natt"][n0:].sum())
+    v = att / dt
+    sample = ("the workload at 1/10 scale (1e6 walkers, core 1e3 chosen at iteration 2000), grown on the "
+              "CPU from 500 walkers; one oracle iteration per step")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "config": {"workload": _workload_desc(), "sample": sample, "grow_seconds": round(t_grow, 1),
+                       "mean_walkers": float(r["nw_post"][n0:].mean()) / 2 ** 32},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -104,6 +104,10 @@ typedef struct {
   int64_t state_capacity;     /* max determinants in the main list (0 = default) */
   int64_t spawn_capacity;     /* max spawns per iteration (0 = default) */
   int record_capacity;        /* estimator records kept on the device (0 = default) */
+  int tile_capacity;          /* distinct spawned keys one annihilation tile holds on chip:
+                                 0 = default (2048 for 64/128-bit keys, 1024 for 512-bit),
+                                 else a power of two in [64, default]; smaller values only
+                                 send more buckets through the oversized-bucket path */
 } hande_qmc;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  `alloc`
@@ -141,6 +145,19 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
 /* Advance n >= 0 iterations (asynchronous; one CUDA-graph launch per iteration). */
 hande_status hande_iterate(hande_ctx* ctx, int n);
 
+/* Number of phases reported by hande_iterate_timed, in order: determinant pass
+ * (estimators, initiator flags, attempt counts, death), attempt-count scan,
+ * bucket splitters, deterministic-space projection, spawning attempts,
+ * bucket-count scan, bucket scatter, merge (annihilation), diagonal elements
+ * of new determinants, shift/record. */
+#define HANDE_NPHASES 10
+
+/* Advance n iterations like hande_iterate, but launched kernel by kernel
+ * (no graph) with CUDA events between the phases; phase_ms[0..HANDE_NPHASES)
+ * receives the device time of each phase summed over the n iterations.
+ * Synchronises after every iteration.  For profiling only. */
+hande_status hande_iterate_timed(hande_ctx* ctx, int n, float* phase_ms, int nphases);
+
 /* Wait for the stream and report latched device errors. */
 hande_status hande_synchronize(hande_ctx* ctx);
 
@@ -156,12 +173,28 @@ hande_status hande_estimators(hande_ctx* ctx, hande_estimate* out, int max, int*
 hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, double* hdiag, uint8_t* flags,
                                int64_t cap, int64_t* n);
 
-/* Replace the walker list with n entries (keys strictly ascending, the
- * reference determinant must be present).  hdiag may be NULL, in which case
- * H_ii - E_ref is evaluated on the device.  With semi_stoch_start == 0 the
- * deterministic space is chosen from this list.  Synchronises. */
+/* Replace the walker list with n entries (keys strictly ascending, each with
+ * nalpha + nbeta electrons, the reference determinant present).  hdiag may be
+ * NULL, in which case H_ii - E_ref is evaluated on the device.  If the
+ * deterministic space is in use, or semi_stoch_start == 0, it is chosen again
+ * from this list.  The iteration counter is kept.  Synchronises. */
 hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
                                int64_t n);
+
+/* Diagnostics of the last iteration (synchronises; usable after an error). */
+typedef struct {
+  uint32_t error_bits;        /* device error latch: 1 spawn capacity, 2 walker capacity,
+                                 4 population overflow, 8 wait timeout, 16 tile capacity,
+                                 32 bucket capacity */
+  int64_t ndet;               /* current list length */
+  int64_t natt, nspawn;       /* attempts and spawns of the last iteration */
+  int64_t nbuckets;           /* annihilation buckets of the last iteration */
+  int64_t bucket_main;        /* main-list entries per bucket */
+  int64_t max_bucket_spawns;  /* largest number of spawns that fell in one bucket */
+  int64_t tile_capacity;      /* distinct spawned keys one bucket can hold on chip */
+  int64_t ncore;              /* deterministic-space size */
+} hande_diag;
+hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out);
 
 /* E_ref = H_00 of the reference determinant, and its key (key_words words). */
 hande_status hande_reference(hande_ctx* ctx, double* e_ref, uint64_t* key);

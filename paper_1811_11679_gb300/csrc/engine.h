@@ -15,7 +15,7 @@ struct Engine;
 
 // launchers for one (key width, system kind) pair
 struct Ops {
-  void (*iteration)(Engine& E, int cur, bool core, cudaStream_t s);
+  void (*iteration)(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_t* ev);
   void (*hdiag)(Engine& E, int cur, int64_t n, cudaStream_t s);
   void (*eref)(Engine& E, cudaStream_t s);
   void (*csr_count)(Engine& E, int32_t* rowcnt, cudaStream_t s);
@@ -27,6 +27,8 @@ struct Ops {
   size_t (*merge_smem)(int tc, int sm);
   const void* merge_kernel;
 };
+
+constexpr int kPhases = 10;   // timed phases of one iteration
 
 Ops ops_w1(int kind);
 Ops ops_w2(int kind);
@@ -58,6 +60,7 @@ struct Engine {
   int64_t nnz_cap = 0, ncore_cap = 0;
   double e_ref = 0.0;
   bool failed = false;
+  unsigned err_bits = 0;
   std::string err;
 };
 

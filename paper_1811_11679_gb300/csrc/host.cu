@@ -88,6 +88,7 @@ struct HostTables {
   std::vector<int> hb_start, hb_len;
   std::vector<uint16_t> hb_ab;
   std::vector<uint64_t> hb_cum;
+  std::vector<double> orb_diag, pair_diag;
 };
 
 inline size_t tri_h(size_t p, size_t q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
@@ -134,6 +135,17 @@ void build_ueg(const hande_system& s, SysDev& sd, HostTables& T) {
   sd.vfac = 1.0 / (kPi * box);
   double kf = 2.0 * kPi / box;
   sd.kfac = 0.5 * (kf * kf);
+  // diagonal tables: kinetic |k|^2/2 per orbital, exchange kernel per orbital pair
+  T.orb_diag.resize(s.norb);
+  T.pair_diag.assign((size_t)s.norb * s.norb, 0.0);
+  for (int i = 0; i < s.norb; ++i) {
+    T.orb_diag[i] = sd.kfac * (double)T.kvec[i].w;
+    for (int j = 0; j < s.norb; ++j) {
+      int dx = T.kvec[i].x - T.kvec[j].x, dy = T.kvec[i].y - T.kvec[j].y, dz = T.kvec[i].z - T.kvec[j].z;
+      int m = dx * dx + dy * dy + dz * dz;
+      if (m > 0) T.pair_diag[(size_t)i * s.norb + j] = sd.vfac / (double)m;
+    }
+  }
 }
 
 double g_so(const std::vector<double>& eri, int n, int p, int q, int r, int t) {
@@ -163,6 +175,18 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           T.eri_packed[tri_h(tri_h(a, b), tri_h(c, d))] = v;
         }
   sd.ecore = s.ecore;
+  // diagonal tables: h_kk per spin orbital, (kk|ll) - (kl|lk) per spin-orbital pair
+  const int nsp = 2 * n;
+  T.orb_diag.resize(nsp);
+  T.pair_diag.assign((size_t)nsp * nsp, 0.0);
+  for (int p = 0; p < nsp; ++p) {
+    T.orb_diag[p] = T.h1[(size_t)(p >> 1) * N + (p >> 1)];
+    for (int q = 0; q < nsp; ++q) {
+      double jv = at(p >> 1, p >> 1, q >> 1, q >> 1);
+      double kv = ((p ^ q) & 1) ? 0.0 : at(p >> 1, q >> 1, q >> 1, p >> 1);
+      T.pair_diag[(size_t)p * nsp + q] = jv - kv;
+    }
+  }
   // heat-bath tables: for each occupied pair p<q (index q(q-1)/2 + p), every
   // spin-allowed target pair a<b outside {p, q} with |<pq||ab>| > 0, in ascending
   // (a, b) order, as cumulative thresholds floor(2^64 S_k / S_total) made strictly
@@ -234,6 +258,7 @@ unsigned read_error(Engine& E) {
 hande_status map_error(Engine& E, unsigned e) {
   if (!e) return HANDE_OK;
   E.failed = true;
+  E.err_bits = e;
   if (e & ERR_OVERFLOW) {
     E.err = "population overflow (|N| reached 2^62 in fixed point)";
     return HANDE_ERR_OVERFLOW;
@@ -243,8 +268,8 @@ hande_status map_error(Engine& E, unsigned e) {
     return HANDE_ERR_TIMEOUT;
   }
   if (e & ERR_SPAWN_CAPACITY) E.err = "spawn capacity exceeded (raise spawn_capacity)";
-  else if (e & ERR_STATE_CAPACITY) E.err = "walker-list capacity exceeded (raise state_capacity)";
   else if (e & ERR_TILE_CAPACITY) E.err = "annihilation tile capacity exceeded (too many distinct new determinants in one key range)";
+  else if (e & ERR_STATE_CAPACITY) E.err = "walker-list capacity exceeded (raise state_capacity)";
   else E.err = "bucket capacity exceeded";
   return HANDE_ERR_CAPACITY;
 }
@@ -253,7 +278,7 @@ void ensure_graph(Engine& E, int cur, int core) {
   if (E.graph[cur][core]) return;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(E.cap_stream, cudaStreamCaptureModeThreadLocal));
-  E.ops.iteration(E, cur, core != 0, E.cap_stream);
+  E.ops.iteration(E, cur, core != 0, E.cap_stream, nullptr);
   cudaError_t launch_err = cudaGetLastError();
   CK(cudaStreamEndCapture(E.cap_stream, &g));
   if (launch_err != cudaSuccess) {
@@ -459,6 +484,12 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (P.scap >= ((int64_t)1 << 31)) throw Fail{HANDE_ERR_INVALID, "spawn_capacity must be below 2^31"};
     P.rec_cap = q.record_capacity > 0 ? q.record_capacity : 1 << 16;
     P.tile_cap = E.W == 1 ? 2048 : (E.W == 2 ? 2048 : 1024);
+    if (q.tile_capacity > 0) {
+      int tc = q.tile_capacity;
+      if (tc < 64 || tc > P.tile_cap || (tc & (tc - 1)))
+        throw Fail{HANDE_ERR_INVALID, "tile_capacity must be a power of two in [64, default]"};
+      P.tile_cap = tc;
+    }
     P.seg_max = P.tile_cap / 2;
     E.core_size = q.semi_stoch_size;
     E.core_start = q.semi_stoch_start;
@@ -495,6 +526,8 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.hb_len = upload(E, T.hb_len);
     sd.hb_ab = upload(E, T.hb_ab);
     sd.hb_cum = upload(E, T.hb_cum);
+    sd.orb_diag = upload(E, T.orb_diag);
+    sd.pair_diag = upload(E, T.pair_diag);
 
     // ---- device buffers
     const int64_t cap = P.cap, scap = P.scap;
@@ -574,6 +607,41 @@ hande_status hande_iterate(hande_ctx* ctx, int n) {
       int core = E.core_active ? 1 : 0;
       ensure_graph(E, E.cur, core);
       CK(cudaGraphLaunch(E.graph[E.cur][core], E.stream));
+      E.cur ^= 1;
+      E.host_iter += 1;
+      if (E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start) {
+        hande_status es = map_error(E, read_error(E));
+        if (es != HANDE_OK) return es;
+        select_core(E);
+      }
+    }
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_iterate_timed(hande_ctx* ctx, int n, float* phase_ms, int nphases) {
+  if (!ctx || n < 0 || !phase_ms || nphases < kPhases) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    cudaEvent_t ev[kPhases + 1];
+    for (int k = 0; k <= kPhases; ++k) CK(cudaEventCreate(&ev[k]));
+    struct Cleanup {
+      cudaEvent_t* e;
+      ~Cleanup() {
+        for (int k = 0; k <= kPhases; ++k) cudaEventDestroy(e[k]);
+      }
+    } cleanup{ev};
+    for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0f;
+    for (int it = 0; it < n; ++it) {
+      E.ops.iteration(E, E.cur, E.core_active, E.stream, ev);
+      CK(cudaGetLastError());
+      CK(cudaEventSynchronize(ev[kPhases]));
+      for (int k = 0; k < kPhases; ++k) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+        phase_ms[k] += ms;
+      }
       E.cur ^= 1;
       E.host_iter += 1;
       if (E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start) {
@@ -717,12 +785,41 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     if (hdiag) CK(cudaMemcpyAsync(E.P.hdiag[cur], hdiag, n * 8, cudaMemcpyHostToDevice, E.stream));
     else E.ops.hdiag(E, cur, n, E.stream);
     CK(cudaGetLastError());
-    // the deterministic space refers to the old list
+    // the deterministic space refers to the old list: choose it again from the
+    // new one if it is in use (or chosen at the start)
+    const bool reselect = E.core_size > 0 && (E.core_start == 0 || E.core_active);
     E.core_active = false;
     E.P.ncore = 0;
     drop_graphs(E, 1);
-    if (E.core_size > 0 && E.core_start == 0) select_core(E);
+    if (reselect) select_core(E);
     CK(cudaStreamSynchronize(E.stream));
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out) {
+  if (!ctx || !out) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  return run_guarded(&E, [&]() -> hande_status {
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, E.P.st, sizeof hs, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    std::memset(out, 0, sizeof *out);
+    out->error_bits = hs.error | E.err_bits;
+    out->ndet = hs.ndet[E.cur];
+    out->natt = hs.natt;
+    out->nspawn = hs.nspawn;
+    out->nbuckets = hs.nbuckets;
+    out->bucket_main = hs.sb;
+    out->tile_capacity = E.P.tile_cap;
+    out->ncore = E.P.ncore;
+    int64_t nb = std::min<int64_t>(hs.nbuckets, E.P.cap);
+    if (nb > 0) {
+      std::vector<uint32_t> cnt((size_t)nb);
+      CK(cudaMemcpyAsync(cnt.data(), E.P.bcount, nb * 4, cudaMemcpyDeviceToHost, E.stream));
+      CK(cudaStreamSynchronize(E.stream));
+      for (uint32_t c : cnt) out->max_bucket_spawns = std::max<int64_t>(out->max_bucket_spawns, c);
+    }
     return HANDE_OK;
   });
 }

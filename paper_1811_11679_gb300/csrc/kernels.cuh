@@ -51,6 +51,8 @@ struct DevState {
   double e_ref;
   int vary;
   int64_t scan_total;
+  int64_t nspawn_prev;   // spawns of the previous iteration (bucket sizing)
+  int64_t nnew;          // new determinants written by the merge
   unsigned error;
   unsigned merge_ticket;
 };
@@ -326,7 +328,9 @@ __global__ void k_split(Params P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t n = st->ndet[cur];
-  const int64_t na = st->natt;
+  // expected spawns: the previous iteration's count with 25% headroom (the
+  // attempt count before the first iteration)
+  const int64_t na = st->nspawn_prev > 0 ? st->nspawn_prev + st->nspawn_prev / 4 : st->natt;
   int64_t sb = (int64_t)P.seg_max;
   int64_t half = P.tile_cap / 4;   // expected spawns per bucket: a quarter tile
   if (na > 0) {
@@ -340,6 +344,7 @@ __global__ void k_split(Params P, int cur) {
     st->nbuckets = nb;
     st->sb = sb;
     st->nspawn = 0;
+    st->nnew = 0;
     st->merge_ticket = 0;
     if (nb > P.cap) set_error(st, ERR_BUCKET_CAPACITY);
   }
@@ -536,24 +541,32 @@ __global__ void __launch_bounds__(256) k_scatter(Params P) {
 template <int W>
 struct MergeSmem {
   // tile arrays are carved from dynamic shared memory
-  uint64_t* skey;    // [W][TC]
+  uint64_t* skey;    // [W][TC]  spawned keys, sorted unique after sort_reduce
   int64_t* samt;     // [TC]
-  uint32_t* sflg;    // [TC]   bit0 initiator parent, bit31 padding
+  uint32_t* sflg;    // [TC]     bit0 initiator parent, bit31 padding
   int32_t* uid;      // [TC]
   int64_t* uamt;     // [TC]
   uint32_t* uflg;    // [TC]
-  uint64_t* mkey;    // [W][SM]
-  int32_t* mmatch;   // [SM]   unique index matching main entry, or -1
-  int32_t* mlb;      // [SM]   number of unique keys below main key
-  int32_t* ulb;      // [TC]   number of main keys below unique key (or -1 if matched)
-  uint32_t* mscan;   // [TC+1] exclusive prefix of matched flags over unique list
-  uint32_t* keep;    // [TC+SM] keep flag by merged rank, scanned in place
+  uint64_t* mkey;    // [W][SM]  main-list keys of the bucket's segment
+  int32_t* mmatch;   // [SM]     unique index matching a main entry, or -1
+  int32_t* mlb;      // [SM]     unique keys below the main key
+  int32_t* ulb;      // [TC]     main keys below the unique key (-1 if matched)
+  uint32_t* mscan;   // [TC+1]   exclusive prefix of matched flags over the unique list
+  uint32_t* keep;    // [TC+SM]  keep flags by merged rank, scanned in place
+  uint64_t* spl;     // [W][RMAX] sub-range splitters of an oversized bucket
+  int32_t* rcnt;     // [RMAX+1] spawns per sub-range
+  int32_t* roff;     // [RMAX+1]
+  int32_t* rcur;     // [RMAX+1]
+  int32_t* runiq;    // [RMAX+1] unique keys per sub-range
+  int32_t* rkeep;    // [RMAX+1] surviving entries per sub-range
 };
+
+constexpr int kSubRanges = 256;   // RMAX: sub-ranges of one oversized bucket
 
 template <int W>
 __host__ __device__ inline size_t merge_smem_bytes(int TC, int SM) {
   return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4) +
-         (size_t)(TC + SM) * 4 + 512;
+         (size_t)(TC + SM) * 4 + (size_t)kSubRanges * 8 * W + (size_t)(kSubRanges + 1) * 4 * 5 + 1024;
 }
 
 template <int W>
@@ -568,6 +581,13 @@ __device__ __forceinline__ Key<W> mkey_at(const MergeSmem<W>& m, int SM, int i) 
   Key<W> k;
 #pragma unroll
   for (int j = 0; j < W; ++j) k.w[j] = m.mkey[j * SM + i];
+  return k;
+}
+template <int W>
+__device__ __forceinline__ Key<W> spl_at(const MergeSmem<W>& m, int i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = m.spl[j * kSubRanges + i];
   return k;
 }
 template <int W>
@@ -593,9 +613,9 @@ __device__ __forceinline__ void rec_swap(MergeSmem<W>& m, int TC, int a, int b) 
   m.sflg[b] = z;
 }
 
-// sort records [0, n) in place (padding to a power of two), then combine equal
-// keys: on return records [0, u) are the sorted unique keys with summed amounts
-// and OR-ed initiator bits.  Returns u.
+// Sort records [0, n) in place (bitonic, padded to a power of two), then combine
+// equal keys: on return records [0, u) are the sorted unique keys with summed
+// amounts and OR-ed initiator bits.  Returns u.
 template <int W>
 __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
   int n2 = 1;
@@ -615,7 +635,6 @@ __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
       __syncthreads();
     }
   }
-  // heads and unique ids
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     bool head = (i == 0) || !key_eq<W>(skey_at<W>(m, TC, i), skey_at<W>(m, TC, i - 1));
     m.uid[i] = head ? 1 : 0;
@@ -623,10 +642,8 @@ __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
     m.uflg[i] = 0;
   }
   __syncthreads();
-  // inclusive scan of heads -> unique id + 1
   uint32_t* u32 = reinterpret_cast<uint32_t*>(m.uid);
   uint32_t total = block_scan_excl<uint32_t>(u32, n, wsum);
-  // u32 now holds exclusive prefix; unique id of element i = prefix + head - 1
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     bool head = (i == 0) || !key_eq<W>(skey_at<W>(m, TC, i), skey_at<W>(m, TC, i - 1));
     int id = (int)u32[i] + (head ? 1 : 0) - 1;
@@ -659,9 +676,34 @@ __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
   return (int)total;
 }
 
+// Load spawns [beg, end) of (key, amt, flag) arrays into the tile and reduce
+// them; chunks are appended to the unique keys kept so far, so repeated keys
+// (many spawns onto one determinant) collapse as they arrive.  Returns the
+// number of unique keys, or -1 if more than TC distinct keys arrive.
 template <int W>
-__device__ __forceinline__ int lb_smem_main(const MergeSmem<W>& m, int SM, int nm, const Key<W>& k) {
-  int lo = 0, hi = nm;
+__device__ int load_reduce(MergeSmem<W>& m, int TC, const uint64_t* key, int64_t kstride, const int64_t* amt,
+                           const uint8_t* flg8, const uint64_t* flg64, int64_t beg, int64_t end, uint32_t* wsum) {
+  int nu = 0;
+  for (int64_t pos = beg; pos < end;) {
+    int take = TC - nu;
+    if (take <= 0) return -1;
+    if ((int64_t)take > end - pos) take = (int)(end - pos);
+    for (int i = threadIdx.x; i < take; i += blockDim.x) {
+      int64_t src = pos + i;
+#pragma unroll
+      for (int j = 0; j < W; ++j) m.skey[j * TC + nu + i] = key[j * kstride + src];
+      m.samt[nu + i] = amt[src];
+      m.sflg[nu + i] = flg8 ? (uint32_t)flg8[src] : (uint32_t)(flg64[src] & 1u);
+    }
+    __syncthreads();
+    nu = sort_reduce<W>(m, TC, nu + take, wsum);
+    pos += take;
+  }
+  return nu;
+}
+
+template <int W>
+__device__ __forceinline__ int lb_smem_main(const MergeSmem<W>& m, int SM, int lo, int hi, const Key<W>& k) {
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
     if (key_lt<W>(mkey_at<W>(m, SM, mid), k)) lo = mid + 1;
@@ -680,10 +722,8 @@ __device__ __forceinline__ int lb_smem_uniq(const MergeSmem<W>& m, int TC, int n
   return lo;
 }
 
-// The decision for one merged candidate.  Main entries keep their list slot if
-// core or reference, otherwise they survive with a nonzero population after the
-// real-weight occupation rounding.  New determinants need an initiator parent
-// (Sec. 2.1) and a nonzero amount.
+// Real-weight occupation rounding of 0 < |N| < 1 walker to 0 or +-1 walker
+// with probability |N| (per-determinant Philox word z).
 template <int W>
 __device__ __forceinline__ int64_t round_small(const Params& P, int64_t t, const Key<W>& k, int64_t p) {
   int64_t mag = iabs64(p);
@@ -695,6 +735,159 @@ __device__ __forceinline__ int64_t round_small(const Params& P, int64_t t, const
   return p;
 }
 
+// Context of one merge: the bucket's main segment and the list buffers.
+struct MergeCtx {
+  int64_t m0;           // first main-list index of the bucket segment
+  int64_t t;            // iteration number
+  const int64_t* pop;
+  const double* hd;
+  const uint8_t* fl;
+  uint64_t* okey;
+  int64_t* opop;
+  double* ohd;
+  uint8_t* ofl;
+};
+
+// Merge the sorted unique spawns [0, nu) with the main segment entries [ml, mh)
+// (segment-local indices, keys in m.mkey): candidates in key order, the keep
+// decision of each written to m.keep[rank] and scanned.  Main entries keep their
+// slot if core or reference, otherwise they survive with a nonzero population
+// after the real-weight occupation rounding.  New determinants need an
+// initiator parent (Sec. 2.1) and a nonzero amount.  Returns the number kept.
+template <int W>
+__device__ uint32_t tile_decide(const Params& P, MergeSmem<W>& m, const MergeCtx& c, int TC, int SM, int nu,
+                                int ml, int mh, uint32_t* wsum, int& nc_out) {
+  const int nm = mh - ml;
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+    Key<W> k = skey_at<W>(m, TC, j);
+    int lb = lb_smem_main<W>(m, SM, ml, mh, k);
+    bool match = lb < mh && key_eq<W>(mkey_at<W>(m, SM, lb), k);
+    m.ulb[j] = match ? -1 : lb - ml;
+    m.mscan[j] = match ? 1u : 0u;
+  }
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    Key<W> k = mkey_at<W>(m, SM, ml + i);
+    int lb = lb_smem_uniq<W>(m, TC, nu, k);
+    m.mlb[i] = lb;
+    m.mmatch[i] = (lb < nu && key_eq<W>(skey_at<W>(m, TC, lb), k)) ? lb : -1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) m.mscan[nu] = 0;
+  __syncthreads();
+  uint32_t nmatched = block_scan_excl<uint32_t>(m.mscan, nu + 1, wsum);
+  const int nc = nm + nu - (int)nmatched;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
+    int64_t gi = c.m0 + ml + i;
+    int64_t p = c.pop[gi];
+    if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
+    uint8_t f = c.fl[gi];
+    bool always = (f & (F_CORE | F_REF)) != 0;
+    if (!always) p = round_small<W>(P, c.t, mkey_at<W>(m, SM, ml + i), p);
+    m.keep[rank] = (always || p != 0) ? 1u : 0u;
+  }
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+    int lb = m.ulb[j];
+    if (lb < 0) continue;
+    int rank = lb + (j - (int)m.mscan[j]);
+    int64_t p = m.samt[j];
+    bool ok = (!P.initiator || (m.sflg[j] & 1u)) && p != 0;
+    if (ok) p = round_small<W>(P, c.t, skey_at<W>(m, TC, j), p);
+    m.keep[rank] = (ok && p != 0) ? 1u : 0u;
+  }
+  __syncthreads();
+  nc_out = nc;
+  return block_scan_excl<uint32_t>(m.keep, nc, wsum);
+}
+
+// Write the entries kept by tile_decide at out + (their rank among the kept).
+template <int W, int SYS>
+__device__ int64_t tile_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c, int TC, int SM, int nu, int ml,
+                              int mh, int nc, uint32_t nkeep, int64_t out) {
+  DevState* st = P.st;
+  const int nm = mh - ml;
+  int64_t nwsum = 0;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
+    uint32_t pos = m.keep[rank];
+    uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+    if (nx == pos) continue;
+    int64_t gi = c.m0 + ml + i;
+    int64_t p = c.pop[gi];
+    if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
+    uint8_t f = c.fl[gi];
+    Key<W> k = mkey_at<W>(m, SM, ml + i);
+    bool always = (f & (F_CORE | F_REF)) != 0;
+    if (!always) p = round_small<W>(P, c.t, k, p);
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    int64_t o = out + pos;
+    store_key<W>(c.okey, P.cap, o, k);
+    c.opop[o] = p;
+    c.ohd[o] = c.hd[gi];
+    c.ofl[o] = f & F_CORE;
+    nwsum += iabs64(p);
+  }
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+    int lb = m.ulb[j];
+    if (lb < 0) continue;
+    int rank = lb + (j - (int)m.mscan[j]);
+    uint32_t pos = m.keep[rank];
+    uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+    if (nx == pos) continue;
+    Key<W> k = skey_at<W>(m, TC, j);
+    int64_t p = round_small<W>(P, c.t, k, m.samt[j]);
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    int64_t o = out + pos;
+    store_key<W>(c.okey, P.cap, o, k);
+    c.opop[o] = p;
+    c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
+    c.ofl[o] = 0;
+    P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    nwsum += iabs64(p);
+  }
+  __syncthreads();
+  return nwsum;
+}
+
+// Decoupled look-back (single-pass chained scan) over bucket output counts.
+// Buckets are taken in ticket order, so every predecessor is owned by a running
+// CTA and publishes its count without waiting: the spin always ends, and is
+// bounded anyway.  Returns the exclusive prefix; sets *abort on failure.
+__device__ __forceinline__ unsigned long long lookback(const Params& P, int64_t b, uint32_t count, int* abort) {
+  DevState* st = P.st;
+  const unsigned long long AGG = 1ull << 62, INC = 2ull << 62, MASK = (1ull << 62) - 1;
+  unsigned long long excl = 0;
+  if (b == 0) {
+    atomicExch(&P.tile_state[0], INC | (unsigned long long)count);
+    return 0;
+  }
+  atomicExch(&P.tile_state[b], AGG | (unsigned long long)count);
+  int64_t p = b - 1;
+  long long spins = 0;
+  while (p >= 0) {
+    unsigned long long v = atomicAdd(&P.tile_state[p], 0ull);
+    unsigned long long s = v & ~MASK;
+    if (s == 0) {
+      ++spins;
+      if ((spins & 1023) == 0 && *(volatile unsigned*)&st->error) {
+        *abort = 1;   // another tile failed: give up without adding an error
+        return 0;
+      }
+      if (spins > (1ll << 22)) {
+        set_error(st, ERR_TIMEOUT);
+        *abort = 1;
+        return 0;
+      }
+      continue;
+    }
+    excl += v & MASK;
+    if (s == INC) break;
+    --p;
+  }
+  atomicExch(&P.tile_state[b], INC | (excl + count));
+  return excl;
+}
+
 template <int W, int SYS>
 __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
   DevState* st = P.st;
@@ -704,6 +897,7 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
   __shared__ int tile_id;
   __shared__ unsigned long long s_base;
   __shared__ int s_abort;
+  __shared__ int s_nsub;
   const int TC = P.tile_cap, SM = P.seg_max;
   MergeSmem<W> m;
   {
@@ -717,6 +911,7 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
     m.samt = (int64_t*)carve(sizeof(int64_t) * TC);
     m.uamt = (int64_t*)carve(sizeof(int64_t) * TC);
     m.mkey = (uint64_t*)carve(sizeof(uint64_t) * W * SM);
+    m.spl = (uint64_t*)carve(sizeof(uint64_t) * W * kSubRanges);
     m.sflg = (uint32_t*)carve(4 * TC);
     m.uid = (int32_t*)carve(4 * TC);
     m.uflg = (uint32_t*)carve(4 * TC);
@@ -725,16 +920,26 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
     m.mmatch = (int32_t*)carve(4 * SM);
     m.mlb = (int32_t*)carve(4 * SM);
     m.keep = (uint32_t*)carve(4 * (TC + SM));
+    m.rcnt = (int32_t*)carve(4 * (kSubRanges + 1));
+    m.roff = (int32_t*)carve(4 * (kSubRanges + 1));
+    m.rcur = (int32_t*)carve(4 * (kSubRanges + 1));
+    m.runiq = (int32_t*)carve(4 * (kSubRanges + 1));
+    m.rkeep = (int32_t*)carve(4 * (kSubRanges + 1));
   }
   const int64_t n = st->ndet[cur];
   const int64_t nb = st->nbuckets;
   const int64_t sb = st->sb;
-  const int64_t t = st->iter + 1;
   const int nxt = cur ^ 1;
+  MergeCtx c;
+  c.t = st->iter + 1;
+  c.pop = P.pop[cur];
+  c.hd = P.hdiag[cur];
+  c.fl = P.flags[cur];
+  c.okey = P.key[nxt];
+  c.opop = P.pop[nxt];
+  c.ohd = P.hdiag[nxt];
+  c.ofl = P.flags[nxt];
   const uint64_t* key = P.key[cur];
-  const int64_t* pop = P.pop[cur];
-  const double* hd = P.hdiag[cur];
-  const uint8_t* fl = P.flags[cur];
   int64_t nwsum = 0;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -746,159 +951,163 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
     if (b < 0 || b >= nb) break;
     const int64_t s0 = P.boff[b];
     const int64_t ns = P.bcount[b];
-    const int64_t m0 = b * sb;
-    const int nm = (int)((m0 + sb < n ? m0 + sb : n) - m0);
-    // ---- spawns of this bucket: chunked sort + reduce (duplicates collapse)
-    int nu = 0;
-    for (int64_t pos = 0; pos < ns;) {
-      int take = TC - nu;
-      if (take <= 0) {
-        if (threadIdx.x == 0) {
-          set_error(st, ERR_TILE_CAPACITY);
+    c.m0 = b * sb;
+    const int nm = (int)((c.m0 + sb < n ? c.m0 + sb : n) - c.m0);
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) m.mkey[j * SM + i] = key[j * P.cap + c.m0 + i];
+    }
+    __syncthreads();
+    if (ns <= TC) {
+      // ---- common case: all spawns of the bucket fit on chip
+      int nu = load_reduce<W>(m, TC, P.b_key, P.scap, P.b_amt, P.b_flag, nullptr, s0, s0 + ns, wsum);
+      int nc = 0;
+      uint32_t nkeep = tile_decide<W>(P, m, c, TC, SM, nu, 0, nm, wsum, nc);
+      if (threadIdx.x == 0) {
+        s_base = lookback(P, b, nkeep, &s_abort);
+        if (!s_abort && (int64_t)(s_base + nkeep) > P.cap) {
+          set_error(st, ERR_STATE_CAPACITY);
           s_abort = 1;
         }
-        break;
-      }
-      if ((int64_t)take > ns - pos) take = (int)(ns - pos);
-      for (int i = threadIdx.x; i < take; i += blockDim.x) {
-        int64_t src = s0 + pos + i;
-#pragma unroll
-        for (int j = 0; j < W; ++j) m.skey[j * TC + nu + i] = P.b_key[j * P.scap + src];
-        m.samt[nu + i] = P.b_amt[src];
-        m.sflg[nu + i] = P.b_flag[src];
+        if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + nkeep);
       }
       __syncthreads();
-      nu = sort_reduce<W>(m, TC, nu + take, wsum);
-      pos += take;
+      if (s_abort) break;
+      nwsum += tile_write<W, SYS>(P, m, c, TC, SM, nu, 0, nm, nc, nkeep, (int64_t)s_base);
+      continue;
     }
-    __syncthreads();
-    if (s_abort) break;
-    // ---- main segment keys
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    // ---- oversized bucket: split its spawns into key sub-ranges with splitters
+    // sampled from the spawns themselves, partition them into the staging
+    // arrays, reduce each sub-range on chip, keep the unique runs in the
+    // bucket's own region, then merge each run with its share of the segment.
+    {
+      int R = (int)((ns + TC / 4 - 1) / (TC / 4));
+      if (R > kSubRanges) R = kSubRanges;
+      int nsamp = R * 8 < TC ? R * 8 : TC;
+      int64_t stride = ns / nsamp;
+      for (int i = threadIdx.x; i < nsamp; i += blockDim.x) {
+        int64_t src = s0 + (int64_t)i * stride;
 #pragma unroll
-      for (int j = 0; j < W; ++j) m.mkey[j * SM + i] = key[j * P.cap + m0 + i];
-    }
-    __syncthreads();
-    // ---- match unique spawns against the segment
-    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
-      Key<W> k = skey_at<W>(m, TC, j);
-      int lb = lb_smem_main<W>(m, SM, nm, k);
-      bool match = lb < nm && key_eq<W>(mkey_at<W>(m, SM, lb), k);
-      m.ulb[j] = match ? -1 : lb;
-      m.mscan[j] = match ? 1u : 0u;
-    }
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-      Key<W> k = mkey_at<W>(m, SM, i);
-      int lb = lb_smem_uniq<W>(m, TC, nu, k);
-      m.mlb[i] = lb;
-      m.mmatch[i] = (lb < nu && key_eq<W>(skey_at<W>(m, TC, lb), k)) ? lb : -1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) m.mscan[nu] = 0;
-    __syncthreads();
-    uint32_t nmatched = block_scan_excl<uint32_t>(m.mscan, nu + 1, wsum);
-    const int nc = nm + nu - (int)nmatched;
-    // ---- pass A: keep flags by merged rank
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-      int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
-      int64_t p = pop[m0 + i];
-      if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
-      uint8_t f = fl[m0 + i];
-      bool always = (f & (F_CORE | F_REF)) != 0;
-      if (!always) p = round_small<W>(P, t, mkey_at<W>(m, SM, i), p);
-      m.keep[rank] = (always || p != 0) ? 1u : 0u;
-    }
-    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
-      int lb = m.ulb[j];
-      if (lb < 0) continue;
-      int rank = lb + (j - (int)m.mscan[j]);
-      int64_t p = m.samt[j];
-      bool ok = (!P.initiator || (m.sflg[j] & 1u)) && p != 0;
-      if (ok) p = round_small<W>(P, t, skey_at<W>(m, TC, j), p);
-      m.keep[rank] = (ok && p != 0) ? 1u : 0u;
-    }
-    __syncthreads();
-    uint32_t nkeep = block_scan_excl<uint32_t>(m.keep, nc, wsum);
-    // ---- decoupled look-back for the output offset of this bucket
-    if (threadIdx.x == 0) {
-      const unsigned long long AGG = 1ull << 62, INC = 2ull << 62, MASK = (1ull << 62) - 1;
-      unsigned long long excl = 0;
-      if (b == 0) {
-        atomicExch(&P.tile_state[0], INC | (unsigned long long)nkeep);
-      } else {
-        atomicExch(&P.tile_state[b], AGG | (unsigned long long)nkeep);
-        int64_t p = b - 1;
-        long long spins = 0;
-        while (p >= 0) {
-          unsigned long long v = atomicAdd(&P.tile_state[p], 0ull);
-          unsigned long long s = v & ~MASK;
-          if (s == 0) {
-            ++spins;
-            if (spins > (1ll << 22) || ((spins & 1023) == 0 && *(volatile unsigned*)&st->error)) {
-              set_error(st, ERR_TIMEOUT);
-              s_abort = 1;
-              break;
-            }
-            continue;
-          }
-          excl += v & MASK;
-          if (s == INC) break;
-          --p;
+        for (int j = 0; j < W; ++j) m.skey[j * TC + i] = P.b_key[j * P.scap + src];
+        m.samt[i] = 0;
+        m.sflg[i] = 0;
+      }
+      __syncthreads();
+      int nuq = sort_reduce<W>(m, TC, nsamp, wsum);
+      int nsub = R < nuq ? R : nuq;   // sub-ranges; splitters = nsub - 1 evenly spaced samples
+      for (int r = threadIdx.x; r < nsub - 1; r += blockDim.x) {
+        int at = (int)(((int64_t)(r + 1) * nuq) / nsub);
+        Key<W> k = skey_at<W>(m, TC, at);
+#pragma unroll
+        for (int j = 0; j < W; ++j) m.spl[j * kSubRanges + r] = k.w[j];
+      }
+      for (int r = threadIdx.x; r <= kSubRanges; r += blockDim.x) {
+        m.rcnt[r] = 0;
+        m.rcur[r] = 0;
+      }
+      if (threadIdx.x == 0) s_nsub = nsub;
+      __syncthreads();
+      // histogram of sub-ranges: r = number of splitters <= key
+      for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        Key<W> k = load_key<W>(P.b_key, P.scap, s0 + i);
+        int lo = 0, hi = nsub - 1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (key_le<W>(spl_at<W>(m, mid), k)) lo = mid + 1;
+          else hi = mid;
         }
-        if (!s_abort) atomicExch(&P.tile_state[b], INC | (excl + nkeep));
+        atomicAdd(&m.rcnt[lo], 1);
       }
-      s_base = excl;
-      if (b == nb - 1) st->ndet[nxt] = (int64_t)(excl + nkeep);
-      if ((int64_t)(excl + nkeep) > P.cap) {
-        set_error(st, ERR_STATE_CAPACITY);
-        s_abort = 1;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int r = 0; r < nsub; ++r) {
+          m.roff[r] = acc;
+          acc += m.rcnt[r];
+        }
+      }
+      __syncthreads();
+      // partition into the staging arrays (free after the scatter)
+      for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        Key<W> k = load_key<W>(P.b_key, P.scap, s0 + i);
+        int lo = 0, hi = nsub - 1;
+        while (lo < hi) {
+          int mid = (lo + hi) >> 1;
+          if (key_le<W>(spl_at<W>(m, mid), k)) lo = mid + 1;
+          else hi = mid;
+        }
+        int64_t dst = s0 + m.roff[lo] + atomicAdd(&m.rcur[lo], 1);
+        store_key<W>(P.s_key, P.scap, dst, k);
+        P.s_amt[dst] = P.b_amt[s0 + i];
+        P.s_meta[dst] = P.b_flag[s0 + i];
+      }
+      __syncthreads();
+      // pass 1: reduce each sub-range, store its unique run, count survivors
+      int64_t uoff = 0;
+      uint32_t total = 0;
+      for (int r = 0; r < nsub; ++r) {
+        int64_t beg = s0 + m.roff[r];
+        int nu = load_reduce<W>(m, TC, P.s_key, P.scap, P.s_amt, nullptr, P.s_meta, beg, beg + m.rcnt[r], wsum);
+        if (nu < 0) {
+          if (threadIdx.x == 0) {
+            set_error(st, ERR_TILE_CAPACITY);
+            s_abort = 1;
+          }
+          __syncthreads();
+          break;
+        }
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+          int64_t dst = s0 + uoff + i;
+#pragma unroll
+          for (int j = 0; j < W; ++j) P.b_key[j * P.scap + dst] = m.skey[j * TC + i];
+          P.b_amt[dst] = m.samt[i];
+          P.b_flag[dst] = (uint8_t)(m.sflg[i] & 1u);
+        }
+        int ml = r == 0 ? 0 : lb_smem_main<W>(m, SM, 0, nm, spl_at<W>(m, r - 1));
+        int mh = r == nsub - 1 ? nm : lb_smem_main<W>(m, SM, 0, nm, spl_at<W>(m, r));
+        int nc = 0;
+        uint32_t k = tile_decide<W>(P, m, c, TC, SM, nu, ml, mh, wsum, nc);
+        if (threadIdx.x == 0) {
+          m.runiq[r] = nu;
+          m.rkeep[r] = (int)k;
+        }
+        uoff += nu;
+        total += k;
+        __syncthreads();
+      }
+      if (s_abort) break;
+      if (threadIdx.x == 0) {
+        s_base = lookback(P, b, total, &s_abort);
+        if (!s_abort && (int64_t)(s_base + total) > P.cap) {
+          set_error(st, ERR_STATE_CAPACITY);
+          s_abort = 1;
+        }
+        if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + total);
+      }
+      __syncthreads();
+      if (s_abort) break;
+      // pass 2: reload each unique run, decide again (same result), write
+      int64_t out = (int64_t)s_base;
+      uoff = 0;
+      for (int r = 0; r < s_nsub; ++r) {
+        int nu = m.runiq[r];
+        for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+          int64_t src = s0 + uoff + i;
+#pragma unroll
+          for (int j = 0; j < W; ++j) m.skey[j * TC + i] = P.b_key[j * P.scap + src];
+          m.samt[i] = P.b_amt[src];
+          m.sflg[i] = P.b_flag[src];
+        }
+        __syncthreads();
+        int ml = r == 0 ? 0 : lb_smem_main<W>(m, SM, 0, nm, spl_at<W>(m, r - 1));
+        int mh = r == s_nsub - 1 ? nm : lb_smem_main<W>(m, SM, 0, nm, spl_at<W>(m, r));
+        int nc = 0;
+        uint32_t k = tile_decide<W>(P, m, c, TC, SM, nu, ml, mh, wsum, nc);
+        nwsum += tile_write<W, SYS>(P, m, c, TC, SM, nu, ml, mh, nc, k, out);
+        out += k;
+        uoff += nu;
       }
     }
-    __syncthreads();
-    if (s_abort) break;
-    const int64_t base = (int64_t)s_base;
-    uint64_t* okey = P.key[nxt];
-    int64_t* opop = P.pop[nxt];
-    double* ohd = P.hdiag[nxt];
-    uint8_t* ofl = P.flags[nxt];
-    // ---- pass B: write the surviving entries
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-      int rank = i + m.mlb[i] - (int)m.mscan[m.mlb[i]];
-      uint32_t pos = m.keep[rank];
-      uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
-      if (nx == pos) continue;
-      int64_t p = pop[m0 + i];
-      if (m.mmatch[i] >= 0) p += m.samt[m.mmatch[i]];
-      uint8_t f = fl[m0 + i];
-      Key<W> k = mkey_at<W>(m, SM, i);
-      bool always = (f & (F_CORE | F_REF)) != 0;
-      if (!always) p = round_small<W>(P, t, k, p);
-      if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
-      int64_t o = base + pos;
-      store_key<W>(okey, P.cap, o, k);
-      opop[o] = p;
-      ohd[o] = hd[m0 + i];
-      ofl[o] = f & F_CORE;
-      nwsum += iabs64(p);
-    }
-    for (int j = threadIdx.x; j < nu; j += blockDim.x) {
-      int lb = m.ulb[j];
-      if (lb < 0) continue;
-      int rank = lb + (j - (int)m.mscan[j]);
-      uint32_t pos = m.keep[rank];
-      uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
-      if (nx == pos) continue;
-      Key<W> k = skey_at<W>(m, TC, j);
-      int64_t p = round_small<W>(P, t, k, m.samt[j]);
-      if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
-      int64_t o = base + pos;
-      store_key<W>(okey, P.cap, o, k);
-      opop[o] = p;
-      ohd[o] = __dsub_rn(h_diag<W, SYS>(P.sys, k), st->e_ref);
-      ofl[o] = 0;
-      nwsum += iabs64(p);
-    }
-    __syncthreads();
   }
   int64_t tot = block_sum<int64_t>(nwsum, sh64);
   if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)tot);
@@ -931,6 +1140,7 @@ static __global__ void k_finalize(Params P, int cur) {
   r.ndet = st->ndet[cur ^ 1];
   r.natt = st->natt;
   r.nspawn = st->nspawn;
+  st->nspawn_prev = st->nspawn;
   I128 num{(uint64_t)st->num[0], (int64_t)st->num[1]};
   r.num_lo = num.lo;
   r.num_hi = num.hi;
@@ -942,6 +1152,20 @@ static __global__ void k_finalize(Params P, int cur) {
   st->num[0] = 0;
   st->num[1] = 0;
   st->nw_post = 0;
+}
+
+// diagonal elements of the determinants the merge created (list in natt[])
+template <int W, int SYS>
+__global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  const int nxt = cur ^ 1;
+  const int64_t nn = st->nnew;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = P.natt[i];
+    Key<W> k = load_key<W>(P.key[nxt], P.cap, o);
+    P.hdiag[nxt][o] = __dsub_rn(h_diag<W, SYS>(P.sys, k), st->e_ref);
+  }
 }
 
 // ------------------------------------------------------------------ utilities

@@ -110,29 +110,47 @@ __global__ void k_sel_gather(Params P, int cur, uint64_t* core_key, int64_t ncor
 }
 
 // ------------------------------------------------------------------ launchers
+// One iteration.  With `ev` non-null, ev[k] is recorded before phase k and
+// ev[kPhases] after the last one (phases: det pass, attempt scan, split, core,
+// attempts, bucket scan, scatter, merge, new diagonals, finalize).
 template <int W, int SYS>
-void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s) {
+void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_t* ev) {
   Params& P = E.P;
   DevState* st = P.st;
+  auto mark = [&](int k) {
+    if (ev) cudaEventRecord(ev[k], s);
+  };
+  mark(0);
   k_det_pass<W, SYS><<<kScanBlocks, kScanThreads, 0, s>>>(P, cur);
+  mark(1);
   k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, natt)), st);
   k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, s>>>(
       P.natt, P.att_begin, st_field_i64(st, offsetof(DevState, ndet) + 8 * cur), P.part, st);
+  mark(2);
   k_split<W><<<kScanBlocks, 256, 0, s>>>(P, cur);
+  mark(3);
   if (core && P.ncore > 0) {
     int nb = (P.ncore + 255) / 256;
     k_core_locate<W><<<nb, 256, 0, s>>>(P, cur);
     k_core_spmv<<<(int)(((int64_t)P.ncore * 32 + 255) / 256), 256, 0, s>>>(P, cur);
     k_core_apply<<<nb, 256, 0, s>>>(P, cur);
   }
+  mark(4);
   k_attempt<W, SYS><<<E.attempt_grid, 256, 0, s>>>(P, cur);
+  mark(5);
   int64_t* nbk = st_field_i64(st, offsetof(DevState, nbuckets));
   k_scan_reduce<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, nbk, P.part, st);
   k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, scan_total)), st);
   k_scan_apply<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, P.boff, nbk, P.part, st);
+  mark(6);
   k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
+  mark(7);
   k_merge<W, SYS><<<E.merge_grid, 512, E.merge_smem_bytes, s>>>(P, cur);
+  mark(8);
+  k_new_hdiag<W, SYS><<<E.attempt_grid, 256, 0, s>>>(P, cur);
+  mark(9);
   k_finalize<<<1, 32, 0, s>>>(P, cur);
+  mark(10);
 }
 
 template <int W, int SYS>

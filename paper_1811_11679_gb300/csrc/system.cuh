@@ -46,6 +46,11 @@ struct SysDev {
   const uint64_t* hb_cum;
   uint32_t psingle_thr;
   double p_single, p_double;
+  // diagonal tables: orb_diag[k] = h_kk (molecule, spin orbitals) or |k|^2/2
+  // (UEG, spatial); pair_diag = (kk|ll) - (kl|lk) (molecule, nspin^2) or the
+  // exchange kernel 4 pi / (Omega |k_k - k_l|^2) (UEG, norb^2)
+  const double* orb_diag;
+  const double* pair_diag;
 };
 
 __device__ __forceinline__ int tri(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
@@ -90,7 +95,7 @@ __device__ double h_diag(const SysDev& s, const Key<W>& d) {
     return __dmul_rn(s.U, (double)dbl);
   } else if (SYS == SYS_UEG) {
     double e = 0.0;
-    HANDE_FOR_OCC(W, d, p, { e = __dadd_rn(e, __dmul_rn(s.kfac, (double)__ldg(&s.kvec[p >> 1]).w)); })
+    HANDE_FOR_OCC(W, d, p, { e = __dadd_rn(e, __ldg(&s.orb_diag[p >> 1])); })
     HANDE_FOR_OCC(W, d, p, {
       // partners l > p with the same spin
       Key<W> rest = d;
@@ -101,12 +106,13 @@ __device__ double h_diag(const SysDev& s, const Key<W>& d) {
         else if (lo > 0) rest.w[jj] &= ~((1ull << lo) - 1);
         rest.w[jj] &= (p & 1) ? 0xAAAAAAAAAAAAAAAAull : 0x5555555555555555ull;
       }
-      HANDE_FOR_OCC(W, rest, l, { e = __dsub_rn(e, ueg_v(s, ueg_dist2(s, p >> 1, l >> 1))); })
+      const double* row = s.pair_diag + (size_t)(p >> 1) * s.norb;
+      HANDE_FOR_OCC(W, rest, l, { e = __dsub_rn(e, __ldg(&row[l >> 1])); })
     })
     return e;
   } else {
     double e1 = 0.0, e2 = 0.0;
-    HANDE_FOR_OCC(W, d, p, { e1 = __dadd_rn(e1, h1_so(s, p, p)); })
+    HANDE_FOR_OCC(W, d, p, { e1 = __dadd_rn(e1, __ldg(&s.orb_diag[p])); })
     HANDE_FOR_OCC(W, d, p, {
       Key<W> rest = d;
 #pragma unroll
@@ -115,11 +121,8 @@ __device__ double h_diag(const SysDev& s, const Key<W>& d) {
         if (lo >= 64) rest.w[jj] = 0;
         else if (lo > 0) rest.w[jj] &= ~((1ull << lo) - 1);
       }
-      HANDE_FOR_OCC(W, rest, q, {
-        double j_ = eri_sp(s, p >> 1, p >> 1, q >> 1, q >> 1);
-        double k_ = ((p ^ q) & 1) ? 0.0 : eri_sp(s, p >> 1, q >> 1, q >> 1, p >> 1);
-        e2 = __dadd_rn(e2, __dsub_rn(j_, k_));
-      })
+      const double* row = s.pair_diag + (size_t)p * s.nspin;
+      HANDE_FOR_OCC(W, rest, q, { e2 = __dadd_rn(e2, __ldg(&row[q])); })
     })
     return __dadd_rn(__dadd_rn(e1, e2), s.ecore);
   }

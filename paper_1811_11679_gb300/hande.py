@@ -42,7 +42,7 @@ class _Qmc(C.Structure):
                 ("p_single", C.c_double), ("shift_period", C.c_int), ("initiator", C.c_int),
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int), ("semi_stoch_start", C.c_int),
                 ("seed", C.c_uint64), ("replica", C.c_uint64), ("state_capacity", C.c_int64),
-                ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int)]
+                ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int), ("tile_capacity", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -59,9 +59,15 @@ class _Estimate(C.Structure):
                 ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64)]
 
 
+class _Diag(C.Structure):
+    _fields_ = [("error_bits", C.c_uint32), ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64),
+                ("nbuckets", C.c_int64), ("bucket_main", C.c_int64), ("max_bucket_spawns", C.c_int64),
+                ("tile_capacity", C.c_int64), ("ncore", C.c_int64)]
+
+
 # names declared in include/hande.h, in order
-EXPORTS = ["hande_init_system", "hande_iterate", "hande_synchronize", "hande_estimators", "hande_get_walkers",
-           "hande_set_walkers", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
+EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
+           "hande_set_walkers", "hande_diagnostics", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -88,6 +94,7 @@ def load(build_if_needed: bool = True):
         lib.hande_init_system.argtypes = [C.POINTER(_System), C.POINTER(_Qmc), C.POINTER(_Allocator), P,
                                           C.POINTER(P)]
         lib.hande_iterate.argtypes = [P, C.c_int]
+        lib.hande_iterate_timed.argtypes = [P, C.c_int, C.POINTER(C.c_float), C.c_int]
         lib.hande_synchronize.argtypes = [P]
         lib.hande_estimators.argtypes = [P, C.POINTER(_Estimate), C.c_int, C.POINTER(C.c_int)]
         lib.hande_get_walkers.argtypes = [P, u64p, i64p, dp, C.POINTER(C.c_uint8), C.c_int64, i64p]
@@ -99,7 +106,8 @@ def load(build_if_needed: bool = True):
         lib.hande_destroy.restype = None
         lib.hande_last_error.argtypes = [P]
         lib.hande_last_error.restype = C.c_char_p
-        for name in EXPORTS[:7]:
+        lib.hande_diagnostics.argtypes = [P, C.POINTER(_Diag)]
+        for name in EXPORTS[:9]:
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -165,6 +173,7 @@ class Hande:
         q.state_capacity = int(qmc.get("state_capacity", 0))
         q.spawn_capacity = int(qmc.get("spawn_capacity", 0))
         q.record_capacity = int(qmc.get("record_capacity", 0))
+        q.tile_capacity = int(qmc.get("tile_capacity", 0))
         self.W = s.key_words
         alloc_p = None
         if stream is None or torch_memory:
@@ -190,6 +199,21 @@ class Hande:
 
     def iterate(self, n: int = 1) -> None:
         self._check(self._lib.hande_iterate(self._h, int(n)), "hande_iterate")
+
+    PHASES = ("det_pass", "attempt_scan", "split", "core", "attempt", "bucket_scan", "scatter", "merge",
+              "new_hdiag", "finalize")
+
+    def iterate_timed(self, n: int = 1) -> dict:
+        """n iterations launched kernel by kernel with CUDA events between the
+        phases; returns summed device milliseconds per phase."""
+        buf = (C.c_float * len(self.PHASES))()
+        self._check(self._lib.hande_iterate_timed(self._h, int(n), buf, len(self.PHASES)), "hande_iterate_timed")
+        return {k: float(v) for k, v in zip(self.PHASES, buf)}
+
+    def diagnostics(self) -> dict:
+        d = _Diag()
+        self._check(self._lib.hande_diagnostics(self._h, C.byref(d)), "hande_diagnostics")
+        return {name: getattr(d, name) for name, _ in _Diag._fields_}
 
     def synchronize(self) -> None:
         self._check(self._lib.hande_synchronize(self._h), "hande_synchronize")

@@ -25,11 +25,14 @@ import numpy as np
 def molecule_integrals(norb: int, seed: int = 11):
     """Seeded one- and two-electron integrals with 8-fold symmetry.
 
+    Orbitals behave like localised functions on a line: products p*q decay
+    with |p-q| and interactions between products with their separation.
     h_pq  : diagonal -2 + 0.15 p (Fock-like ordering), off-diagonal
             g exp(-|p-q|/4), g ~ U(-0.1, 0.1), symmetric.
-    (pq|rs): Coulomb (pp|rr) = 0.5 exp(-|p-r|/8) + 0.05 u, u ~ U(0, 1) (> 0);
-            exchange-like (pq|pq) = |g| exp(-|p-q|/2) (> 0);
-            everything else g exp(-(|p-q| + |r-s|)/4), g ~ U(-0.1, 0.1).
+    (pq|rs): Coulomb (pp|rr) = 0.25 exp(-|p-r|/8) + 0.05 u, u ~ U(0, 1) (> 0);
+            exchange-like (pq|pq) = |g| exp(-|p-q|/2), g ~ U(-0.1, 0.1) (> 0);
+            everything else g exp(-(|p-q| + |r-s|)/2 - |p+q-r-s|/4),
+            g ~ U(-0.05, 0.05).
     Returns (h1[norb, norb], eri[norb, norb, norb, norb]) in chemist order.
     """
     rng = np.random.Generator(np.random.Philox(seed))
@@ -45,11 +48,12 @@ def molecule_integrals(norb: int, seed: int = 11):
     for ia, (p, q) in enumerate(pairs):
         for (r, s) in pairs[: ia + 1]:
             if p == q and r == s:
-                v = 0.5 * np.exp(-abs(p - r) / 8.0) + 0.05 * rng.uniform(0.0, 1.0)
+                v = 0.25 * np.exp(-abs(p - r) / 8.0) + 0.05 * rng.uniform(0.0, 1.0)
             elif (p, q) == (r, s):
                 v = abs(rng.uniform(-0.1, 0.1)) * np.exp(-abs(p - q) / 2.0)
             else:
-                v = rng.uniform(-0.1, 0.1) * np.exp(-(abs(p - q) + abs(r - s)) / 4.0)
+                v = rng.uniform(-0.05, 0.05) * np.exp(-(abs(p - q) + abs(r - s)) / 2.0
+                                                      - abs(p + q - r - s) / 4.0)
             for (a, b) in ((p, q), (q, p)):
                 for (c, d) in ((r, s), (s, r)):
                     eri[a, b, c, d] = v
@@ -109,3 +113,98 @@ def workload(name: str, **overrides):
     q = qf()
     q.update(overrides)
     return sysf(), q
+
+
+def reference_key(system: dict) -> np.ndarray:
+    """Reference determinant as key words: Neel (alpha on even sites, beta on odd
+    sites) for the real-space Hubbard model, aufbau otherwise."""
+    W = int(system["key_words"])
+    bits = 0
+    na, nb = int(system["nalpha"]), int(system["nbeta"])
+    if system["kind"] == "hubbard":
+        for k in range(na):
+            bits |= 1 << (2 * (2 * k))
+        for k in range(nb):
+            bits |= 1 << (2 * (2 * k + 1) + 1)
+    else:
+        for k in range(na):
+            bits |= 1 << (2 * k)
+        for k in range(nb):
+            bits |= 1 << (2 * k + 1)
+    return np.array([(bits >> (64 * j)) & ((1 << 64) - 1) for j in range(W)], dtype=np.uint64)
+
+
+def _choose(rng, m: int, pool: np.ndarray, k: int) -> np.ndarray:
+    """k distinct entries of `pool` per row (m rows), uniformly at random."""
+    if k == 0:
+        return np.zeros((m, 0), dtype=np.int64)
+    r = rng.random((m, len(pool)), dtype=np.float32)
+    if k >= len(pool):
+        return np.broadcast_to(pool, (m, len(pool))).copy()
+    return pool[np.argpartition(r, k - 1, axis=1)[:, :k]]
+
+
+def synthetic_walkers(system: dict, n_det: int, n_walkers: float, seed: int = 21,
+                      ref_fraction: float = 0.1, levels=(0.05, 0.45, 0.3, 0.2)):
+    """A seeded walker list with the shape of a converged large run: the reference
+    holds `ref_fraction` of the walkers; the other n_det - 1 determinants are
+    random spin-conserving 1-4-fold excitations of it (level probabilities
+    `levels`), with heavy-tailed (Pareto, shape 1.2) populations of at least one
+    walker and random signs.  Returns (keys[n, W] ascending, pops int64 fixed point).
+    Only random numbers and bit patterns: no Hamiltonian is evaluated."""
+    W = int(system["key_words"])
+    nspin = 2 * int(system["norb"])
+    rng = np.random.Generator(np.random.Philox(seed))
+    d0 = reference_key(system)
+    bit = lambda p: (int(d0[p // 64]) >> (p % 64)) & 1
+    occ = [np.array([p for p in range(s, nspin, 2) if bit(p)], dtype=np.int64) for s in (0, 1)]
+    vir = [np.array([p for p in range(s, nspin, 2) if not bit(p)], dtype=np.int64) for s in (0, 1)]
+    cap = [min(len(occ[s]), len(vir[s])) for s in (0, 1)]
+    lv = np.asarray(levels, dtype=np.float64)
+    lv = lv / lv.sum()
+    want = n_det - 1
+    found = np.zeros((0, W), dtype=np.uint64)
+    while len(found) < want:
+        m = int(min(2_000_000, (want - len(found)) * 1.3 + 1000))
+        level = rng.choice(np.arange(1, len(lv) + 1), size=m, p=lv)
+        lo = np.maximum(0, level - cap[1])
+        hi = np.minimum(level, cap[0])
+        ok = hi >= lo
+        na = lo + np.floor(rng.random(m) * (hi - lo + 1)).astype(np.int64)
+        nb = level - na
+        keys = np.tile(d0, (m, 1))
+        for a in range(cap[0] + 1):
+            for b in range(cap[1] + 1):
+                rows = np.nonzero(ok & (na == a) & (nb == b))[0]
+                if len(rows) == 0:
+                    continue
+                flips = [_choose(rng, len(rows), occ[0], a), _choose(rng, len(rows), vir[0], a),
+                         _choose(rng, len(rows), occ[1], b), _choose(rng, len(rows), vir[1], b)]
+                pos = np.concatenate(flips, axis=1)
+                sub = keys[rows]
+                for c in range(pos.shape[1]):
+                    word = pos[:, c] // 64
+                    mask = np.left_shift(np.uint64(1), (pos[:, c] % 64).astype(np.uint64))
+                    for j in range(W):
+                        sub[:, j] ^= np.where(word == j, mask, np.uint64(0))
+                keys[rows] = sub
+        keys = np.concatenate([found, keys[ok]])
+        order = np.lexsort([keys[:, j] for j in range(W)])
+        keys = keys[order]
+        fresh = np.ones(len(keys), dtype=bool)
+        fresh[1:] = np.any(keys[1:] != keys[:-1], axis=1)
+        found = keys[fresh]
+        found = found[~np.all(found == d0[None, :], axis=1)]
+    pick = np.sort(rng.choice(len(found), size=want, replace=False))
+    allk = np.concatenate([found[pick], d0[None, :]])
+    allk = allk[np.lexsort([allk[:, j] for j in range(W)])]   # last key = most significant word
+    F = float(1 << 32)
+    is0 = np.all(allk == d0[None, :], axis=1)
+    extra = rng.pareto(1.2, size=len(allk))
+    extra[is0] = 0.0
+    spare = max((1.0 - ref_fraction) * n_walkers - (len(allk) - 1), 0.0)
+    mag = 1.0 + extra * (spare / extra.sum())
+    pops = np.rint(mag * F).astype(np.int64)
+    pops *= rng.choice(np.array([-1, 1], dtype=np.int64), size=len(pops))
+    pops[is0] = int(round(ref_fraction * n_walkers * F))
+    return allk, pops

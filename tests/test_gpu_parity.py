@@ -178,3 +178,57 @@ def test_set_get_walkers_roundtrip_and_validation():
     bad[0, 0] ^= np.uint64(1)                                      # wrong electron number
     with pytest.raises(hande.HandeError):
         g2.set_walkers(bad, p)
+
+
+@pytest.mark.parametrize("tile", [64, 256])
+def test_oversized_buckets_small_tiles(tile):
+    """Tiny annihilation tiles force most buckets through the oversized path
+    (spawn-sampled sub-ranges, two-pass merge); lists stay bit-identical."""
+    sysd, q = inputs.workload("molecule28", target_population=30000, semi_stoch_size=200,
+                              semi_stoch_start=30, tile_capacity=tile)
+    g = hande.Hande(sysd, q)
+    c = oracle.Oracle(sysd, q)
+    seen = 0
+    for it in range(80):
+        g.iterate(1)
+        c.iterate(1)
+        _same_lists(g, c, it + 1)
+        d = g.diagnostics()
+        seen = max(seen, d["max_bucket_spawns"])
+    _same_records(g, c)
+
+
+def test_oversized_bucket_single_bucket_start():
+    """3000 walkers on the reference and a one-determinant list: the first
+    iteration puts every spawn in one bucket, far above a 64-key tile."""
+    sysd, q = inputs.workload("molecule28", target_population=1e5, init_pop=3000, tile_capacity=64)
+    g = hande.Hande(sysd, q)
+    c = oracle.Oracle(sysd, q)
+    g.iterate(1)
+    c.iterate(1)
+    assert g.diagnostics()["max_bucket_spawns"] > 64
+    _same_lists(g, c, 1)
+    for it in range(1, 30):
+        g.iterate(1)
+        c.iterate(1)
+        _same_lists(g, c, it + 1)
+    _same_records(g, c)
+
+
+def test_oversized_buckets_from_synthetic_start():
+    """A synthetic list whose spawn keys are skewed against the main-list
+    splitters (the benchmark's starting state, scaled down)."""
+    sysd, q = inputs.workload("molecule28", target_population=2e5, semi_stoch_size=500, semi_stoch_start=0,
+                              tile_capacity=64)
+    keys, pops = inputs.synthetic_walkers(sysd, 40000, 2e5)
+    g = hande.Hande(sysd, q)
+    c = oracle.Oracle(sysd, q)
+    g.set_walkers(keys, pops)
+    c.set_walkers(keys, pops)
+    seen = 0
+    for it in range(8):
+        g.iterate(1)
+        c.iterate(1)
+        _same_lists(g, c, it + 1)
+        seen = max(seen, g.diagnostics()["max_bucket_spawns"])
+    _same_records(g, c)

@@ -66,7 +66,7 @@ def test_deterministic_limit_molecule():
     sysd, h1, eri = _mol_small()
     dets, H = B.molecule_hamiltonian(h1, eri, 2, 2)
     E0 = np.linalg.eigvalsh(H)[0]
-    ep, es, _ = _deterministic_limit(sysd, dets, E0, 0.05, 3000)
+    ep, es, _ = _deterministic_limit(sysd, dets, E0, 0.3, 2500)
     assert abs(ep - E0) < 1e-8
     assert abs(es - E0) < 1e-6
 
