@@ -196,6 +196,27 @@ typedef struct {
 } hande_diag;
 hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out);
 
+/* No-allocation projected-energy sums.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they
+ * need the estimator -- code under CUDA stream capture, code in stream host
+ * callbacks, and frameworks that fix their device-memory budget up front.
+ * It computes, for the walker list given in caller-owned DEVICE arrays,
+ *   d_out[0] = sum |N_i|, d_out[1] = N on the reference determinant,
+ *   d_out[2], d_out[3] = lo, hi words of the exact 128-bit numerator
+ *                         sum_{j != ref} N_j H_0j * 2^16 (as in hande_estimate),
+ * with d_keys[n*key_words] (row-major, word 0 first per walker, any order) and
+ * d_pops[n] (fixed point), asynchronously on the context's stream.  It calls no
+ * allocation routine: its per-block partial sums use one fixed device array
+ * of 4096 slots (128 KiB, held by every device that loads the library until
+ * the process exits), so n may be at most 16,777,216 (4096 x 4096); larger n
+ * returns HANDE_ERR_CAPACITY.  Every call shares that array and overwrites the
+ * slots it uses, so calls in flight at the same time (on different streams)
+ * race.  The first call on each device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture. */
+hande_status hande_estimate_noalloc(hande_ctx* ctx, const uint64_t* d_keys, const int64_t* d_pops, int64_t n,
+                                    int64_t* d_out);
+
 /* E_ref = H_00 of the reference determinant, and its key (key_words words). */
 hande_status hande_reference(hande_ctx* ctx, double* e_ref, uint64_t* key);
 

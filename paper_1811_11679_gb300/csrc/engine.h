@@ -65,3 +65,8 @@ struct Engine {
 };
 
 }  // namespace hande
+
+// the opaque context of the C ABI
+struct hande_ctx {
+  hande::Engine E;
+};

@@ -16,10 +16,6 @@
 
 using namespace hande;
 
-struct hande_ctx {
-  Engine E;
-};
-
 namespace {
 
 const double kPi = 3.14159265358979323846;

@@ -67,7 +67,7 @@ class _Diag(C.Structure):
 
 # names declared in include/hande.h, in order
 EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
-           "hande_set_walkers", "hande_diagnostics", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
+           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -107,7 +107,8 @@ def load(build_if_needed: bool = True):
         lib.hande_last_error.argtypes = [P]
         lib.hande_last_error.restype = C.c_char_p
         lib.hande_diagnostics.argtypes = [P, C.POINTER(_Diag)]
-        for name in EXPORTS[:9]:
+        lib.hande_estimate_noalloc.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+        for name in EXPORTS[:10]:
             getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
@@ -209,6 +210,12 @@ class Hande:
         buf = (C.c_float * len(self.PHASES))()
         self._check(self._lib.hande_iterate_timed(self._h, int(n), buf, len(self.PHASES)), "hande_iterate_timed")
         return {k: float(v) for k, v in zip(self.PHASES, buf)}
+
+    def estimate_noalloc(self, d_keys: int, d_pops: int, n: int, d_out: int) -> None:
+        """Projected-energy sums of a walker list in device memory (pointers as
+        ints), written to d_out[4] on the context's stream; allocates nothing."""
+        self._check(self._lib.hande_estimate_noalloc(self._h, C.c_void_p(d_keys), C.c_void_p(d_pops), int(n),
+                                                     C.c_void_p(d_out)), "hande_estimate_noalloc")
 
     def diagnostics(self) -> dict:
         d = _Diag()
