@@ -289,6 +289,28 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: a seeded synthetic list of 4e6 determinants
+    (8e6 walkers; main list and spawn arrays larger than L2) set on the device,
+    then 3 + 3 iterations; few kernel launches precede the captured ones."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande, inputs
+    torch.cuda.set_device(0)
+    sysd, q = inputs.workload(WORKLOAD, target_population=7e6, semi_stoch_size=CORE, semi_stoch_start=0,
+                              state_capacity=12_000_000, spawn_capacity=16_000_000)
+    keys, pops = inputs.synthetic_walkers(sysd, 4_000_000, 8e6)
+    eng = hande.Hande(sysd, q)
+    eng.set_walkers(keys, pops)
+    eng.iterate(3)
+    eng.iterate(3)
+    eng.synchronize()
+    r = eng.estimators()
+    print(json.dumps({"profile_case": True, "ndet": int(r["ndet"][-1]), "natt": int(r["natt"][-1]),
+                      "nspawn": int(r["nspawn"][-1])}))
+    eng.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -296,10 +318,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small synthetic-start case for ncu captures (no timing output)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
