@@ -99,7 +99,7 @@ def _load():
         lib.orc_hdiag.restype = C.c_double
         lib.orc_hij.argtypes = [P, u64p, u64p]
         lib.orc_hij.restype = C.c_double
-        lib.orc_generate.argtypes = [P, u64p, u64p, u64p, dp, dp]
+        lib.orc_generate.argtypes = [P, u64p, u64p, u64p, dp, dp, dp]
         lib.orc_generate.restype = C.c_int
         lib.orc_enumerate.argtypes = [P, u64p, u64p, dp, C.c_int64]
         lib.orc_enumerate.restype = C.c_int64
@@ -259,10 +259,12 @@ class Oracle:
         w, wp = _u64(np.asarray(words).reshape(4))
         child = np.zeros(self.W, dtype=np.uint64)
         pg, hv = C.c_double(), C.c_double()
+        inv = np.zeros(2, dtype=np.float64)
         ok = self._lib.orc_generate(self._h, kp, wp, child.ctypes.data_as(C.POINTER(C.c_uint64)),
-                                    C.byref(pg), C.byref(hv))
+                                    C.byref(pg), C.byref(hv), inv.ctypes.data_as(C.POINTER(C.c_double)))
         if not ok:
             return None
+        self.last_inv = (float(inv[0]), float(inv[1]))
         return child, pg.value, hv.value
 
     def enumerate(self, key):

@@ -403,6 +403,9 @@ struct Excit {
     Det child;
     double pgen;
     double hij;
+    /* 1/p_gen as two factors inv_a * inv_b, each exact or one rounding of a
+     * ratio of the generator's counts and table widths */
+    double inv_a, inv_b;
 };
 
 /* pair index -> (i, j), i < j, with P = j(j-1)/2 + i */
@@ -430,6 +433,8 @@ Excit gen_hubbard(const Ctx& c, const Det& d, const uint64_t w[4]) {
     int q = 2 * ns + spin;
     if (occ_bit(d, q)) return e;
     e.pgen = 1.0 / (2.0 * (double)n);
+    e.inv_a = 2.0 * (double)n;
+    e.inv_b = 1.0;
     e.hij = h_single(c, d, p, q);
     e.child = d;
     flip_bit(e.child, p);
@@ -458,6 +463,8 @@ Excit gen_ueg(const Ctx& c, const Det& d, const uint64_t w[4]) {
     if (a == b || occ_bit(d, a) || occ_bit(d, b)) return e;
     double ways = ((p & 1) == (q & 1)) ? 2.0 : 1.0;
     e.pgen = ways / ((double)npairs * (double)c.norb);
+    e.inv_a = ((double)npairs * (double)c.norb) / ways;
+    e.inv_b = 1.0;
     int lo = a < b ? a : b, hi = a < b ? b : a;
     e.hij = h_double(c, d, p, q, lo, hi);
     e.child = d;
@@ -484,6 +491,8 @@ Excit gen_heat_bath(const Ctx& c, const Det& d, const uint64_t w[4]) {
         if (empty.empty()) return e;
         int a = empty[draw_index(w[2], (uint64_t)empty.size())];
         e.pgen = c.p_single / ((double)n * (double)empty.size());
+        e.inv_a = ((double)n * (double)empty.size()) / c.p_single;
+        e.inv_b = 1.0;
         e.hij = h_single(c, d, i, a);
         e.child = d;
         flip_bit(e.child, i); flip_bit(e.child, a);
@@ -500,16 +509,20 @@ Excit gen_heat_bath(const Ctx& c, const Det& d, const uint64_t w[4]) {
     while (k + 1 < tab.size() && !(w[2] < tab[k].cum)) ++k;
     int a = tab[k].a, b = tab[k].b;
     if (occ_bit(d, a) || occ_bit(d, b)) return e;
-    double pk;
+    double pk, inv_pk;
     if (tab.size() == 1) {
         pk = 1.0;
+        inv_pk = 1.0;
     } else {
         uint64_t prev = k == 0 ? 0 : tab[k - 1].cum;
         uint64_t width = (k + 1 == tab.size()) ? (0 - prev) : (tab[k].cum - prev);
         pk = (double)width * 0x1p-64;
+        inv_pk = 18446744073709551616.0 / (double)width;
     }
     double pg = c.p_double / (double)npairs;
     e.pgen = pg * pk;
+    e.inv_a = (double)npairs / c.p_double;
+    e.inv_b = inv_pk;
     e.hij = h_double(c, d, p, q, a, b);
     e.child = d;
     flip_bit(e.child, p); flip_bit(e.child, q);
@@ -673,7 +686,8 @@ void iterate_once(Ctx& c) {
             if (ex.null) continue;
             if (ex.hij == 0.0) continue;
             if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
-            double m = (c.tau * fabs(ex.hij)) / ex.pgen;
+            /* spawn weight tau |H_ij| / p_gen, as a product with the reciprocal factors */
+            double m = ((c.tau * fabs(ex.hij)) * ex.inv_a) * ex.inv_b;
             int64_t q;
             if (!c.real_amp) {
                 double fl = floor(m);
@@ -682,8 +696,8 @@ void iterate_once(Ctx& c) {
                 if (k == 0.0) continue;
                 q = (int64_t)k * (int64_t)FIXED_ONE;
             } else {
-                if (m < c.cutoff) {
-                    if (draw_unit(w[3]) < m / c.cutoff) m = c.cutoff;
+                if (m < c.cutoff) {   /* kept with probability m / cutoff */
+                    if (draw_unit(w[3]) * c.cutoff < m) m = c.cutoff;
                     else continue;
                 }
                 q = llrint(m * 4294967296.0);
@@ -1086,7 +1100,8 @@ double orc_hij(void* h, const uint64_t* source, const uint64_t* target) {
 }
 
 /* one excitation from the Philox words w[4]; returns 0 if null */
-int orc_generate(void* h, const uint64_t* key, const uint64_t* w, uint64_t* child, double* pgen, double* hij) {
+int orc_generate(void* h, const uint64_t* key, const uint64_t* w, uint64_t* child, double* pgen, double* hij,
+                 double* inv) {
     Ctx* c = (Ctx*)h;
     Det d;
     memset(&d, 0, sizeof d);
@@ -1096,6 +1111,10 @@ int orc_generate(void* h, const uint64_t* key, const uint64_t* w, uint64_t* chil
     for (int k = 0; k < c->W; ++k) child[k] = e.child.w[k];
     *pgen = e.pgen;
     *hij = e.hij;
+    if (inv) {
+        inv[0] = e.inv_a;
+        inv[1] = e.inv_b;
+    }
     return 1;
 }
 

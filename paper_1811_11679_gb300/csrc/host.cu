@@ -84,6 +84,10 @@ struct HostTables {
   std::vector<int> hb_start, hb_len;
   std::vector<uint16_t> hb_ab;
   std::vector<uint64_t> hb_cum;
+  std::vector<double> hb_inv;
+  std::vector<uint16_t> pair_ij;
+  std::vector<double> single_g;
+  std::vector<uint16_t> hb_guide;
   std::vector<double> orb_diag, pair_diag;
 };
 
@@ -206,6 +210,7 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           if (!(w > 0.0)) continue;
           T.hb_ab.push_back((uint16_t)(a | (b << 8)));
           T.hb_cum.push_back(0);
+          T.hb_inv.push_back(1.0);
           wts.push_back(w);
         }
       }
@@ -228,7 +233,37 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           last = c;
         }
         T.hb_cum[start + len - 1] = ~0ull;
+        // reciprocal of each entry's probability width / 2^64
+        if (len > 1) {
+          uint64_t prev = 0;
+          for (int k = 0; k < len; ++k) {
+            uint64_t width = (k + 1 == len) ? (0ull - prev) : (T.hb_cum[start + k] - prev);
+            T.hb_inv[start + k] = 18446744073709551616.0 / (double)width;
+            prev = T.hb_cum[start + k];
+          }
+        }
       }
+    }
+  }
+  // single-excitation terms (ia|kk) - (ik|ka) over spin orbitals (zero unless spin(i) = spin(a))
+  T.single_g.assign((size_t)ns * ns * ns, 0.0);
+  for (int i = 0; i < ns; ++i)
+    for (int a = 0; a < ns; ++a) {
+      if ((i ^ a) & 1) continue;
+      for (int k = 0; k < ns; ++k)
+        T.single_g[((size_t)i * ns + a) * ns + k] = g_so(eri, n, i, a, k, k) - g_so(eri, n, i, k, k, a);
+    }
+  // guide index of every heat-bath table
+  T.hb_guide.assign((size_t)ns * (ns - 1) / 2 * 65, 0);
+  for (int idx = 0; idx < ns * (ns - 1) / 2; ++idx) {
+    const int start = T.hb_start[idx], len = T.hb_len[idx];
+    if (len > 65535) throw Fail{HANDE_ERR_INVALID, "heat-bath table too long"};
+    int k = 0;
+    for (int g = 0; g <= 64; ++g) {
+      // first entry k (among the first len-1) with cum[k] > g * 2^58, else len - 1
+      const unsigned long long bound = g == 64 ? ~0ull : ((unsigned long long)g << 58);
+      while (k < len - 1 && !(T.hb_cum[start + k] > bound)) ++k;
+      T.hb_guide[(size_t)idx * 65 + g] = (uint16_t)(len > 0 ? k : 0);
     }
   }
   sd.psingle_thr = (uint32_t)llrint(q.p_single * 4294967296.0);
@@ -479,14 +514,18 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     P.scap = q.spawn_capacity > 0 ? q.spawn_capacity : (int64_t)1 << 21;
     if (P.scap >= ((int64_t)1 << 31)) throw Fail{HANDE_ERR_INVALID, "spawn_capacity must be below 2^31"};
     P.rec_cap = q.record_capacity > 0 ? q.record_capacity : 1 << 16;
-    P.tile_cap = E.W == 1 ? 2048 : (E.W == 2 ? 2048 : 1024);
+    // on-chip tile: distinct new keys (TC, a power of two for the bitonic sort) and
+    // main-list entries (SM) per bucket; sized so two 512-thread CTAs share an SM
+    // for 64- and 128-bit keys
+    P.tile_cap = E.W == 8 ? 512 : 1024;
+    P.seg_max = E.W == 1 ? 1536 : (E.W == 2 ? 1024 : 512);
     if (q.tile_capacity > 0) {
       int tc = q.tile_capacity;
       if (tc < 64 || tc > P.tile_cap || (tc & (tc - 1)))
         throw Fail{HANDE_ERR_INVALID, "tile_capacity must be a power of two in [64, default]"};
       P.tile_cap = tc;
+      P.seg_max = std::min(P.seg_max, tc);
     }
-    P.seg_max = P.tile_cap / 2;
     E.core_size = q.semi_stoch_size;
     E.core_start = q.semi_stoch_start;
 
@@ -514,6 +553,22 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     HostTables T;
     if (s.kind == HANDE_UEG) build_ueg(s, sd, T);
     if (s.kind == HANDE_MOLECULE) build_molecule(s, q, sd, T);
+    {
+      const int n = sd.nel;
+      const double npairs = (double)((int64_t)n * (n - 1) / 2);
+      sd.pg_hub = 1.0 / (2.0 * (double)n);
+      sd.pg_ueg[0] = 2.0 / (npairs * (double)s.norb);
+      sd.pg_ueg[1] = 1.0 / (npairs * (double)s.norb);
+      sd.pg_single[0] = sd.p_single / ((double)n * (double)(s.norb - s.nalpha));
+      sd.pg_single[1] = sd.p_single / ((double)n * (double)(s.norb - s.nbeta));
+      sd.pg_double = sd.p_double / npairs;
+      sd.inv_hub = 2.0 * (double)n;
+      sd.inv_ueg[0] = (npairs * (double)s.norb) / 2.0;
+      sd.inv_ueg[1] = (npairs * (double)s.norb) / 1.0;
+      sd.inv_single[0] = ((double)n * (double)(s.norb - s.nalpha)) / sd.p_single;
+      sd.inv_single[1] = ((double)n * (double)(s.norb - s.nbeta)) / sd.p_single;
+      sd.inv_double = npairs / sd.p_double;
+    }
     sd.kvec = upload(E, T.kvec);
     sd.klookup = upload(E, T.klookup);
     sd.h1 = upload(E, T.h1);
@@ -522,6 +577,12 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.hb_len = upload(E, T.hb_len);
     sd.hb_ab = upload(E, T.hb_ab);
     sd.hb_cum = upload(E, T.hb_cum);
+    sd.hb_inv = upload(E, T.hb_inv);
+    for (int j = 1; j < sd.nel; ++j)
+      for (int i = 0; i < j; ++i) T.pair_ij.push_back((uint16_t)(i | (j << 8)));
+    sd.pair_ij = upload(E, T.pair_ij);
+    sd.single_g = upload(E, T.single_g);
+    sd.hb_guide = upload(E, T.hb_guide);
     sd.orb_diag = upload(E, T.orb_diag);
     sd.pair_diag = upload(E, T.pair_diag);
 

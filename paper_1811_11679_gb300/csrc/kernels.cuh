@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const
 // ------------------------------------------------------------------ buckets
 // Bucket b holds the main-list segment [b*sb, (b+1)*sb) and every spawn whose key
 // lies in [key[b*sb], key[(b+1)*sb]); sb is chosen so a bucket expects at most
-// a quarter tile of spawns.
+// half a tile of spawns (even if every one went to a new determinant).
 template <int W>
 __global__ void k_split(Params P, int cur) {
   DevState* st = P.st;
@@ -332,7 +332,7 @@ __global__ void k_split(Params P, int cur) {
   // attempt count before the first iteration)
   const int64_t na = st->nspawn_prev > 0 ? st->nspawn_prev + st->nspawn_prev / 4 : st->natt;
   int64_t sb = (int64_t)P.seg_max;
-  int64_t half = P.tile_cap / 4;   // expected spawns per bucket: a quarter tile
+  int64_t half = P.tile_cap / 2;   // expected spawns per bucket: half a tile
   if (na > 0) {
     int64_t want = (int64_t)(((double)half * (double)n) / (double)na);
     if (want < sb) sb = want;
@@ -435,13 +435,25 @@ template <int W, int SYS>
 __global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
+  // splitter keys staged in shared memory when they fit (bucket search on chip)
+  constexpr int kSplitSmem = W == 8 ? 256 : (W == 2 ? 2048 : 4096);
+  __shared__ uint64_t ssplit[W * kSplitSmem];
   const int64_t natt = st->natt;
   const int64_t n = st->ndet[cur];
   const int64_t nb = st->nbuckets;
   const int64_t t = st->iter + 1;
   const uint64_t* key = P.key[cur];
   const uint8_t* fl = P.flags[cur];
+  const bool split_on_chip = nb <= kSplitSmem;
+  if (split_on_chip) {
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) ssplit[j * kSplitSmem + b] = P.split_key[j * P.cap + b];
+    }
+  }
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int lane = (int)warp_lane();
   for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < natt; g0 += stride) {
     int64_t g = g0 + threadIdx.x;
     bool have = false;
@@ -449,9 +461,27 @@ __global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
     int64_t amt = 0;
     uint32_t bkt = 0;
     uint8_t initf = 0;
+    // parents of the warp's attempts: the first and last by binary search over
+    // the attempt offsets, each lane's inside that (short) range
+    const int64_t gw = g0 + (threadIdx.x & ~31u);
+    int64_t plo = 0, phi = 0;
+    if (gw < natt) {
+      if (lane < 2) {
+        const int64_t gq = lane == 0 ? gw : (gw + 31 < natt ? gw + 31 : natt - 1);
+        int64_t lo = 0, hi = n - 1;
+        while (lo < hi) {
+          int64_t mid = (lo + hi + 1) >> 1;
+          if (P.att_begin[mid] <= gq) lo = mid;
+          else hi = mid - 1;
+        }
+        plo = lo;
+      }
+      phi = __shfl_sync(0xffffffffu, plo, 1);
+      plo = __shfl_sync(0xffffffffu, plo, 0);
+    }
     if (g < natt) {
-      // parent: last i with att_begin[i] <= g
-      int64_t lo = 0, hi = n - 1;
+      // parent: last i in [plo, phi] with att_begin[i] <= g
+      int64_t lo = plo, hi = phi;
       while (lo < hi) {
         int64_t mid = (lo + hi + 1) >> 1;
         if (P.att_begin[mid] <= g) lo = mid;
@@ -464,7 +494,8 @@ __global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
       Words4 w = draw<W>(P.seed, P.replica, t, a, k);
       Excitation<W> ex = generate<W, SYS>(P.sys, k, w);
       if (ex.ok && ex.hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
-        double m = __ddiv_rn(__dmul_rn(P.tau, fabs(ex.hij)), ex.pgen);
+        // spawn weight tau |H_ij| / p_gen = tau |H_ij| inv_a inv_b (no division)
+        double m = __dmul_rn(__dmul_rn(__dmul_rn(P.tau, fabs(ex.hij)), ex.inv_a), ex.inv_b);
         int64_t q = 0;
         if (!P.real_amp) {
           double flo = floor(m);
@@ -473,8 +504,8 @@ __global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
           if (kk != 0.0) q = (int64_t)kk * kOne;
         } else {
           bool keep = true;
-          if (m < P.cutoff) {
-            if (draw_unit(w.w) < __ddiv_rn(m, P.cutoff)) m = P.cutoff;
+          if (m < P.cutoff) {   // kept with probability m / cutoff
+            if (__dmul_rn(draw_unit(w.w), P.cutoff) < m) m = P.cutoff;
             else keep = false;
           }
           if (keep) q = __double2ll_rn(__dmul_rn(m, 4294967296.0));
@@ -487,11 +518,20 @@ __global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
           initf = (f & F_INIT) ? 1 : 0;
           // bucket = number of splitters s_j (j >= 1) with s_j <= child
           int64_t blo = 1, bhi = nb;
-          while (blo < bhi) {
-            int64_t mid = (blo + bhi) >> 1;
-            Key<W> sk = load_key<W>(P.split_key, P.cap, mid);
-            if (key_le<W>(sk, child)) blo = mid + 1;
-            else bhi = mid;
+          if (split_on_chip) {
+            while (blo < bhi) {
+              int64_t mid = (blo + bhi) >> 1;
+              Key<W> sk = load_key<W>(ssplit, kSplitSmem, mid);
+              if (key_le<W>(sk, child)) blo = mid + 1;
+              else bhi = mid;
+            }
+          } else {
+            while (blo < bhi) {
+              int64_t mid = (blo + bhi) >> 1;
+              Key<W> sk = load_key<W>(P.split_key, P.cap, mid);
+              if (key_le<W>(sk, child)) blo = mid + 1;
+              else bhi = mid;
+            }
           }
           bkt = (uint32_t)(blo - 1);
           have = true;
@@ -553,6 +593,7 @@ struct MergeSmem {
   int32_t* ulb;      // [TC]     main keys below the unique key (-1 if matched)
   uint32_t* mscan;   // [TC+1]   exclusive prefix of matched flags over the unique list
   uint32_t* keep;    // [TC+SM]  keep flags by merged rank, scanned in place
+  int64_t* macc;     // [SM]     spawned amounts added to each main entry
   uint64_t* spl;     // [W][RMAX] sub-range splitters of an oversized bucket
   int32_t* rcnt;     // [RMAX+1] spawns per sub-range
   int32_t* roff;     // [RMAX+1]
@@ -565,7 +606,7 @@ constexpr int kSubRanges = 256;   // RMAX: sub-ranges of one oversized bucket
 
 template <int W>
 __host__ __device__ inline size_t merge_smem_bytes(int TC, int SM) {
-  return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4) +
+  return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4 + 8) +
          (size_t)(TC + SM) * 4 + (size_t)kSubRanges * 8 * W + (size_t)(kSubRanges + 1) * 4 * 5 + 1024;
 }
 
@@ -849,6 +890,77 @@ __device__ int64_t tile_write(const Params& P, MergeSmem<W>& m, const MergeCtx& 
   return nwsum;
 }
 
+// Common-path merge: spawns onto segment entries were added into m.macc,
+// spawns onto new determinants are the sorted unique keys [0, nu); no key is
+// in both.  Keep flags by merged rank, scanned; returns the number kept.
+template <int W>
+__device__ uint32_t acc_decide(const Params& P, MergeSmem<W>& m, const MergeCtx& c, int TC, int SM, int nu,
+                               int nm, uint32_t* wsum) {
+  for (int j = threadIdx.x; j < nu; j += blockDim.x)
+    m.ulb[j] = lb_smem_main<W>(m, SM, 0, nm, skey_at<W>(m, TC, j));
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) m.mlb[i] = lb_smem_uniq<W>(m, TC, nu, mkey_at<W>(m, SM, i));
+  __syncthreads();
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    int64_t gi = c.m0 + i;
+    int64_t p = c.pop[gi] + m.macc[i];
+    bool always = (c.fl[gi] & (F_CORE | F_REF)) != 0;
+    if (!always) p = round_small<W>(P, c.t, mkey_at<W>(m, SM, i), p);
+    m.keep[i + m.mlb[i]] = (always || p != 0) ? 1u : 0u;
+  }
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+    int64_t p = m.samt[j];
+    bool ok = (!P.initiator || (m.sflg[j] & 1u)) && p != 0;
+    if (ok) p = round_small<W>(P, c.t, skey_at<W>(m, TC, j), p);
+    m.keep[m.ulb[j] + j] = (ok && p != 0) ? 1u : 0u;
+  }
+  __syncthreads();
+  return block_scan_excl<uint32_t>(m.keep, nm + nu, wsum);
+}
+
+template <int W, int SYS>
+__device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c, int TC, int SM, int nu, int nm,
+                             uint32_t nkeep, int64_t out) {
+  DevState* st = P.st;
+  const int nc = nm + nu;
+  int64_t nwsum = 0;
+  for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+    int rank = i + m.mlb[i];
+    uint32_t pos = m.keep[rank];
+    uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+    if (nx == pos) continue;
+    int64_t gi = c.m0 + i;
+    int64_t p = c.pop[gi] + m.macc[i];
+    uint8_t f = c.fl[gi];
+    Key<W> k = mkey_at<W>(m, SM, i);
+    if (!(f & (F_CORE | F_REF))) p = round_small<W>(P, c.t, k, p);
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    int64_t o = out + pos;
+    store_key<W>(c.okey, P.cap, o, k);
+    c.opop[o] = p;
+    c.ohd[o] = c.hd[gi];
+    c.ofl[o] = f & F_CORE;
+    nwsum += iabs64(p);
+  }
+  for (int j = threadIdx.x; j < nu; j += blockDim.x) {
+    int rank = m.ulb[j] + j;
+    uint32_t pos = m.keep[rank];
+    uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
+    if (nx == pos) continue;
+    Key<W> k = skey_at<W>(m, TC, j);
+    int64_t p = round_small<W>(P, c.t, k, m.samt[j]);
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    int64_t o = out + pos;
+    store_key<W>(c.okey, P.cap, o, k);
+    c.opop[o] = p;
+    c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
+    c.ofl[o] = 0;
+    P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    nwsum += iabs64(p);
+  }
+  __syncthreads();
+  return nwsum;
+}
+
 // Decoupled look-back (single-pass chained scan) over bucket output counts.
 // Buckets are taken in ticket order, so every predecessor is owned by a running
 // CTA and publishes its count without waiting: the spin always ends, and is
@@ -889,7 +1001,7 @@ __device__ __forceinline__ unsigned long long lookback(const Params& P, int64_t 
 }
 
 template <int W, int SYS>
-__global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
+__global__ void __launch_bounds__(512, (W == 8 ? 1 : 2)) k_merge(Params P, int cur) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t wsum[33];
@@ -898,6 +1010,7 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
   __shared__ unsigned long long s_base;
   __shared__ int s_abort;
   __shared__ int s_nsub;
+  __shared__ int s_nnew;
   const int TC = P.tile_cap, SM = P.seg_max;
   MergeSmem<W> m;
   {
@@ -925,6 +1038,7 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
     m.rcur = (int32_t*)carve(4 * (kSubRanges + 1));
     m.runiq = (int32_t*)carve(4 * (kSubRanges + 1));
     m.rkeep = (int32_t*)carve(4 * (kSubRanges + 1));
+    m.macc = (int64_t*)carve(8 * SM);
   }
   const int64_t n = st->ndet[cur];
   const int64_t nb = st->nbuckets;
@@ -958,23 +1072,77 @@ __global__ void __launch_bounds__(512) k_merge(Params P, int cur) {
       for (int j = 0; j < W; ++j) m.mkey[j * SM + i] = key[j * P.cap + c.m0 + i];
     }
     __syncthreads();
-    if (ns <= TC) {
-      // ---- common case: all spawns of the bucket fit on chip
-      int nu = load_reduce<W>(m, TC, P.b_key, P.scap, P.b_amt, P.b_flag, nullptr, s0, s0 + ns, wsum);
-      int nc = 0;
-      uint32_t nkeep = tile_decide<W>(P, m, c, TC, SM, nu, 0, nm, wsum, nc);
-      if (threadIdx.x == 0) {
-        s_base = lookback(P, b, nkeep, &s_abort);
-        if (!s_abort && (int64_t)(s_base + nkeep) > P.cap) {
-          set_error(st, ERR_STATE_CAPACITY);
-          s_abort = 1;
-        }
-        if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + nkeep);
-      }
+    {
+      // ---- common path: spawns onto entries of the segment are added into
+      // per-entry accumulators (integer sums: order-free); spawns onto new
+      // determinants are collected and, whenever the collection fills up,
+      // sorted and reduced on chip so repeated keys collapse.
+      for (int i = threadIdx.x; i < nm; i += blockDim.x) m.macc[i] = 0;
+      if (threadIdx.x == 0) s_nnew = 0;
       __syncthreads();
-      if (s_abort) break;
-      nwsum += tile_write<W, SYS>(P, m, c, TC, SM, nu, 0, nm, nc, nkeep, (int64_t)s_base);
-      continue;
+      int nnew = 0;
+      bool over = false;
+      for (int64_t base = 0; base < ns; base += blockDim.x) {
+        if (nnew + (int)blockDim.x > TC) {
+          nnew = sort_reduce<W>(m, TC, nnew, wsum);
+          if (nnew + (int)blockDim.x > TC) {
+            over = true;   // block-uniform: too many distinct new keys for one tile
+            break;
+          }
+          if (threadIdx.x == 0) s_nnew = nnew;
+          __syncthreads();
+        }
+        const int64_t i = base + threadIdx.x;
+        const bool have = i < ns;
+        Key<W> k;
+        int64_t a = 0;
+        uint32_t f = 0;
+        bool match = false;
+        int idx = 0;
+        if (have) {
+          k = load_key<W>(P.b_key, P.scap, s0 + i);
+          a = P.b_amt[s0 + i];
+          f = P.b_flag[s0 + i];
+          idx = lb_smem_main<W>(m, SM, 0, nm, k);
+          match = idx < nm && key_eq<W>(mkey_at<W>(m, SM, idx), k);
+        }
+        if (have && match) atomicAdd((unsigned long long*)&m.macc[idx], (unsigned long long)a);
+        const unsigned nmask = __ballot_sync(0xffffffffu, have && !match);
+        int wbase = 0;
+        if (nmask) {
+          const int lead = __ffs(nmask) - 1;
+          if ((int)warp_lane() == lead) wbase = atomicAdd(&s_nnew, __popc(nmask));
+          wbase = __shfl_sync(0xffffffffu, wbase, lead);
+        }
+        if (have && !match) {
+          const int slot = wbase + __popc(nmask & ((1u << warp_lane()) - 1u));
+#pragma unroll
+          for (int j = 0; j < W; ++j) m.skey[j * TC + slot] = k.w[j];
+          m.samt[slot] = a;
+          m.sflg[slot] = f;
+        }
+        __syncthreads();
+        nnew = s_nnew;
+        __syncthreads();
+      }
+      if (!over) {
+        const int nu = sort_reduce<W>(m, TC, nnew, wsum);
+        const uint32_t nkeep = acc_decide<W>(P, m, c, TC, SM, nu, nm, wsum);
+        if (threadIdx.x == 0) {
+          s_base = lookback(P, b, nkeep, &s_abort);
+          if (!s_abort && (int64_t)(s_base + nkeep) > P.cap) {
+            set_error(st, ERR_STATE_CAPACITY);
+            s_abort = 1;
+          }
+          if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + nkeep);
+        }
+        __syncthreads();
+        if (s_abort) break;
+        nwsum += acc_write<W, SYS>(P, m, c, TC, SM, nu, nm, nkeep, (int64_t)s_base);
+        continue;
+      }
+      // too many distinct new determinants for one tile: the sub-range path
+      // below starts again from the bucket's spawns
     }
     // ---- oversized bucket: split its spawns into key sub-ranges with splitters
     // sampled from the spawns themselves, partition them into the staging

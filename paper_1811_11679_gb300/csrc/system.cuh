@@ -51,6 +51,31 @@ struct SysDev {
   // exchange kernel 4 pi / (Omega |k_k - k_l|^2) (UEG, norb^2)
   const double* orb_diag;
   const double* pair_diag;
+  // generation-probability factors that depend only on the system (electron
+  // and orbital counts), evaluated once on the host with the same expressions:
+  // Hubbard 1/(2N); UEG {2, 1}/(C(N,2) M) for same / opposite spins;
+  // heat-bath p_s/(N n_empty(spin)) per spin and p_d/C(N,2)
+  double pg_hub;
+  double pg_ueg[2];
+  double pg_single[2];
+  double pg_double;
+  // reciprocal factors of p_gen for the spawn weight tau |H| inv_a inv_b:
+  // 2N; C(N,2) M / {2, 1}; N n_empty / p_s; C(N,2) / p_d; and per heat-bath
+  // table entry 2^64 / width (1 for a one-entry table)
+  double inv_hub;
+  double inv_ueg[2];
+  double inv_single[2];
+  double inv_double;
+  const double* hb_inv;
+  // pair index P = j(j-1)/2 + i -> (i | j << 8), i < j < nel
+  const uint16_t* pair_ij;
+  // molecule: single-excitation terms G[(i*nspin + a)*nspin + k] = (ia|kk) - (ik|ka)
+  // over spin orbitals (each the same one-rounding difference the sum adds)
+  const double* single_g;
+  // heat-bath guide: for table t and g = 0..64, the first entry whose threshold
+  // exceeds g * 2^58 (clamped to len - 1): the search for word w starts in
+  // [guide[w >> 58], guide[(w >> 58) + 1]]
+  const uint16_t* hb_guide;
 };
 
 __device__ __forceinline__ int tri(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
@@ -143,12 +168,9 @@ __device__ double h_single(const SysDev& s, const Key<W>& d, int i, int a) {
     return 0.0;
   } else {
     double acc = 0.0;
+    const double* row = s.single_g + ((size_t)i * s.nspin + a) * s.nspin;
     HANDE_FOR_OCC(W, d, k, {
-      if (k != i) {
-        double g1 = eri_so(s, i, a, k, k);
-        double g2 = eri_so(s, i, k, k, a);
-        acc = __dadd_rn(acc, __dsub_rn(g1, g2));
-      }
+      if (k != i) acc = __dadd_rn(acc, __ldg(&row[k]));
     })
     v = __dadd_rn(h1_so(s, i, a), acc);
   }
@@ -203,13 +225,14 @@ struct Excitation {
   Key<W> child;
   double pgen;
   double hij;
+  double inv_a, inv_b;   // 1/p_gen = inv_a * inv_b
 };
 
-__device__ __forceinline__ void unrank_pair(uint64_t P, int& i, int& j) {
-  int jj = 1;
-  while ((uint64_t)(jj + 1) * jj / 2 <= P) ++jj;
-  j = jj;
-  i = (int)(P - (uint64_t)jj * (jj - 1) / 2);
+// pair index P = j(j-1)/2 + i  ->  (i, j), i < j (tabulated)
+__device__ __forceinline__ void unrank_pair(const SysDev& s, uint64_t P, int& i, int& j) {
+  uint16_t v = __ldg(&s.pair_ij[P]);
+  i = v & 0xff;
+  j = v >> 8;
 }
 
 template <int W>
@@ -242,7 +265,9 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     }
     int q = 2 * ns + spin;
     if (key_bit<W>(d, q)) return e;
-    e.pgen = __ddiv_rn(1.0, __dmul_rn(2.0, (double)n));
+    e.pgen = s.pg_hub;
+    e.inv_a = s.inv_hub;
+    e.inv_b = 1.0;
     e.hij = h_single<W, SYS>(s, d, p, q);
     e.child = d;
     key_flip<W>(e.child, p);
@@ -252,7 +277,7 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
   } else if (SYS == SYS_UEG) {
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;
     int ii, jj;
-    unrank_pair(draw_index(w.y, npairs), ii, jj);
+    unrank_pair(s, draw_index(w.y, npairs), ii, jj);
     int p = select_bit<W>(d, ii), q = select_bit<W>(d, jj);
     int A = (int)draw_index(w.z, (uint64_t)s.norb);
     int a = 2 * A + (p & 1);
@@ -263,8 +288,9 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     if (B < 0) return e;
     int b = 2 * B + (q & 1);
     if (a == b || key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
-    double ways = ((p ^ q) & 1) ? 1.0 : 2.0;
-    e.pgen = __ddiv_rn(ways, __dmul_rn((double)npairs, (double)s.norb));
+    e.pgen = s.pg_ueg[(p ^ q) & 1];
+    e.inv_a = s.inv_ueg[(p ^ q) & 1];
+    e.inv_b = 1.0;
     int lo = a < b ? a : b, hi = a < b ? b : a;
     e.hij = h_double<W, SYS>(s, d, p, q, lo, hi);
     e.child = d;
@@ -285,7 +311,9 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
       for (int j = 0; j < W; ++j) ne += __popcll(empty.w[j]);
       if (ne == 0) return e;
       int a = select_bit<W>(empty, (int)draw_index(w.z, (uint64_t)ne));
-      e.pgen = __ddiv_rn(s.p_single, __dmul_rn((double)n, (double)ne));
+      e.pgen = s.pg_single[i & 1];
+      e.inv_a = s.inv_single[i & 1];
+      e.inv_b = 1.0;
       e.hij = h_single<W, SYS>(s, d, i, a);
       e.child = d;
       key_flip<W>(e.child, i);
@@ -295,14 +323,16 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     }
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;
     int ii, jj;
-    unrank_pair(draw_index(w.y, npairs), ii, jj);
+    unrank_pair(s, draw_index(w.y, npairs), ii, jj);
     int p = select_bit<W>(d, ii), q = select_bit<W>(d, jj);
     int pidx = q * (q - 1) / 2 + p;
     int len = __ldg(&s.hb_len[pidx]);
     if (len == 0) return e;
     int start = __ldg(&s.hb_start[pidx]);
     // smallest k with w.z < cum[k] among the first len-1 entries, else the last
-    int lo = 0, hi = len - 1;
+    const uint16_t* gd = s.hb_guide + (size_t)pidx * 65;
+    const int gt = (int)(w.z >> 58);
+    int lo = __ldg(&gd[gt]), hi = __ldg(&gd[gt + 1]);
     while (lo < hi) {
       int mid = (lo + hi) >> 1;
       if (__ldg(&s.hb_cum[start + mid]) <= w.z) lo = mid + 1;
@@ -320,8 +350,9 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
       uint64_t width = (k + 1 == len) ? (0ull - prev) : (__ldg(&s.hb_cum[start + k]) - prev);
       pk = __dmul_rn(__ull2double_rn(width), 0x1p-64);
     }
-    double pg = __ddiv_rn(s.p_double, (double)npairs);
-    e.pgen = __dmul_rn(pg, pk);
+    e.pgen = __dmul_rn(s.pg_double, pk);
+    e.inv_a = s.inv_double;
+    e.inv_b = __ldg(&s.hb_inv[start + k]);
     e.hij = h_double<W, SYS>(s, d, p, q, a, b);
     e.child = d;
     key_flip<W>(e.child, p);

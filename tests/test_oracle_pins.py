@@ -230,6 +230,9 @@ def _check_generator(orc, W, dets, nsamples=0, seed=0):
             child, pg, h = r
             cb = B.words_to_bits(child)
             assert abs(pg - tot[cb]) <= 1e-14 * tot[cb]
+            # the spawn weight uses 1/p_gen as two reciprocal factors
+            ia, ib = orc.last_inv
+            assert abs(ia * ib * pg - 1.0) < 1e-15
             assert h == orc.hij(key, child)
         if nsamples:
             # chi^2 of the empirical child distribution against the exact one
