@@ -26,6 +26,8 @@ struct Ops {
   void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);
   size_t (*merge_smem)(int tc, int sm);
   const void* merge_kernel;
+  const void* attempt_kernel;
+  size_t attempt_smem;
 };
 
 constexpr int kPhases = 10;   // timed phases of one iteration

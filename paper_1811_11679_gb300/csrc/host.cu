@@ -622,7 +622,13 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, E.ops.merge_kernel, 512, E.merge_smem_bytes));
     if (per_sm < 1) throw Fail{HANDE_ERR_CUDA, "annihilation kernel does not fit on an SM"};
     E.merge_grid = per_sm * nsm;
-    E.attempt_grid = 8 * nsm;
+    CK(cudaFuncSetAttribute(E.ops.attempt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)E.ops.attempt_smem));
+    int att_per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&att_per_sm, E.ops.attempt_kernel, kAttemptThreads,
+                                                     E.ops.attempt_smem));
+    if (att_per_sm < 1) throw Fail{HANDE_ERR_CUDA, "spawning kernel does not fit on an SM"};
+    E.attempt_grid = att_per_sm * nsm;
 
     // ---- initial state: init_pop walkers on the reference
     DevState hs;

@@ -431,133 +431,265 @@ static __global__ void k_core_apply(Params P, int cur) {
 }
 
 // ------------------------------------------------------------------ attempts
+// ------------------------------------------------------------------ attempts
+// Attempts are processed 32 per warp.  Lanes diverge on what an attempt
+// produces (nothing, a spawn, a molecular single needing an O(N) matrix
+// element), so the rare outcomes go through per-warp shared-memory queues and
+// are finished 32 at a time by full warps: singles (evaluate H_ia, weight,
+// rounding) and spawns (bucket search, append to the staging arrays).
+constexpr int kAttemptThreads = 512;
+constexpr int kAttemptWarps = kAttemptThreads / 32;
+constexpr int kQueue = 64;   // per-warp queue capacity (holds 31 + 32 entries)
+
+template <int W>
+__host__ __device__ constexpr int attempt_split_smem() {
+  return W == 8 ? 256 : (W == 2 ? 2048 : 4096);
+}
+template <int W>
+__host__ __device__ inline size_t attempt_smem_bytes() {
+  return (size_t)attempt_split_smem<W>() * 8 * W +
+         (size_t)kAttemptWarps * kQueue * (8 + 8 + 2 + 8 * W + 8 + 1) + 256;
+}
+
+struct AttemptQueues {
+  int64_t* sq_par;     // pending singles: parent index
+  uint64_t* sq_word;   // their Philox word w (rounding)
+  uint16_t* sq_ia;     // hole | particle << 8
+  uint64_t* pq_key;    // finished spawns: key words [W][kQueue]
+  int64_t* pq_amt;
+  uint8_t* pq_flg;
+};
+
+// signed spawn amount (0 = nothing) for weight tau |H| inv_a inv_b, Philox word u
+__device__ __forceinline__ int64_t spawn_amount(const Params& P, double hij, double inv_a, double inv_b,
+                                                uint64_t u, uint8_t pf) {
+  double m = __dmul_rn(__dmul_rn(__dmul_rn(P.tau, fabs(hij)), inv_a), inv_b);
+  int64_t q = 0;
+  if (!P.real_amp) {
+    double flo = floor(m);
+    double kk = flo;
+    if (draw_unit(u) < __dsub_rn(m, flo)) kk = __dadd_rn(kk, 1.0);
+    if (kk != 0.0) q = (int64_t)kk * kOne;
+  } else {
+    bool keep = true;
+    if (m < P.cutoff) {   // kept with probability m / cutoff
+      if (__dmul_rn(draw_unit(u), P.cutoff) < m) m = P.cutoff;
+      else keep = false;
+    }
+    if (keep) q = __double2ll_rn(__dmul_rn(m, 4294967296.0));
+  }
+  if (q == 0) return 0;
+  int hs = hij < 0.0 ? -1 : 1;
+  int ps = (pf & F_NEG) ? -1 : 1;
+  return (-hs * ps) < 0 ? -q : q;
+}
+
+// the top `take` queued spawns of this warp: bucket, rank, staging slot
+template <int W>
+__device__ void flush_spawns(const Params& P, const AttemptQueues& Q, int& pq_n, int take, int64_t nb,
+                             const uint64_t* split, int64_t split_stride) {
+  DevState* st = P.st;
+  const int lane = (int)warp_lane();
+  const bool have = lane < take;
+  Key<W> child;
+  int64_t amt = 0;
+  uint8_t initf = 0;
+  uint32_t bkt = 0;
+  if (have) {
+    const int e = pq_n - take + lane;
+#pragma unroll
+    for (int j = 0; j < W; ++j) child.w[j] = Q.pq_key[j * kQueue + e];
+    amt = Q.pq_amt[e];
+    initf = Q.pq_flg[e];
+    // bucket = number of splitters s_j (j >= 1) with s_j <= child
+    int64_t blo = 1, bhi = nb;
+    while (blo < bhi) {
+      int64_t mid = (blo + bhi) >> 1;
+      Key<W> sk = load_key<W>(split, split_stride, mid);
+      if (key_le<W>(sk, child)) blo = mid + 1;
+      else bhi = mid;
+    }
+    bkt = (uint32_t)(blo - 1);
+  }
+  const unsigned want = __ballot_sync(0xffffffffu, have);
+  int64_t base = 0;
+  if (want && lane == 0)
+    base = (int64_t)atomicAdd((unsigned long long*)&st->nspawn, (unsigned long long)__popc(want));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (have) {
+    const int64_t slot = base + lane;
+    const uint32_t rank = atomicAdd(&P.bcount[bkt], 1u);
+    if (slot < P.scap) {
+      store_key<W>(P.s_key, P.scap, slot, child);
+      P.s_amt[slot] = amt;
+      P.s_meta[slot] = ((uint64_t)bkt << 32) | ((uint64_t)rank << 1) | initf;
+    } else {
+      set_error(st, ERR_SPAWN_CAPACITY);
+    }
+  }
+  pq_n -= take;
+  __syncwarp();
+}
+
+template <int W>
+__device__ __forceinline__ void push_spawn(const Params& P, const AttemptQueues& Q, int& pq_n, bool have,
+                                           const Key<W>& child, int64_t amt, uint8_t initf, int64_t nb,
+                                           const uint64_t* split, int64_t split_stride) {
+  const unsigned m = __ballot_sync(0xffffffffu, have);
+  if (have) {
+    const int e = pq_n + __popc(m & ((1u << warp_lane()) - 1u));
+#pragma unroll
+    for (int j = 0; j < W; ++j) Q.pq_key[j * kQueue + e] = child.w[j];
+    Q.pq_amt[e] = amt;
+    Q.pq_flg[e] = initf;
+  }
+  pq_n += __popc(m);
+  __syncwarp();
+  if (pq_n >= 32) flush_spawns<W>(P, Q, pq_n, 32, nb, split, split_stride);
+}
+
+// the top `take` queued molecular singles: H_ia, core test, weight, rounding
 template <int W, int SYS>
-__global__ void __launch_bounds__(256) k_attempt(Params P, int cur) {
+__device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n, int& pq_n, int take,
+                              const uint64_t* key, const uint8_t* fl, int64_t nb, const uint64_t* split,
+                              int64_t split_stride) {
+  const int lane = (int)warp_lane();
+  bool have = false;
+  Key<W> child;
+  int64_t amt = 0;
+  uint8_t initf = 0;
+  if (lane < take) {
+    const int e = sq_n - take + lane;
+    const int64_t par = Q.sq_par[e];
+    const uint64_t u = Q.sq_word[e];
+    const int i = Q.sq_ia[e] & 0xff, a = Q.sq_ia[e] >> 8;
+    const Key<W> k = load_key<W>(key, P.cap, par);
+    const uint8_t f = fl[par];
+    child = k;
+    key_flip<W>(child, i);
+    key_flip<W>(child, a);
+    const double hij = h_single<W, SYS>(P.sys, k, i, a);
+    if (hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
+      amt = spawn_amount(P, hij, P.sys.inv_single[i & 1], 1.0, u, f);
+      initf = (f & F_INIT) ? 1 : 0;
+      have = amt != 0;
+    }
+  }
+  sq_n -= take;
+  __syncwarp();
+  push_spawn<W>(P, Q, pq_n, have, child, amt, initf, nb, split, split_stride);
+}
+
+template <int W, int SYS>
+__global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
-  // splitter keys staged in shared memory when they fit (bucket search on chip)
-  constexpr int kSplitSmem = W == 8 ? 256 : (W == 2 ? 2048 : 4096);
-  __shared__ uint64_t ssplit[W * kSplitSmem];
+  constexpr int KS = attempt_split_smem<W>();
+  extern __shared__ __align__(16) unsigned char att_smem[];
+  uint64_t* ssplit = reinterpret_cast<uint64_t*>(att_smem);
+  const int wid = threadIdx.x >> 5;
+  AttemptQueues Q;
+  {
+    unsigned char* p = att_smem + (size_t)KS * 8 * W;
+    const size_t per = kQueue;
+    Q.sq_par = reinterpret_cast<int64_t*>(p) + wid * per;
+    p += kAttemptWarps * per * 8;
+    Q.sq_word = reinterpret_cast<uint64_t*>(p) + wid * per;
+    p += kAttemptWarps * per * 8;
+    Q.pq_key = reinterpret_cast<uint64_t*>(p) + wid * per * W;
+    p += kAttemptWarps * per * 8 * W;
+    Q.pq_amt = reinterpret_cast<int64_t*>(p) + wid * per;
+    p += kAttemptWarps * per * 8;
+    Q.sq_ia = reinterpret_cast<uint16_t*>(p) + wid * per;
+    p += kAttemptWarps * per * 2;
+    Q.pq_flg = reinterpret_cast<uint8_t*>(p) + wid * per;
+  }
   const int64_t natt = st->natt;
   const int64_t n = st->ndet[cur];
   const int64_t nb = st->nbuckets;
   const int64_t t = st->iter + 1;
   const uint64_t* key = P.key[cur];
   const uint8_t* fl = P.flags[cur];
-  const bool split_on_chip = nb <= kSplitSmem;
+  // splitter keys staged in shared memory when they fit (bucket search on chip)
+  const bool split_on_chip = nb <= KS;
   if (split_on_chip) {
     for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
 #pragma unroll
-      for (int j = 0; j < W; ++j) ssplit[j * kSplitSmem + b] = P.split_key[j * P.cap + b];
+      for (int j = 0; j < W; ++j) ssplit[j * KS + b] = P.split_key[j * P.cap + b];
     }
   }
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const uint64_t* split = split_on_chip ? ssplit : P.split_key;
+  const int64_t split_stride = split_on_chip ? KS : P.cap;
   const int lane = (int)warp_lane();
-  for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < natt; g0 += stride) {
-    int64_t g = g0 + threadIdx.x;
-    bool have = false;
-    Key<W> child;
-    int64_t amt = 0;
-    uint32_t bkt = 0;
-    uint8_t initf = 0;
+  const int64_t total_warps = (int64_t)gridDim.x * kAttemptWarps;
+  int sq_n = 0, pq_n = 0;   // warp-uniform queue lengths
+  for (int64_t gw = ((int64_t)blockIdx.x * kAttemptWarps + wid) * 32; gw < natt; gw += total_warps * 32) {
+    const int64_t g = gw + lane;
     // parents of the warp's attempts: the first and last by binary search over
     // the attempt offsets, each lane's inside that (short) range
-    const int64_t gw = g0 + (threadIdx.x & ~31u);
-    int64_t plo = 0, phi = 0;
-    if (gw < natt) {
-      if (lane < 2) {
-        const int64_t gq = lane == 0 ? gw : (gw + 31 < natt ? gw + 31 : natt - 1);
-        int64_t lo = 0, hi = n - 1;
-        while (lo < hi) {
-          int64_t mid = (lo + hi + 1) >> 1;
-          if (P.att_begin[mid] <= gq) lo = mid;
-          else hi = mid - 1;
-        }
-        plo = lo;
+    int64_t plo = 0;
+    if (lane < 2) {
+      const int64_t gq = lane == 0 ? gw : (gw + 31 < natt ? gw + 31 : natt - 1);
+      int64_t lo = 0, hi = n - 1;
+      while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (P.att_begin[mid] <= gq) lo = mid;
+        else hi = mid - 1;
       }
-      phi = __shfl_sync(0xffffffffu, plo, 1);
-      plo = __shfl_sync(0xffffffffu, plo, 0);
+      plo = lo;
     }
+    const int64_t phi = __shfl_sync(0xffffffffu, plo, 1);
+    plo = __shfl_sync(0xffffffffu, plo, 0);
+    bool have = false, single = false;
+    Key<W> child;
+    int64_t amt = 0;
+    uint8_t initf = 0;
+    int64_t par = 0;
+    uint64_t word = 0;
+    uint16_t ia = 0;
     if (g < natt) {
-      // parent: last i in [plo, phi] with att_begin[i] <= g
       int64_t lo = plo, hi = phi;
       while (lo < hi) {
         int64_t mid = (lo + hi + 1) >> 1;
         if (P.att_begin[mid] <= g) lo = mid;
         else hi = mid - 1;
       }
-      const int64_t i = lo;
-      const uint64_t a = (uint64_t)(g - P.att_begin[i]);
-      Key<W> k = load_key<W>(key, P.cap, i);
-      const uint8_t f = fl[i];
-      Words4 w = draw<W>(P.seed, P.replica, t, a, k);
-      Excitation<W> ex = generate<W, SYS>(P.sys, k, w);
-      if (ex.ok && ex.hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
-        // spawn weight tau |H_ij| / p_gen = tau |H_ij| inv_a inv_b (no division)
-        double m = __dmul_rn(__dmul_rn(__dmul_rn(P.tau, fabs(ex.hij)), ex.inv_a), ex.inv_b);
-        int64_t q = 0;
-        if (!P.real_amp) {
-          double flo = floor(m);
-          double kk = flo;
-          if (draw_unit(w.w) < __dsub_rn(m, flo)) kk = __dadd_rn(kk, 1.0);
-          if (kk != 0.0) q = (int64_t)kk * kOne;
-        } else {
-          bool keep = true;
-          if (m < P.cutoff) {   // kept with probability m / cutoff
-            if (__dmul_rn(draw_unit(w.w), P.cutoff) < m) m = P.cutoff;
-            else keep = false;
-          }
-          if (keep) q = __double2ll_rn(__dmul_rn(m, 4294967296.0));
-        }
-        if (q != 0) {
-          int hs = ex.hij < 0.0 ? -1 : 1;
-          int ps = (f & F_NEG) ? -1 : 1;
-          amt = (-hs * ps) < 0 ? -q : q;
-          child = ex.child;
-          initf = (f & F_INIT) ? 1 : 0;
-          // bucket = number of splitters s_j (j >= 1) with s_j <= child
-          int64_t blo = 1, bhi = nb;
-          if (split_on_chip) {
-            while (blo < bhi) {
-              int64_t mid = (blo + bhi) >> 1;
-              Key<W> sk = load_key<W>(ssplit, kSplitSmem, mid);
-              if (key_le<W>(sk, child)) blo = mid + 1;
-              else bhi = mid;
-            }
-          } else {
-            while (blo < bhi) {
-              int64_t mid = (blo + bhi) >> 1;
-              Key<W> sk = load_key<W>(P.split_key, P.cap, mid);
-              if (key_le<W>(sk, child)) blo = mid + 1;
-              else bhi = mid;
-            }
-          }
-          bkt = (uint32_t)(blo - 1);
-          have = true;
-        }
+      par = lo;
+      const uint64_t a = (uint64_t)(g - P.att_begin[par]);
+      const Key<W> k = load_key<W>(key, P.cap, par);
+      const uint8_t f = fl[par];
+      const Words4 w = draw<W>(P.seed, P.replica, t, a, k);
+      const Excitation<W> ex = generate<W, SYS, true>(P.sys, k, w);
+      if (ex.single) {
+        single = true;
+        word = w.w;
+        ia = (uint16_t)(ex.si | (ex.sa << 8));
+      } else if (ex.ok && ex.hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
+        amt = spawn_amount(P, ex.hij, ex.inv_a, ex.inv_b, w.w, f);
+        child = ex.child;
+        initf = (f & F_INIT) ? 1 : 0;
+        have = amt != 0;
       }
     }
-    // warp-aggregated slot allocation
-    unsigned act = __activemask();
-    unsigned want = __ballot_sync(act, have);
-    int64_t base = 0;
-    int leader = want ? __ffs(want) - 1 : 0;
-    if (want && (int)warp_lane() == leader)
-      base = (int64_t)atomicAdd((unsigned long long*)&st->nspawn, (unsigned long long)__popc(want));
-    base = __shfl_sync(act, base, leader);
-    if (have) {
-      int64_t slot = base + __popc(want & ((1u << warp_lane()) - 1u));
-      uint32_t rank = atomicAdd(&P.bcount[bkt], 1u);
-      if (slot < P.scap) {
-        store_key<W>(P.s_key, P.scap, slot, child);
-        P.s_amt[slot] = amt;
-        P.s_meta[slot] = ((uint64_t)bkt << 32) | ((uint64_t)rank << 1) | initf;
-      } else {
-        set_error(st, ERR_SPAWN_CAPACITY);
+    if (SYS == SYS_MOLECULE) {
+      const unsigned sm = __ballot_sync(0xffffffffu, single);
+      if (single) {
+        const int e = sq_n + __popc(sm & ((1u << lane) - 1u));
+        Q.sq_par[e] = par;
+        Q.sq_word[e] = word;
+        Q.sq_ia[e] = ia;
       }
+      sq_n += __popc(sm);
+      __syncwarp();
     }
+    push_spawn<W>(P, Q, pq_n, have, child, amt, initf, nb, split, split_stride);
+    if (SYS == SYS_MOLECULE && sq_n >= 32)
+      flush_singles<W, SYS>(P, Q, sq_n, pq_n, 32, key, fl, nb, split, split_stride);
   }
+  if (SYS == SYS_MOLECULE && sq_n > 0)
+    flush_singles<W, SYS>(P, Q, sq_n, pq_n, sq_n, key, fl, nb, split, split_stride);
+  if (pq_n > 0) flush_spawns<W>(P, Q, pq_n, pq_n, nb, split, split_stride);
 }
 
 template <int W>

@@ -226,6 +226,8 @@ struct Excitation {
   double pgen;
   double hij;
   double inv_a, inv_b;   // 1/p_gen = inv_a * inv_b
+  bool single;           // a molecular single selected but not evaluated (DEFER)
+  int si, sa;            // its hole and particle
 };
 
 // pair index P = j(j-1)/2 + i  ->  (i, j), i < j (tabulated)
@@ -249,10 +251,13 @@ __device__ __forceinline__ Key<W> spin_mask(int spin, int nspin) {
   return m;
 }
 
-template <int W, int SYS>
+// DEFER: a molecular single excitation is only selected (e.single, e.si, e.sa);
+// its matrix element is left to the caller (evaluated later by full warps).
+template <int W, int SYS, bool DEFER = false>
 __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4& w) {
   Excitation<W> e;
   e.ok = false;
+  e.single = false;
   const int n = s.nel;
   if (SYS == SYS_HUBBARD) {
     int p = select_bit<W>(d, (int)draw_index(w.x, (uint64_t)n));
@@ -311,6 +316,12 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
       for (int j = 0; j < W; ++j) ne += __popcll(empty.w[j]);
       if (ne == 0) return e;
       int a = select_bit<W>(empty, (int)draw_index(w.z, (uint64_t)ne));
+      if (DEFER) {
+        e.single = true;
+        e.si = i;
+        e.sa = a;
+        return e;
+      }
       e.pgen = s.pg_single[i & 1];
       e.inv_a = s.inv_single[i & 1];
       e.inv_b = 1.0;
