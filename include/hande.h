@@ -105,7 +105,7 @@ typedef struct {
   int64_t spawn_capacity;     /* max spawns per iteration (0 = default) */
   int record_capacity;        /* estimator records kept on the device (0 = default) */
   int tile_capacity;          /* distinct new spawned keys one annihilation tile holds on
-                                 chip: 0 = default (1024 for 64/128-bit keys, 512 for
+                                 chip: 0 = default (512 for 64/128-bit keys, 256 for
                                  512-bit), else a power of two in [64, default]; smaller
                                  values only send more buckets through the slower paths */
 } hande_qmc;

@@ -515,10 +515,10 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (P.scap >= ((int64_t)1 << 31)) throw Fail{HANDE_ERR_INVALID, "spawn_capacity must be below 2^31"};
     P.rec_cap = q.record_capacity > 0 ? q.record_capacity : 1 << 16;
     // on-chip tile: distinct new keys (TC, a power of two for the bitonic sort) and
-    // main-list entries (SM) per bucket; sized so two 512-thread CTAs share an SM
+    // main-list entries (SM) per bucket; sized so four 256-thread CTAs share an SM
     // for 64- and 128-bit keys
-    P.tile_cap = E.W == 8 ? 512 : 1024;
-    P.seg_max = E.W == 1 ? 1536 : (E.W == 2 ? 1024 : 512);
+    P.tile_cap = E.W == 8 ? 256 : 512;
+    P.seg_max = E.W == 1 ? 768 : (E.W == 2 ? 512 : 256);
     if (q.tile_capacity > 0) {
       int tc = q.tile_capacity;
       if (tc < 64 || tc > P.tile_cap || (tc & (tc - 1)))
@@ -619,7 +619,8 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     CK(cudaFuncSetAttribute(E.ops.merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)E.merge_smem_bytes));
     int per_sm = 0;
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, E.ops.merge_kernel, 512, E.merge_smem_bytes));
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, E.ops.merge_kernel, kMergeThreads,
+                                                     E.merge_smem_bytes));
     if (per_sm < 1) throw Fail{HANDE_ERR_CUDA, "annihilation kernel does not fit on an SM"};
     E.merge_grid = per_sm * nsm;
     CK(cudaFuncSetAttribute(E.ops.attempt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

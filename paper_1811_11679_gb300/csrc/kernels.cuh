@@ -791,23 +791,35 @@ __device__ __forceinline__ void rec_swap(MergeSmem<W>& m, int TC, int a, int b) 
 // amounts and OR-ed initiator bits.  Returns u.
 template <int W>
 __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
-  int n2 = 1;
+  int n2 = 64;
   while (n2 < n) n2 <<= 1;
   for (int i = n + threadIdx.x; i < n2; i += blockDim.x) m.sflg[i] = 0x80000000u;
   __syncthreads();
+  // bitonic network over n2 keys; compare-swap pair p joins elements
+  // i = 2p - (p mod j) and i + j, so for strides j <= 32 the 32 pairs of a warp
+  // stay inside its own 64-element segment and a warp barrier suffices
+  const int npairs = n2 >> 1;
+  const bool warp_local_ok = npairs <= (int)blockDim.x;
+  int prev_j = 64;
   for (int k = 2; k <= n2; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-        int l = i ^ j;
-        if (l > i) {
-          bool up = (i & k) == 0;
-          bool sw = up ? rec_lt<W>(m, TC, l, i) : rec_lt<W>(m, TC, i, l);
+      // a block barrier separates two stages unless both stay inside warps
+      if (!warp_local_ok || j > 32 || prev_j > 32) __syncthreads();
+      else __syncwarp();
+      prev_j = j;
+      for (int pbase = 0; pbase < npairs; pbase += blockDim.x) {
+        const int p = pbase + threadIdx.x;
+        if (p < npairs) {
+          const int i = 2 * p - (p & (j - 1));
+          const int l = i + j;
+          const bool up = (i & k) == 0;
+          const bool sw = up ? rec_lt<W>(m, TC, l, i) : rec_lt<W>(m, TC, i, l);
           if (sw) rec_swap<W>(m, TC, i, l);
         }
       }
-      __syncthreads();
     }
   }
+  __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     bool head = (i == 0) || !key_eq<W>(skey_at<W>(m, TC, i), skey_at<W>(m, TC, i - 1));
     m.uid[i] = head ? 1 : 0;
@@ -1093,47 +1105,59 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
   return nwsum;
 }
 
-// Decoupled look-back (single-pass chained scan) over bucket output counts.
-// Buckets are taken in ticket order, so every predecessor is owned by a running
-// CTA and publishes its count without waiting: the spin always ends, and is
-// bounded anyway.  Returns the exclusive prefix; sets *abort on failure.
-__device__ __forceinline__ unsigned long long lookback(const Params& P, int64_t b, uint32_t count, int* abort) {
+// Decoupled look-back (single-pass chained scan) over bucket output counts,
+// run by one warp: each step reads 32 predecessor states at once.  Buckets are
+// taken in ticket order, so every predecessor is owned by a running CTA and
+// publishes its count without waiting: the spin always ends, and is bounded
+// anyway.  Returns the exclusive prefix (all lanes); sets *abort on failure.
+__device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int64_t b, uint32_t count, int* abort) {
   DevState* st = P.st;
   const unsigned long long AGG = 1ull << 62, INC = 2ull << 62, MASK = (1ull << 62) - 1;
-  unsigned long long excl = 0;
+  const int lane = (int)warp_lane();
   if (b == 0) {
-    atomicExch(&P.tile_state[0], INC | (unsigned long long)count);
+    if (lane == 0) atomicExch(&P.tile_state[0], INC | (unsigned long long)count);
     return 0;
   }
-  atomicExch(&P.tile_state[b], AGG | (unsigned long long)count);
+  if (lane == 0) atomicExch(&P.tile_state[b], AGG | (unsigned long long)count);
+  unsigned long long excl = 0;
   int64_t p = b - 1;
   long long spins = 0;
-  while (p >= 0) {
-    unsigned long long v = atomicAdd(&P.tile_state[p], 0ull);
-    unsigned long long s = v & ~MASK;
-    if (s == 0) {
+  for (;;) {
+    const int64_t idx = p - lane;
+    const unsigned long long v = idx >= 0 ? atomicAdd(&P.tile_state[idx], 0ull) : INC;
+    const unsigned long long s = v >> 62;
+    const unsigned inc = __ballot_sync(0xffffffffu, s == 2);
+    const unsigned none = __ballot_sync(0xffffffffu, s == 0);
+    const int first = inc ? __ffs(inc) - 1 : 31;
+    const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (none & need) {   // a state we need is not published yet
       ++spins;
-      if ((spins & 1023) == 0 && *(volatile unsigned*)&st->error) {
+      if ((spins & 255) == 0 && *(volatile unsigned*)&st->error) {
         *abort = 1;   // another tile failed: give up without adding an error
         return 0;
       }
-      if (spins > (1ll << 22)) {
-        set_error(st, ERR_TIMEOUT);
+      if (spins > (1ll << 20)) {
+        if (lane == 0) set_error(st, ERR_TIMEOUT);
         *abort = 1;
         return 0;
       }
       continue;
     }
-    excl += v & MASK;
-    if (s == INC) break;
-    --p;
+    unsigned long long add = (lane <= first) ? (v & MASK) : 0ull;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+    excl += add;
+    if (inc) break;
+    p -= 32;
   }
-  atomicExch(&P.tile_state[b], INC | (excl + count));
+  if (lane == 0) atomicExch(&P.tile_state[b], INC | (excl + count));
   return excl;
 }
 
+constexpr int kMergeThreads = 256;
+
 template <int W, int SYS>
-__global__ void __launch_bounds__(512, (W == 8 ? 1 : 2)) k_merge(Params P, int cur) {
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t wsum[33];
@@ -1260,13 +1284,18 @@ __global__ void __launch_bounds__(512, (W == 8 ? 1 : 2)) k_merge(Params P, int c
       if (!over) {
         const int nu = sort_reduce<W>(m, TC, nnew, wsum);
         const uint32_t nkeep = acc_decide<W>(P, m, c, TC, SM, nu, nm, wsum);
-        if (threadIdx.x == 0) {
-          s_base = lookback(P, b, nkeep, &s_abort);
-          if (!s_abort && (int64_t)(s_base + nkeep) > P.cap) {
-            set_error(st, ERR_STATE_CAPACITY);
-            s_abort = 1;
+        if (threadIdx.x < 32) {
+          int ab = 0;
+          const unsigned long long base = lookback_warp(P, b, nkeep, &ab);
+          if (threadIdx.x == 0) {
+            s_base = base;
+            s_abort = ab;
+            if (!ab && (int64_t)(base + nkeep) > P.cap) {
+              set_error(st, ERR_STATE_CAPACITY);
+              s_abort = 1;
+            }
+            if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(base + nkeep);
           }
-          if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + nkeep);
         }
         __syncthreads();
         if (s_abort) break;
@@ -1376,13 +1405,18 @@ __global__ void __launch_bounds__(512, (W == 8 ? 1 : 2)) k_merge(Params P, int c
         __syncthreads();
       }
       if (s_abort) break;
-      if (threadIdx.x == 0) {
-        s_base = lookback(P, b, total, &s_abort);
-        if (!s_abort && (int64_t)(s_base + total) > P.cap) {
-          set_error(st, ERR_STATE_CAPACITY);
-          s_abort = 1;
+      if (threadIdx.x < 32) {
+        int ab = 0;
+        const unsigned long long base = lookback_warp(P, b, total, &ab);
+        if (threadIdx.x == 0) {
+          s_base = base;
+          s_abort = ab;
+          if (!ab && (int64_t)(base + total) > P.cap) {
+            set_error(st, ERR_STATE_CAPACITY);
+            s_abort = 1;
+          }
+          if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(base + total);
         }
-        if (!s_abort && b == nb - 1) st->ndet[nxt] = (int64_t)(s_base + total);
       }
       __syncthreads();
       if (s_abort) break;

@@ -145,7 +145,7 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   mark(6);
   k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
   mark(7);
-  k_merge<W, SYS><<<E.merge_grid, 512, E.merge_smem_bytes, s>>>(P, cur);
+  k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur);
   mark(8);
   k_new_hdiag<W, SYS><<<E.attempt_grid, 256, 0, s>>>(P, cur);
   mark(9);
