@@ -725,7 +725,8 @@ struct MergeSmem {
   int32_t* ulb;      // [TC]     main keys below the unique key (-1 if matched)
   uint32_t* mscan;   // [TC+1]   exclusive prefix of matched flags over the unique list
   uint32_t* keep;    // [TC+SM]  keep flags by merged rank, scanned in place
-  int64_t* macc;     // [SM]     spawned amounts added to each main entry
+  int64_t* macc;     // [SM]     spawned amounts added to each main entry (then the final N)
+  uint64_t* skey2;   // [W][kCountMax] unique keys of the counting reduction
   uint64_t* spl;     // [W][RMAX] sub-range splitters of an oversized bucket
   int32_t* rcnt;     // [RMAX+1] spawns per sub-range
   int32_t* roff;     // [RMAX+1]
@@ -735,10 +736,11 @@ struct MergeSmem {
 };
 
 constexpr int kSubRanges = 256;   // RMAX: sub-ranges of one oversized bucket
+constexpr int kCountMax = 128;    // new-key sets up to this size are reduced by counting
 
 template <int W>
 __host__ __device__ inline size_t merge_smem_bytes(int TC, int SM) {
-  return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4 + 8) +
+  return (size_t)TC * (8 * W + 8 + 4 + 4 + 8 + 4 + 4 + 4) + 4 + (size_t)SM * (8 * W + 4 + 4 + 8) + (size_t)kCountMax * 8 * W +
          (size_t)(TC + SM) * 4 + (size_t)kSubRanges * 8 * W + (size_t)(kSubRanges + 1) * 4 * 5 + 1024;
 }
 
@@ -859,6 +861,54 @@ __device__ int sort_reduce(MergeSmem<W>& m, int TC, int n, uint32_t* wsum) {
   }
   __syncthreads();
   return (int)total;
+}
+
+// The same result as sort_reduce for n <= kCountMax (<= blockDim) records, by
+// counting: each record finds the first record with its key, each first record
+// counts the first records with smaller keys (its position), and amounts and
+// initiator bits are added into that position.  O(n^2) compares, four barriers.
+template <int W>
+__device__ int count_reduce(MergeSmem<W>& m, int TC, int n) {
+  const int i = threadIdx.x;
+  Key<W> ki;
+  int rep = i;
+  if (i < n) {
+    ki = skey_at<W>(m, TC, i);
+    for (int j = 0; j < i; ++j)
+      if (key_eq<W>(skey_at<W>(m, TC, j), ki)) {
+        rep = j;
+        break;
+      }
+    m.uid[i] = rep;
+    m.uamt[i] = 0;
+    m.uflg[i] = 0;
+  }
+  __syncthreads();
+  if (i < n && rep == i) {
+    int r = 0;
+    for (int j = 0; j < n; ++j)
+      if (m.uid[j] == j && key_lt<W>(skey_at<W>(m, TC, j), ki)) ++r;
+    m.ulb[i] = r;
+  }
+  const int u = __syncthreads_count(i < n && rep == i);
+  if (i < n) {
+    const int r = m.ulb[rep];
+    atomicAdd((unsigned long long*)&m.uamt[r], (unsigned long long)m.samt[i]);
+    if (m.sflg[i] & 1u) atomicOr(&m.uflg[r], 1u);
+    if (rep == i) {
+#pragma unroll
+      for (int j = 0; j < W; ++j) m.skey2[j * kCountMax + r] = ki.w[j];
+    }
+  }
+  __syncthreads();
+  if (i < u) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) m.skey[j * TC + i] = m.skey2[j * kCountMax + i];
+    m.samt[i] = m.uamt[i];
+    m.sflg[i] = m.uflg[i];
+  }
+  __syncthreads();
+  return u;
 }
 
 // Load spawns [beg, end) of (key, amt, flag) arrays into the tile and reduce
@@ -1044,17 +1094,23 @@ __device__ uint32_t acc_decide(const Params& P, MergeSmem<W>& m, const MergeCtx&
     m.ulb[j] = lb_smem_main<W>(m, SM, 0, nm, skey_at<W>(m, TC, j));
   for (int i = threadIdx.x; i < nm; i += blockDim.x) m.mlb[i] = lb_smem_uniq<W>(m, TC, nu, mkey_at<W>(m, SM, i));
   __syncthreads();
+  // the final population of every candidate is kept on chip for acc_write:
+  // main entries in macc (flags in mmatch), new determinants in samt
   for (int i = threadIdx.x; i < nm; i += blockDim.x) {
     int64_t gi = c.m0 + i;
     int64_t p = c.pop[gi] + m.macc[i];
-    bool always = (c.fl[gi] & (F_CORE | F_REF)) != 0;
+    const uint8_t f = c.fl[gi];
+    bool always = (f & (F_CORE | F_REF)) != 0;
     if (!always) p = round_small<W>(P, c.t, mkey_at<W>(m, SM, i), p);
+    m.macc[i] = p;
+    m.mmatch[i] = f;
     m.keep[i + m.mlb[i]] = (always || p != 0) ? 1u : 0u;
   }
   for (int j = threadIdx.x; j < nu; j += blockDim.x) {
     int64_t p = m.samt[j];
     bool ok = (!P.initiator || (m.sflg[j] & 1u)) && p != 0;
     if (ok) p = round_small<W>(P, c.t, skey_at<W>(m, TC, j), p);
+    m.samt[j] = p;
     m.keep[m.ulb[j] + j] = (ok && p != 0) ? 1u : 0u;
   }
   __syncthreads();
@@ -1072,11 +1128,10 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
     uint32_t pos = m.keep[rank];
     uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
     if (nx == pos) continue;
-    int64_t gi = c.m0 + i;
-    int64_t p = c.pop[gi] + m.macc[i];
-    uint8_t f = c.fl[gi];
-    Key<W> k = mkey_at<W>(m, SM, i);
-    if (!(f & (F_CORE | F_REF))) p = round_small<W>(P, c.t, k, p);
+    const int64_t gi = c.m0 + i;
+    const int64_t p = m.macc[i];
+    const uint8_t f = (uint8_t)m.mmatch[i];
+    const Key<W> k = mkey_at<W>(m, SM, i);
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
     store_key<W>(c.okey, P.cap, o, k);
@@ -1091,7 +1146,7 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
     uint32_t nx = (rank + 1 < nc) ? m.keep[rank + 1] : nkeep;
     if (nx == pos) continue;
     Key<W> k = skey_at<W>(m, TC, j);
-    int64_t p = round_small<W>(P, c.t, k, m.samt[j]);
+    const int64_t p = m.samt[j];
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
     store_key<W>(c.okey, P.cap, o, k);
@@ -1195,6 +1250,7 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
     m.runiq = (int32_t*)carve(4 * (kSubRanges + 1));
     m.rkeep = (int32_t*)carve(4 * (kSubRanges + 1));
     m.macc = (int64_t*)carve(8 * SM);
+    m.skey2 = (uint64_t*)carve(8 * W * kCountMax);
   }
   const int64_t n = st->ndet[cur];
   const int64_t nb = st->nbuckets;
@@ -1282,7 +1338,8 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
         __syncthreads();
       }
       if (!over) {
-        const int nu = sort_reduce<W>(m, TC, nnew, wsum);
+        const int nu = (nnew <= kCountMax && nnew <= (int)blockDim.x) ? count_reduce<W>(m, TC, nnew)
+                                                                         : sort_reduce<W>(m, TC, nnew, wsum);
         const uint32_t nkeep = acc_decide<W>(P, m, c, TC, SM, nu, nm, wsum);
         if (threadIdx.x < 32) {
           int ab = 0;
