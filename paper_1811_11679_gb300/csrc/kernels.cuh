@@ -624,23 +624,38 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
   const int lane = (int)warp_lane();
   const int64_t total_warps = (int64_t)gridDim.x * kAttemptWarps;
   int sq_n = 0, pq_n = 0;   // warp-uniform queue lengths
-  for (int64_t gw = ((int64_t)blockIdx.x * kAttemptWarps + wid) * 32; gw < natt; gw += total_warps * 32) {
-    const int64_t g = gw + lane;
-    // parents of the warp's attempts: the first and last by binary search over
-    // the attempt offsets, each lane's inside that (short) range
-    int64_t plo = 0;
-    if (lane < 2) {
-      const int64_t gq = lane == 0 ? gw : (gw + 31 < natt ? gw + 31 : natt - 1);
+  // each warp owns one contiguous span of attempts; parents are monotone in
+  // the attempt index, so after one binary search at the span's start each
+  // step resolves its 32 parents from a window of 32 attempt offsets
+  const int64_t span = (((natt + total_warps - 1) / total_warps) + 31) & ~(int64_t)31;
+  const int64_t gbeg = ((int64_t)blockIdx.x * kAttemptWarps + wid) * span;
+  const int64_t gend = gbeg + span < natt ? gbeg + span : natt;
+  int64_t base = 0;   // a lower bound of the parent of the next attempt
+  if (gbeg < gend) {
+    if (lane == 0) {
       int64_t lo = 0, hi = n - 1;
       while (lo < hi) {
         int64_t mid = (lo + hi + 1) >> 1;
-        if (P.att_begin[mid] <= gq) lo = mid;
+        if (P.att_begin[mid] <= gbeg) lo = mid;
         else hi = mid - 1;
       }
-      plo = lo;
+      base = lo;
     }
-    const int64_t phi = __shfl_sync(0xffffffffu, plo, 1);
-    plo = __shfl_sync(0xffffffffu, plo, 0);
+    base = __shfl_sync(0xffffffffu, base, 0);
+  }
+  for (int64_t gw = gbeg; gw < gend; gw += 32) {
+    const int64_t g = gw + lane;
+    // window: offsets of the determinants base .. base + 31
+    const int64_t wi = base + lane;
+    const int64_t av = wi < n ? P.att_begin[wi] : INT64_MAX;
+    // number of window entries <= g (binary search over the lanes' values)
+    int cnt = 0;
+#pragma unroll
+    for (int step = 16; step; step >>= 1) {
+      const int64_t probe = __shfl_sync(0xffffffffu, av, cnt + step - 1);
+      if (probe <= g) cnt += step;
+    }
+    if (__shfl_sync(0xffffffffu, av, cnt < 32 ? cnt : 31) <= g && cnt == 31) cnt = 32;
     bool have = false, single = false;
     Key<W> child;
     int64_t amt = 0;
@@ -648,14 +663,24 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
     int64_t par = 0;
     uint64_t word = 0;
     uint16_t ia = 0;
-    if (g < natt) {
-      int64_t lo = plo, hi = phi;
-      while (lo < hi) {
-        int64_t mid = (lo + hi + 1) >> 1;
-        if (P.att_begin[mid] <= g) lo = mid;
-        else hi = mid - 1;
+    if (g < gend) {
+      if (cnt < 32) {
+        par = base + cnt - 1;
+      } else {   // beyond the window: search onwards from its last entry
+        int64_t lo = base + 31, hi = n - 1;
+        while (lo < hi) {
+          int64_t mid = (lo + hi + 1) >> 1;
+          if (P.att_begin[mid] <= g) lo = mid;
+          else hi = mid - 1;
+        }
+        par = lo;
       }
-      par = lo;
+    }
+    {
+      const int64_t lastpar = __shfl_sync(0xffffffffu, par, (int)((gend - 1 - gw) < 31 ? (gend - 1 - gw) : 31));
+      base = lastpar;
+    }
+    if (g < gend) {
       const uint64_t a = (uint64_t)(g - P.att_begin[par]);
       const Key<W> k = load_key<W>(key, P.cap, par);
       const uint8_t f = fl[par];
