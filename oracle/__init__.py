@@ -75,6 +75,8 @@ def _load():
         lib.orc_log.argtypes = [C.c_double]
         lib.orc_log.restype = C.c_double
         lib.orc_to_fixed.argtypes = [C.c_double, i64p, u64p]
+        lib.orc_fixed_product.argtypes = [C.c_double, C.c_double, C.c_int]
+        lib.orc_fixed_product.restype = C.c_uint64
         lib.orc_create.argtypes = [C.POINTER(_System), C.POINTER(_Qmc)]
         lib.orc_create.restype = P
         lib.orc_destroy.argtypes = [P]
@@ -136,6 +138,11 @@ def to_fixed(x: float) -> int:
     hi, lo = C.c_int64(), C.c_uint64()
     _load().orc_to_fixed(float(x), C.byref(hi), C.byref(lo))
     return (hi.value << 64) | lo.value
+
+
+def fixed_product(a: float, b: float, round_half: bool) -> int:
+    """floor(a b 2^32) (or floor(a b 2^32 + 1/2)) of the exact product, saturated at 2^62."""
+    return int(_load().orc_fixed_product(float(a), float(b), 1 if round_half else 0))
 
 
 class Oracle:

@@ -160,6 +160,34 @@ double from_fixed(i128 s) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Spawned amount in walker fixed point (units of 2^-32 walkers) from  */
+/* the exact product of two non-negative finite doubles:               */
+/*   round = 0: floor(a * b * 2^32)                                    */
+/*   round = 1: floor(a * b * 2^32 + 1/2)                              */
+/* One rounding of the exact product, no intermediate double rounding; */
+/* results at or above 2^62 saturate to 2^62.                          */
+/* ------------------------------------------------------------------ */
+const uint64_t AMOUNT_MAX = 1ull << 62;
+
+uint64_t fixed_product(double a, double b, int round) {
+    if (a == 0.0 || b == 0.0) return 0;
+    int ea, eb;
+    double fa = frexp(a, &ea), fb = frexp(b, &eb);   /* a = fa 2^ea, fa in [1/2, 1) */
+    uint64_t ma = (uint64_t)ldexp(fa, 53);           /* exact 53-bit integers */
+    uint64_t mb = (uint64_t)ldexp(fb, 53);
+    u128 p = (u128)ma * mb;                          /* a b 2^32 = p 2^(ea+eb-106+32) */
+    int e = ea + eb - 74;
+    if (e >= 0) {
+        if (e >= 62 || (p >> (62 - e)) != 0) return AMOUNT_MAX;
+        return (uint64_t)(p << e);
+    }
+    int s = -e;
+    if (s >= 120) return 0;                          /* p < 2^106: below 2^-14 */
+    u128 r = round ? ((p >> (s - 1)) + 1) >> 1 : p >> s;
+    return r >= (u128)AMOUNT_MAX ? AMOUNT_MAX : (uint64_t)r;
+}
+
+/* ------------------------------------------------------------------ */
 /* Determinant helpers.  Spin orbital p = 2*spatial + spin (alpha = 0), */
 /* bit p lives in word p/64.  Keys order as unsigned big integers       */
 /* (most significant word = word W-1).                                  */
@@ -245,6 +273,7 @@ struct Ctx {
     int period, initiator, real_amp, core_size, core_start;
     uint64_t seed, replica;
     int64_t target_fixed, init_thr;
+    uint64_t cutoff_fixed;   /* spawn cutoff in walker fixed point */
     /* state */
     Det d0;
     double e_ref;
@@ -686,22 +715,25 @@ void iterate_once(Ctx& c) {
             if (ex.null) continue;
             if (ex.hij == 0.0) continue;
             if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
-            /* spawn weight tau |H_ij| / p_gen, as a product with the reciprocal factors */
-            double m = ((c.tau * fabs(ex.hij)) * ex.inv_a) * ex.inv_b;
+            /* spawn weight tau |H_ij| / p_gen = |H_ij| * ct, ct = (tau inv_a) inv_b,
+             * taken exactly in walker fixed point (one rounding of the product) */
+            double ct = (c.tau * ex.inv_a) * ex.inv_b;
             int64_t q;
             if (!c.real_amp) {
-                double fl = floor(m);
-                double k = fl;
-                if (draw_unit(w[3]) < m - fl) k = k + 1.0;
-                if (k == 0.0) continue;
-                q = (int64_t)k * (int64_t)FIXED_ONE;
+                /* floor(m) walkers, one more with probability frac(m) (frac to 2^-32) */
+                uint64_t f = fixed_product(fabs(ex.hij), ct, 0);
+                uint64_t k = f >> 32;
+                if ((w[3] >> 32) < (f & 0xffffffffull)) k += 1;
+                if (k == 0) continue;
+                q = k >= (1ull << 30) ? (int64_t)AMOUNT_MAX : (int64_t)(k << 32);
             } else {
-                if (m < c.cutoff) {   /* kept with probability m / cutoff */
-                    if (draw_unit(w[3]) * c.cutoff < m) m = c.cutoff;
+                uint64_t r = fixed_product(fabs(ex.hij), ct, 1);
+                if (r < c.cutoff_fixed) {   /* kept, as the cutoff, with probability r / cutoff */
+                    if (draw_index(w[3], c.cutoff_fixed) < r) r = c.cutoff_fixed;
                     else continue;
                 }
-                q = llrint(m * 4294967296.0);
-                if (q == 0) continue;
+                if (r == 0) continue;
+                q = (int64_t)r;
             }
             int hs = ex.hij < 0.0 ? -1 : 1;
             Spawn s;
@@ -896,6 +928,7 @@ typedef struct {
 
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 double orc_log(double x) { return own_log(x); }
+uint64_t orc_fixed_product(double a, double b, int round) { return fixed_product(a, b, round); }
 void orc_to_fixed(double x, int64_t* hi, uint64_t* lo) {
     i128 v = to_fixed(x);
     *hi = (int64_t)(v >> 64);
@@ -983,6 +1016,8 @@ void* orc_create(const orc_system* s, const orc_qmc* q) {
                           ? INT64_MAX : llrint(c->target * 4294967296.0);
     c->init_thr = c->n_a * 4294967296.0 >= 9223372036854775807.0
                       ? INT64_MAX : llrint(c->n_a * 4294967296.0);
+    c->cutoff_fixed = c->cutoff * 4294967296.0 >= 4611686018427387904.0
+                          ? AMOUNT_MAX : (uint64_t)llrint(c->cutoff * 4294967296.0);
     /* p_single as an exact dyadic: threshold on the top 32 bits of a word */
     c->psingle_thr = (uint32_t)llrint(q->p_single * 4294967296.0);
     c->p_single = (double)c->psingle_thr * 0x1p-32;

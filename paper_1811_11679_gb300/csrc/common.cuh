@@ -13,6 +13,16 @@ namespace hande {
 
 constexpr int64_t kOne = int64_t(1) << 32;            // one walker
 constexpr uint64_t kDetDraw = ~0ull;                   // attempt index of per-determinant draws
+constexpr uint64_t kAmountMax = 1ull << 62;            // saturation of one spawned amount
+
+// x != 0.0 (either sign) from the bits, without the FP64 pipe
+__host__ __device__ __forceinline__ bool nonzero(double x) {
+#ifdef __CUDA_ARCH__
+  return ((uint64_t)__double_as_longlong(x) << 1) != 0;
+#else
+  return x != 0.0;
+#endif
+}
 
 // error bits (reported through the C ABI as hande_status codes)
 enum : unsigned {

@@ -84,7 +84,7 @@ struct HostTables {
   std::vector<int> hb_start, hb_len;
   std::vector<uint16_t> hb_ab;
   std::vector<uint64_t> hb_cum;
-  std::vector<double> hb_inv;
+  std::vector<double> hb_c;   // inv_b per entry, then (tau inv_a) inv_b
   std::vector<uint16_t> pair_ij;
   std::vector<double> single_g;
   std::vector<uint16_t> hb_guide;
@@ -210,7 +210,7 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           if (!(w > 0.0)) continue;
           T.hb_ab.push_back((uint16_t)(a | (b << 8)));
           T.hb_cum.push_back(0);
-          T.hb_inv.push_back(1.0);
+          T.hb_c.push_back(1.0);
           wts.push_back(w);
         }
       }
@@ -238,7 +238,7 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           uint64_t prev = 0;
           for (int k = 0; k < len; ++k) {
             uint64_t width = (k + 1 == len) ? (0ull - prev) : (T.hb_cum[start + k] - prev);
-            T.hb_inv[start + k] = 18446744073709551616.0 / (double)width;
+            T.hb_c[start + k] = 18446744073709551616.0 / (double)width;
             prev = T.hb_cum[start + k];
           }
         }
@@ -498,6 +498,9 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     P.W = E.W;
     P.tau = q.tau;
     P.cutoff = q.spawn_cutoff;
+    P.cutoff_fixed = q.spawn_cutoff * 4294967296.0 >= 4611686018427387904.0
+                         ? kAmountMax
+                         : (uint64_t)llrint(q.spawn_cutoff * 4294967296.0);
     P.zeta = q.shift_damping;
     P.real_amp = q.real_amplitudes ? 1 : 0;
     P.initiator = q.initiator ? 1 : 0;
@@ -556,18 +559,15 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     {
       const int n = sd.nel;
       const double npairs = (double)((int64_t)n * (n - 1) / 2);
-      sd.pg_hub = 1.0 / (2.0 * (double)n);
-      sd.pg_ueg[0] = 2.0 / (npairs * (double)s.norb);
-      sd.pg_ueg[1] = 1.0 / (npairs * (double)s.norb);
-      sd.pg_single[0] = sd.p_single / ((double)n * (double)(s.norb - s.nalpha));
-      sd.pg_single[1] = sd.p_single / ((double)n * (double)(s.norb - s.nbeta));
-      sd.pg_double = sd.p_double / npairs;
-      sd.inv_hub = 2.0 * (double)n;
-      sd.inv_ueg[0] = (npairs * (double)s.norb) / 2.0;
-      sd.inv_ueg[1] = (npairs * (double)s.norb) / 1.0;
-      sd.inv_single[0] = ((double)n * (double)(s.norb - s.nalpha)) / sd.p_single;
-      sd.inv_single[1] = ((double)n * (double)(s.norb - s.nbeta)) / sd.p_single;
-      sd.inv_double = npairs / sd.p_double;
+      // 1/p_gen = inv_a inv_b; spawn-weight factor (tau inv_a) inv_b
+      const double tau = q.tau;
+      sd.c_hub = tau * (2.0 * (double)n);
+      sd.c_ueg[0] = tau * ((npairs * (double)s.norb) / 2.0);
+      sd.c_ueg[1] = tau * ((npairs * (double)s.norb) / 1.0);
+      sd.c_single[0] = tau * (((double)n * (double)(s.norb - s.nalpha)) / sd.p_single);
+      sd.c_single[1] = tau * (((double)n * (double)(s.norb - s.nbeta)) / sd.p_single);
+      const double c_double = tau * (npairs / sd.p_double);
+      for (double& v : T.hb_c) v = c_double * v;
     }
     sd.kvec = upload(E, T.kvec);
     sd.klookup = upload(E, T.klookup);
@@ -577,7 +577,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.hb_len = upload(E, T.hb_len);
     sd.hb_ab = upload(E, T.hb_ab);
     sd.hb_cum = upload(E, T.hb_cum);
-    sd.hb_inv = upload(E, T.hb_inv);
+    sd.hb_c = upload(E, T.hb_c);
     for (int j = 1; j < sd.nel; ++j)
       for (int i = 0; i < j; ++i) T.pair_ij.push_back((uint16_t)(i | (j << 8)));
     sd.pair_ij = upload(E, T.pair_ij);

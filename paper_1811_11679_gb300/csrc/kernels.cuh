@@ -60,6 +60,7 @@ struct DevState {
 struct Params {
   // run
   double tau, cutoff, zeta;
+  uint64_t cutoff_fixed;   // spawn cutoff in walker fixed point
   int real_amp, initiator, period, W;
   int64_t init_thr, target_fixed;
   uint64_t seed, replica;
@@ -460,28 +461,61 @@ struct AttemptQueues {
   uint8_t* pq_flg;
 };
 
-// signed spawn amount (0 = nothing) for weight tau |H| inv_a inv_b, Philox word u
-__device__ __forceinline__ int64_t spawn_amount(const Params& P, double hij, double inv_a, double inv_b,
-                                                uint64_t u, uint8_t pf) {
-  double m = __dmul_rn(__dmul_rn(__dmul_rn(P.tau, fabs(hij)), inv_a), inv_b);
-  int64_t q = 0;
-  if (!P.real_amp) {
-    double flo = floor(m);
-    double kk = flo;
-    if (draw_unit(u) < __dsub_rn(m, flo)) kk = __dadd_rn(kk, 1.0);
-    if (kk != 0.0) q = (int64_t)kk * kOne;
+// floor(|h| ct 2^32) (half = false) or floor(|h| ct 2^32 + 1/2) (half = true)
+// of the exact product of two positive finite doubles given by their bits,
+// saturated at 2^62: 53x53-bit significand product on the integer pipe, one
+// rounding.  |h| ct 2^32 = m_h m_c 2^(e_h + e_c - 2 * 1075 + 32).
+__device__ __forceinline__ uint64_t fixed_amount(uint64_t hb, uint64_t cb, bool half) {
+  constexpr uint64_t kFrac = (1ull << 52) - 1;
+  int eh = (int)(hb >> 52), ec = (int)(cb >> 52);
+  uint64_t mh = hb & kFrac, mc = cb & kFrac;
+  if (eh) mh |= 1ull << 52;
+  else eh = 1;
+  if (ec) mc |= 1ull << 52;
+  else ec = 1;
+  const uint64_t lo = mh * mc, hi = __umul64hi(mh, mc);
+  const int e = eh + ec - 2118;
+  if (e >= 0) {
+    if (e >= 62 || hi != 0 || (lo >> (62 - e)) != 0) return kAmountMax;
+    return lo << e;
+  }
+  int sh = -e;
+  if (sh >= 120) return 0;
+  if (half) sh -= 1;   // floor(x + 1/2) = ceil(floor(2x) / 2)
+  uint64_t t, over;
+  if (sh >= 64) {
+    t = hi >> (sh - 64);
+    over = 0;
+  } else if (sh == 0) {
+    t = lo;
+    over = hi;
   } else {
-    bool keep = true;
-    if (m < P.cutoff) {   // kept with probability m / cutoff
-      if (__dmul_rn(draw_unit(u), P.cutoff) < m) m = P.cutoff;
-      else keep = false;
-    }
-    if (keep) q = __double2ll_rn(__dmul_rn(m, 4294967296.0));
+    t = (lo >> sh) | (hi << (64 - sh));
+    over = hi >> sh;
+  }
+  if (over) return kAmountMax;
+  if (half) t = (t >> 1) + (t & 1);
+  return t >= kAmountMax ? kAmountMax : t;
+}
+
+// signed spawn amount (0 = nothing) for the weight tau |H| / p_gen = |H| ct
+// (H != 0), Philox word u and parent flags pf; sign -sign(H) sign(N_parent)
+__device__ __forceinline__ int64_t spawn_amount(const Params& P, double hij, double ct, uint64_t u, uint8_t pf) {
+  const uint64_t hb = (uint64_t)__double_as_longlong(hij);
+  const uint64_t hab = hb & ~(1ull << 63), cb = (uint64_t)__double_as_longlong(ct);
+  uint64_t q;
+  if (!P.real_amp) {   // floor(m) walkers, one more with probability frac(m)
+    const uint64_t f = fixed_amount(hab, cb, false);
+    uint64_t k = f >> 32;
+    if ((u >> 32) < (f & 0xffffffffull)) k += 1;
+    q = k >= (1ull << 30) ? kAmountMax : k << 32;
+  } else {             // below the cutoff: kept, as the cutoff, with probability m / cutoff
+    q = fixed_amount(hab, cb, true);
+    if (q < P.cutoff_fixed) q = __umul64hi(u, P.cutoff_fixed) < q ? P.cutoff_fixed : 0;
   }
   if (q == 0) return 0;
-  int hs = hij < 0.0 ? -1 : 1;
-  int ps = (pf & F_NEG) ? -1 : 1;
-  return (-hs * ps) < 0 ? -q : q;
+  const bool neg = (hb >> 63) == (uint64_t)((pf & F_NEG) ? 1 : 0);
+  return neg ? -(int64_t)q : (int64_t)q;
 }
 
 // the top `take` queued spawns of this warp: bucket, rank, staging slot
@@ -569,8 +603,8 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
     key_flip<W>(child, i);
     key_flip<W>(child, a);
     const double hij = h_single<W, SYS>(P.sys, k, i, a);
-    if (hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
-      amt = spawn_amount(P, hij, P.sys.inv_single[i & 1], 1.0, u, f);
+    if (nonzero(hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
+      amt = spawn_amount(P, hij, P.sys.c_single[i & 1], u, f);
       initf = (f & F_INIT) ? 1 : 0;
       have = amt != 0;
     }
@@ -690,8 +724,8 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
         single = true;
         word = w.w;
         ia = (uint16_t)(ex.si | (ex.sa << 8));
-      } else if (ex.ok && ex.hij != 0.0 && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
-        amt = spawn_amount(P, ex.hij, ex.inv_a, ex.inv_b, w.w, f);
+      } else if (ex.ok && nonzero(ex.hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
+        amt = spawn_amount(P, ex.hij, ex.ct, w.w, f);
         child = ex.child;
         initf = (f & F_INIT) ? 1 : 0;
         have = amt != 0;

@@ -11,7 +11,7 @@
 // order with round-to-nearest intrinsics, so each element has one defined value.
 //
 // Generators (Sec. 2.4 "spawning": random selection of a connected state with
-// its generation probability) return the child and its exact p_gen:
+// its generation probability) return the child and the factor tau / p_gen:
 //   Hubbard   : uniform electron, uniform direction, p = 1/(2N)
 //   UEG       : uniform pair (i<j), uniform a of spin(i), b fixed by momentum,
 //               p = (2 if same spin else 1) / (C(N,2) M)
@@ -51,22 +51,15 @@ struct SysDev {
   // exchange kernel 4 pi / (Omega |k_k - k_l|^2) (UEG, norb^2)
   const double* orb_diag;
   const double* pair_diag;
-  // generation-probability factors that depend only on the system (electron
-  // and orbital counts), evaluated once on the host with the same expressions:
-  // Hubbard 1/(2N); UEG {2, 1}/(C(N,2) M) for same / opposite spins;
-  // heat-bath p_s/(N n_empty(spin)) per spin and p_d/C(N,2)
-  double pg_hub;
-  double pg_ueg[2];
-  double pg_single[2];
-  double pg_double;
-  // reciprocal factors of p_gen for the spawn weight tau |H| inv_a inv_b:
-  // 2N; C(N,2) M / {2, 1}; N n_empty / p_s; C(N,2) / p_d; and per heat-bath
-  // table entry 2^64 / width (1 for a one-entry table)
-  double inv_hub;
-  double inv_ueg[2];
-  double inv_single[2];
-  double inv_double;
-  const double* hb_inv;
+  // spawn-weight factors ct = (tau inv_a) inv_b with 1/p_gen = inv_a inv_b, so that
+  // tau |H| / p_gen = |H| ct; inv_a: 2N (Hubbard), C(N,2) M / {2, 1} (UEG, same /
+  // opposite spins), N n_empty(spin) / p_s (molecular singles), C(N,2) / p_d
+  // (heat-bath doubles); inv_b: 2^64 / width per heat-bath entry (1 for a
+  // one-entry table), else 1.  Evaluated once on the host.
+  double c_hub;
+  double c_ueg[2];
+  double c_single[2];
+  const double* hb_c;
   // pair index P = j(j-1)/2 + i -> (i | j << 8), i < j < nel
   const uint16_t* pair_ij;
   // molecule: single-excitation terms G[(i*nspin + a)*nspin + k] = (ia|kk) - (ik|ka)
@@ -223,9 +216,8 @@ template <int W>
 struct Excitation {
   bool ok;
   Key<W> child;
-  double pgen;
   double hij;
-  double inv_a, inv_b;   // 1/p_gen = inv_a * inv_b
+  double ct;             // tau / p_gen as (tau inv_a) inv_b
   bool single;           // a molecular single selected but not evaluated (DEFER)
   int si, sa;            // its hole and particle
 };
@@ -270,9 +262,7 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     }
     int q = 2 * ns + spin;
     if (key_bit<W>(d, q)) return e;
-    e.pgen = s.pg_hub;
-    e.inv_a = s.inv_hub;
-    e.inv_b = 1.0;
+    e.ct = s.c_hub;
     e.hij = h_single<W, SYS>(s, d, p, q);
     e.child = d;
     key_flip<W>(e.child, p);
@@ -293,9 +283,7 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     if (B < 0) return e;
     int b = 2 * B + (q & 1);
     if (a == b || key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
-    e.pgen = s.pg_ueg[(p ^ q) & 1];
-    e.inv_a = s.inv_ueg[(p ^ q) & 1];
-    e.inv_b = 1.0;
+    e.ct = s.c_ueg[(p ^ q) & 1];
     int lo = a < b ? a : b, hi = a < b ? b : a;
     e.hij = h_double<W, SYS>(s, d, p, q, lo, hi);
     e.child = d;
@@ -322,9 +310,7 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
         e.sa = a;
         return e;
       }
-      e.pgen = s.pg_single[i & 1];
-      e.inv_a = s.inv_single[i & 1];
-      e.inv_b = 1.0;
+      e.ct = s.c_single[i & 1];
       e.hij = h_single<W, SYS>(s, d, i, a);
       e.child = d;
       key_flip<W>(e.child, i);
@@ -353,17 +339,7 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     uint16_t ab = __ldg(&s.hb_ab[start + k]);
     int a = ab & 0xff, b = ab >> 8;
     if (key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
-    double pk;
-    if (len == 1) {
-      pk = 1.0;
-    } else {
-      uint64_t prev = k == 0 ? 0ull : __ldg(&s.hb_cum[start + k - 1]);
-      uint64_t width = (k + 1 == len) ? (0ull - prev) : (__ldg(&s.hb_cum[start + k]) - prev);
-      pk = __dmul_rn(__ull2double_rn(width), 0x1p-64);
-    }
-    e.pgen = __dmul_rn(s.pg_double, pk);
-    e.inv_a = s.inv_double;
-    e.inv_b = __ldg(&s.hb_inv[start + k]);
+    e.ct = __ldg(&s.hb_c[start + k]);
     e.hij = h_double<W, SYS>(s, d, p, q, a, b);
     e.child = d;
     key_flip<W>(e.child, p);

@@ -88,6 +88,24 @@ def test_fixed_point_is_round_half_even_of_scaled_value():
         assert oracle.to_fixed(float(v)) == fl, v
 
 
+def test_spawn_amount_is_one_rounding_of_the_exact_product():
+    """The spawned amount is floor(a b 2^32) or floor(a b 2^32 + 1/2) of the
+    exact rational product, saturated at 2^62 (checked with Fractions)."""
+    rng = np.random.default_rng(5)
+    a = list(np.abs(rng.normal(0, 1, 3000)) * 10.0 ** rng.integers(-12, 6, 3000))
+    b = list(np.abs(rng.normal(0, 1, 3000)) * 10.0 ** rng.integers(-4, 9, 3000))
+    # exact ties, subnormals, saturation, zero
+    a += [1.5 * 2.0 ** -32, 2.5 * 2.0 ** -32, 3.0 * 2.0 ** -40, 5e-324, 2.2e-308, 1.0, 2.0 ** 29, 0.0, 0.3]
+    b += [1.0, 1.0, 2.0 ** 7, 2.0 ** 1000, 3.0, 2.0 ** 30 - 1, 2.0 ** 33, 5.0, 0.0]
+    cap = 2 ** 62
+    for x, y in zip(a, b):
+        exact = Fraction(float(x)) * Fraction(float(y)) * 2 ** 32
+        fl = math.floor(exact)
+        rd = math.floor(exact + Fraction(1, 2))
+        assert oracle.fixed_product(x, y, False) == min(fl, cap), (x, y)
+        assert oracle.fixed_product(x, y, True) == min(rd, cap), (x, y)
+
+
 # --------------------------------------------------------------------------- Hamiltonians
 def _oracle_matrix(orc: oracle.Oracle, dets, W):
     n = len(dets)
