@@ -614,6 +614,36 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
   push_spawn<W>(P, Q, pq_n, have, child, amt, initf, nb, split, split_stride);
 }
 
+// largest i < n with a[i] <= x, given a[known] <= x (a non-decreasing):
+// doubling steps from `known`, then bisection
+__device__ __forceinline__ int64_t gallop_last_le(const int64_t* a, int64_t known, int64_t n, int64_t x) {
+  int64_t lo = known, hi, step = 1;
+  for (;;) {
+    hi = lo + step;
+    if (hi >= n) {
+      hi = n;
+      break;
+    }
+    if (a[hi] > x) break;
+    lo = hi;
+    step <<= 1;
+  }
+  while (hi - lo > 1) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (a[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+// lane l of a warp: av = a[base + l]; lane 31 also av32 = a[base + 32]
+// (INT64_MAX past n).  No lane waits for the loads here.
+__device__ __forceinline__ void load_window(const int64_t* a, int64_t n, int64_t base, int lane, int64_t& av,
+                                            int64_t& av32) {
+  const int64_t wi = base + lane;
+  av = wi < n ? a[wi] : INT64_MAX;
+  av32 = (lane == 31 && wi + 1 < n) ? a[wi + 1] : INT64_MAX;
+}
+
 template <int W, int SYS>
 __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) {
   DevState* st = P.st;
@@ -658,13 +688,16 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
   const int lane = (int)warp_lane();
   const int64_t total_warps = (int64_t)gridDim.x * kAttemptWarps;
   int sq_n = 0, pq_n = 0;   // warp-uniform queue lengths
-  // each warp owns one contiguous span of attempts; parents are monotone in
-  // the attempt index, so after one binary search at the span's start each
-  // step resolves its 32 parents from a window of 32 attempt offsets
+  // each warp owns one contiguous span of attempts, taken in chunks of 32.
+  // Parents are monotone in the attempt index: with base = the parent of a
+  // chunk's first attempt, the chunk's parents lie in base .. base + 31 unless
+  // determinants without attempts lie in between (then a galloping search).
+  // The offsets att_begin[base .. base + 32] of the next chunk are loaded while
+  // the current chunk is processed.
   const int64_t span = (((natt + total_warps - 1) / total_warps) + 31) & ~(int64_t)31;
   const int64_t gbeg = ((int64_t)blockIdx.x * kAttemptWarps + wid) * span;
   const int64_t gend = gbeg + span < natt ? gbeg + span : natt;
-  int64_t base = 0;   // a lower bound of the parent of the next attempt
+  int64_t base = 0, av = INT64_MAX, av32_l = INT64_MAX;
   if (gbeg < gend) {
     if (lane == 0) {
       int64_t lo = 0, hi = n - 1;
@@ -676,12 +709,11 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       base = lo;
     }
     base = __shfl_sync(0xffffffffu, base, 0);
+    load_window(P.att_begin, n, base, lane, av, av32_l);
   }
   for (int64_t gw = gbeg; gw < gend; gw += 32) {
     const int64_t g = gw + lane;
-    // window: offsets of the determinants base .. base + 31
-    const int64_t wi = base + lane;
-    const int64_t av = wi < n ? P.att_begin[wi] : INT64_MAX;
+    const int64_t av32 = __shfl_sync(0xffffffffu, av32_l, 31);
     // number of window entries <= g (binary search over the lanes' values)
     int cnt = 0;
 #pragma unroll
@@ -689,33 +721,37 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       const int64_t probe = __shfl_sync(0xffffffffu, av, cnt + step - 1);
       if (probe <= g) cnt += step;
     }
-    if (__shfl_sync(0xffffffffu, av, cnt < 32 ? cnt : 31) <= g && cnt == 31) cnt = 32;
+    const int64_t w_at = __shfl_sync(0xffffffffu, av, cnt == 0 ? 0 : (cnt < 32 ? cnt : 31));
+    if (w_at <= g && cnt == 31) cnt = 32;
+    int64_t par = base + cnt - 1;
+    int64_t abeg = __shfl_sync(0xffffffffu, av, (cnt - 1) & 31);
+    const bool beyond = g < gend && cnt == 32 && g >= av32;   // past att_begin[base + 32]
+    // next chunk: its base, and its window in flight during this chunk
+    const int64_t X = gw + 32;
+    if (X < gend) {
+      const int c = __popc(__ballot_sync(0xffffffffu, av <= X));
+      int64_t nbase;
+      if (c < 32) nbase = base + c - 1;
+      else if (X < av32) nbase = base + 31;
+      else nbase = gallop_last_le(P.att_begin, base + 31, n, X);
+      load_window(P.att_begin, n, nbase, lane, av, av32_l);
+      if (beyond) {
+        par = gallop_last_le(P.att_begin, base + 31, n, g);
+        abeg = P.att_begin[par];
+      }
+      base = nbase;
+    } else if (beyond) {
+      par = gallop_last_le(P.att_begin, base + 31, n, g);
+      abeg = P.att_begin[par];
+    }
     bool have = false, single = false;
     Key<W> child;
     int64_t amt = 0;
     uint8_t initf = 0;
-    int64_t par = 0;
     uint64_t word = 0;
     uint16_t ia = 0;
     if (g < gend) {
-      if (cnt < 32) {
-        par = base + cnt - 1;
-      } else {   // beyond the window: search onwards from its last entry
-        int64_t lo = base + 31, hi = n - 1;
-        while (lo < hi) {
-          int64_t mid = (lo + hi + 1) >> 1;
-          if (P.att_begin[mid] <= g) lo = mid;
-          else hi = mid - 1;
-        }
-        par = lo;
-      }
-    }
-    {
-      const int64_t lastpar = __shfl_sync(0xffffffffu, par, (int)((gend - 1 - gw) < 31 ? (gend - 1 - gw) : 31));
-      base = lastpar;
-    }
-    if (g < gend) {
-      const uint64_t a = (uint64_t)(g - P.att_begin[par]);
+      const uint64_t a = (uint64_t)(g - abeg);
       const Key<W> k = load_key<W>(key, P.cap, par);
       const uint8_t f = fl[par];
       const Words4 w = draw<W>(P.seed, P.replica, t, a, k);
