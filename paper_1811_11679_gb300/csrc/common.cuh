@@ -127,6 +127,47 @@ __device__ __forceinline__ int select_bit(const Key<W>& k, int r) {
   return -1;
 }
 
+// floor(|h| ct 2^32) (half = false) or floor(|h| ct 2^32 + 1/2) (half = true)
+// of the exact product of two positive finite doubles given by their bits,
+// saturated at 2^62: 53x53-bit significand product on the integer pipe, one
+// rounding.  |h| ct 2^32 = m_h m_c 2^(e_h + e_c - 2 * 1075 + 32).
+__device__ __forceinline__ uint64_t fixed_amount(uint64_t hb, uint64_t cb, bool half) {
+  constexpr uint64_t kFrac = (1ull << 52) - 1;
+  int eh = (int)(hb >> 52), ec = (int)(cb >> 52);
+  uint64_t mh = hb & kFrac, mc = cb & kFrac;
+  if (eh) mh |= 1ull << 52;
+  else eh = 1;
+  if (ec) mc |= 1ull << 52;
+  else ec = 1;
+  const uint64_t lo = mh * mc, hi = __umul64hi(mh, mc);
+  const int e = eh + ec - 2118;
+  if (e >= 0) {
+    if (e >= 62 || hi != 0 || (lo >> (62 - e)) != 0) return kAmountMax;
+    return lo << e;
+  }
+  int sh = -e;
+  if (sh >= 120) return 0;
+  if (half) sh -= 1;   // floor(x + 1/2) = ceil(floor(2x) / 2)
+  uint64_t t, over;
+  if (sh >= 64) {
+    t = hi >> (sh - 64);
+    over = 0;
+  } else if (sh == 0) {
+    t = lo;
+    over = hi;
+  } else {
+    t = (lo >> sh) | (hi << (64 - sh));
+    over = hi >> sh;
+  }
+  if (over) return kAmountMax;
+  if (half) t = (t >> 1) + (t & 1);
+  return t >= kAmountMax ? kAmountMax : t;
+}
+
+__device__ __forceinline__ uint64_t dbl_bits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ uint64_t abs_bits(double x) { return dbl_bits(x) & ~(1ull << 63); }
+__device__ __forceinline__ bool sign_bit(double x) { return (dbl_bits(x) >> 63) != 0; }
+
 // ------------------------------------------------------------------ Philox4x64-10
 // Counter-based generator of Salmon et al. (SC'11): 10 rounds of two 64x64->128
 // multiplies with Weyl key increments.

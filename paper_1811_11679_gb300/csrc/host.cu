@@ -81,10 +81,12 @@ struct HostTables {
   std::vector<int4> kvec;
   std::vector<int16_t> klookup;
   std::vector<double> h1, eri_packed;
-  std::vector<int> hb_start, hb_len;
-  std::vector<uint16_t> hb_ab;
+  std::vector<int4> hb_pair;     // {start, len, guide offset, guide bits}
+  std::vector<uint16_t> hb_ab;   // a | b << 8
+  std::vector<double> hb_v;      // <pq||ab> (signed)
   std::vector<uint64_t> hb_cum;
-  std::vector<double> hb_c;   // inv_b per entry, then (tau inv_a) inv_b
+  std::vector<double> hb_inv;    // inv_b = 2^64 / width (1 for a one-entry table)
+  std::vector<ulonglong2> hb_ent;
   std::vector<uint16_t> pair_ij;
   std::vector<double> single_g;
   std::vector<uint16_t> hb_guide;
@@ -148,6 +150,33 @@ void build_ueg(const hande_system& s, SysDev& sd, HostTables& T) {
   }
 }
 
+// floor(x y 2^32) (half = false) or floor(x y 2^32 + 1/2) (half = true) of the
+// exact product of two non-negative finite doubles, saturated at 2^62 (the
+// device computes the same in fixed_amount)
+uint64_t host_fixed_amount(double x, double y, bool half) {
+  if (x == 0.0 || y == 0.0) return 0;
+  uint64_t xb, yb;
+  std::memcpy(&xb, &x, 8);
+  std::memcpy(&yb, &y, 8);
+  int ex = (int)(xb >> 52), ey = (int)(yb >> 52);
+  uint64_t mx = xb & ((1ull << 52) - 1), my = yb & ((1ull << 52) - 1);
+  if (ex) mx |= 1ull << 52;
+  else ex = 1;
+  if (ey) my |= 1ull << 52;
+  else ey = 1;
+  const unsigned __int128 prod = (unsigned __int128)mx * my;   // x y 2^32 = prod 2^(ex + ey - 2118)
+  const int e = ex + ey - 2118;
+  const uint64_t cap = 1ull << 62;
+  if (e >= 0) {
+    if (e >= 62 || (prod >> (62 - e)) != 0) return cap;
+    return (uint64_t)(prod << e);
+  }
+  const int sh = -e;
+  if (sh >= 120) return 0;
+  const unsigned __int128 r = half ? ((prod >> (sh - 1)) + 1) >> 1 : prod >> sh;
+  return r >= cap ? cap : (uint64_t)r;
+}
+
 double g_so(const std::vector<double>& eri, int n, int p, int q, int r, int t) {
   if (((p ^ q) & 1) || ((r ^ t) & 1)) return 0.0;
   size_t N = (size_t)n;
@@ -192,8 +221,7 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
   // (a, b) order, as cumulative thresholds floor(2^64 S_k / S_total) made strictly
   // increasing; the last entry takes the remainder.
   const int ns = 2 * n;
-  T.hb_start.assign((size_t)ns * (ns - 1) / 2, 0);
-  T.hb_len.assign((size_t)ns * (ns - 1) / 2, 0);
+  std::vector<int> hb_start((size_t)ns * (ns - 1) / 2, 0), hb_len((size_t)ns * (ns - 1) / 2, 0);
   for (int qq = 1; qq < ns; ++qq) {
     for (int pp = 0; pp < qq; ++pp) {
       const int idx = qq * (qq - 1) / 2 + pp;
@@ -209,14 +237,15 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           double w = std::fabs(v);
           if (!(w > 0.0)) continue;
           T.hb_ab.push_back((uint16_t)(a | (b << 8)));
+          T.hb_v.push_back(v);
           T.hb_cum.push_back(0);
-          T.hb_c.push_back(1.0);
+          T.hb_inv.push_back(1.0);
           wts.push_back(w);
         }
       }
       const int len = (int)wts.size();
-      T.hb_start[idx] = start;
-      T.hb_len[idx] = len;
+      hb_start[idx] = start;
+      hb_len[idx] = len;
       if (len > 0) {
         std::vector<double> run(len);
         double acc = 0.0;
@@ -238,7 +267,7 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
           uint64_t prev = 0;
           for (int k = 0; k < len; ++k) {
             uint64_t width = (k + 1 == len) ? (0ull - prev) : (T.hb_cum[start + k] - prev);
-            T.hb_c[start + k] = 18446744073709551616.0 / (double)width;
+            T.hb_inv[start + k] = 18446744073709551616.0 / (double)width;
             prev = T.hb_cum[start + k];
           }
         }
@@ -253,17 +282,27 @@ void build_molecule(const hande_system& s, const hande_qmc& q, SysDev& sd, HostT
       for (int k = 0; k < ns; ++k)
         T.single_g[((size_t)i * ns + a) * ns + k] = g_so(eri, n, i, a, k, k) - g_so(eri, n, i, k, k, a);
     }
-  // guide index of every heat-bath table
-  T.hb_guide.assign((size_t)ns * (ns - 1) / 2 * 65, 0);
-  for (int idx = 0; idx < ns * (ns - 1) / 2; ++idx) {
-    const int start = T.hb_start[idx], len = T.hb_len[idx];
+  // guide of every heat-bath table: 2^g buckets with 2^g >= 2 len; for
+  // t = 0 .. 2^g the first entry (among the first len - 1) whose threshold
+  // exceeds t 2^(64-g), else len - 1
+  T.hb_pair.assign(hb_start.size(), make_int4(0, 0, 0, 1));
+  for (size_t idx = 0; idx < hb_start.size(); ++idx) {
+    const int start = hb_start[idx], len = hb_len[idx];
     if (len > 65535) throw Fail{HANDE_ERR_INVALID, "heat-bath table too long"};
+    if (len == 0) continue;
+    int g = 1;
+    while ((1 << g) < 2 * len) ++g;
+    const int goff = (int)T.hb_guide.size();
+    T.hb_pair[idx] = make_int4(start, len, goff, g);
     int k = 0;
-    for (int g = 0; g <= 64; ++g) {
-      // first entry k (among the first len-1) with cum[k] > g * 2^58, else len - 1
-      const unsigned long long bound = g == 64 ? ~0ull : ((unsigned long long)g << 58);
-      while (k < len - 1 && !(T.hb_cum[start + k] > bound)) ++k;
-      T.hb_guide[(size_t)idx * 65 + g] = (uint16_t)(len > 0 ? k : 0);
+    for (uint64_t t = 0; t <= (1ull << g); ++t) {
+      if (t < (1ull << g)) {
+        const uint64_t bound = t << (64 - g);
+        while (k < len - 1 && !(T.hb_cum[start + k] > bound)) ++k;
+      } else {
+        k = len - 1;
+      }
+      T.hb_guide.push_back((uint16_t)k);
     }
   }
   sd.psingle_thr = (uint32_t)llrint(q.p_single * 4294967296.0);
@@ -566,18 +605,23 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
       sd.c_ueg[1] = tau * ((npairs * (double)s.norb) / 1.0);
       sd.c_single[0] = tau * (((double)n * (double)(s.norb - s.nalpha)) / sd.p_single);
       sd.c_single[1] = tau * (((double)n * (double)(s.norb - s.nbeta)) / sd.p_single);
+      sd.half = q.real_amplitudes ? 1 : 0;
+      // heat-bath entries: spawn amount of |<pq||ab>| ((tau inv_a) inv_b), then (a, b, sign)
       const double c_double = tau * (npairs / sd.p_double);
-      for (double& v : T.hb_c) v = c_double * v;
+      T.hb_ent.resize(T.hb_ab.size());
+      for (size_t k = 0; k < T.hb_ab.size(); ++k) {
+        const double v = T.hb_v[k];
+        T.hb_ent[k].x = host_fixed_amount(std::fabs(v), c_double * T.hb_inv[k], sd.half != 0);
+        T.hb_ent[k].y = (unsigned long long)T.hb_ab[k] | ((v < 0.0 ? 1ull : 0ull) << 16);
+      }
     }
     sd.kvec = upload(E, T.kvec);
     sd.klookup = upload(E, T.klookup);
     sd.h1 = upload(E, T.h1);
     sd.eri = upload(E, T.eri_packed);
-    sd.hb_start = upload(E, T.hb_start);
-    sd.hb_len = upload(E, T.hb_len);
-    sd.hb_ab = upload(E, T.hb_ab);
+    sd.hb_pair = upload(E, T.hb_pair);
     sd.hb_cum = upload(E, T.hb_cum);
-    sd.hb_c = upload(E, T.hb_c);
+    sd.hb_ent = upload(E, T.hb_ent);
     for (int j = 1; j < sd.nel; ++j)
       for (int i = 0; i < j; ++i) T.pair_ij.push_back((uint16_t)(i | (j << 8)));
     sd.pair_ij = upload(E, T.pair_ij);

@@ -446,9 +446,16 @@ template <int W>
 __host__ __device__ constexpr int attempt_split_smem() {
   return W == 8 ? 256 : (W == 2 ? 2048 : 4096);
 }
-template <int W>
+// molecular generator tables copied to shared memory for 64-bit keys (at most
+// 64 spin orbitals): the pair records (int4) and the pair unranking table
+constexpr int kStagePairs = 64 * 63 / 2;
+template <int W, int SYS>
+__host__ __device__ constexpr size_t attempt_stage_bytes() {
+  return (SYS == SYS_MOLECULE && W == 1) ? (size_t)kStagePairs * (16 + 2) : 0;
+}
+template <int W, int SYS>
 __host__ __device__ inline size_t attempt_smem_bytes() {
-  return (size_t)attempt_split_smem<W>() * 8 * W +
+  return (size_t)attempt_split_smem<W>() * 8 * W + attempt_stage_bytes<W, SYS>() +
          (size_t)kAttemptWarps * kQueue * (8 + 8 + 2 + 8 * W + 8 + 1) + 256;
 }
 
@@ -461,60 +468,21 @@ struct AttemptQueues {
   uint8_t* pq_flg;
 };
 
-// floor(|h| ct 2^32) (half = false) or floor(|h| ct 2^32 + 1/2) (half = true)
-// of the exact product of two positive finite doubles given by their bits,
-// saturated at 2^62: 53x53-bit significand product on the integer pipe, one
-// rounding.  |h| ct 2^32 = m_h m_c 2^(e_h + e_c - 2 * 1075 + 32).
-__device__ __forceinline__ uint64_t fixed_amount(uint64_t hb, uint64_t cb, bool half) {
-  constexpr uint64_t kFrac = (1ull << 52) - 1;
-  int eh = (int)(hb >> 52), ec = (int)(cb >> 52);
-  uint64_t mh = hb & kFrac, mc = cb & kFrac;
-  if (eh) mh |= 1ull << 52;
-  else eh = 1;
-  if (ec) mc |= 1ull << 52;
-  else ec = 1;
-  const uint64_t lo = mh * mc, hi = __umul64hi(mh, mc);
-  const int e = eh + ec - 2118;
-  if (e >= 0) {
-    if (e >= 62 || hi != 0 || (lo >> (62 - e)) != 0) return kAmountMax;
-    return lo << e;
-  }
-  int sh = -e;
-  if (sh >= 120) return 0;
-  if (half) sh -= 1;   // floor(x + 1/2) = ceil(floor(2x) / 2)
-  uint64_t t, over;
-  if (sh >= 64) {
-    t = hi >> (sh - 64);
-    over = 0;
-  } else if (sh == 0) {
-    t = lo;
-    over = hi;
-  } else {
-    t = (lo >> sh) | (hi << (64 - sh));
-    over = hi >> sh;
-  }
-  if (over) return kAmountMax;
-  if (half) t = (t >> 1) + (t & 1);
-  return t >= kAmountMax ? kAmountMax : t;
-}
-
-// signed spawn amount (0 = nothing) for the weight tau |H| / p_gen = |H| ct
-// (H != 0), Philox word u and parent flags pf; sign -sign(H) sign(N_parent)
-__device__ __forceinline__ int64_t spawn_amount(const Params& P, double hij, double ct, uint64_t u, uint8_t pf) {
-  const uint64_t hb = (uint64_t)__double_as_longlong(hij);
-  const uint64_t hab = hb & ~(1ull << 63), cb = (uint64_t)__double_as_longlong(ct);
+// signed spawn amount (0 = nothing) from the fixed-point amount famt of the
+// weight tau |H| / p_gen (floored for integer walkers, rounded for real
+// weights), Philox word u and parent flags pf; sign -sign(H) sign(N_parent)
+__device__ __forceinline__ int64_t spawn_amount(const Params& P, uint64_t famt, bool hneg, uint64_t u, uint8_t pf) {
   uint64_t q;
   if (!P.real_amp) {   // floor(m) walkers, one more with probability frac(m)
-    const uint64_t f = fixed_amount(hab, cb, false);
-    uint64_t k = f >> 32;
-    if ((u >> 32) < (f & 0xffffffffull)) k += 1;
+    uint64_t k = famt >> 32;
+    if ((u >> 32) < (famt & 0xffffffffull)) k += 1;
     q = k >= (1ull << 30) ? kAmountMax : k << 32;
   } else {             // below the cutoff: kept, as the cutoff, with probability m / cutoff
-    q = fixed_amount(hab, cb, true);
+    q = famt;
     if (q < P.cutoff_fixed) q = __umul64hi(u, P.cutoff_fixed) < q ? P.cutoff_fixed : 0;
   }
   if (q == 0) return 0;
-  const bool neg = (hb >> 63) == (uint64_t)((pf & F_NEG) ? 1 : 0);
+  const bool neg = hneg == ((pf & F_NEG) != 0);
   return neg ? -(int64_t)q : (int64_t)q;
 }
 
@@ -604,7 +572,8 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
     key_flip<W>(child, a);
     const double hij = h_single<W, SYS>(P.sys, k, i, a);
     if (nonzero(hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
-      amt = spawn_amount(P, hij, P.sys.c_single[i & 1], u, f);
+      const uint64_t famt = fixed_amount(abs_bits(hij), dbl_bits(P.sys.c_single[i & 1]), P.sys.half);
+      amt = spawn_amount(P, famt, sign_bit(hij), u, f);
       initf = (f & F_INIT) ? 1 : 0;
       have = amt != 0;
     }
@@ -654,7 +623,7 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
   const int wid = threadIdx.x >> 5;
   AttemptQueues Q;
   {
-    unsigned char* p = att_smem + (size_t)KS * 8 * W;
+    unsigned char* p = att_smem + (size_t)KS * 8 * W + attempt_stage_bytes<W, SYS>();
     const size_t per = kQueue;
     Q.sq_par = reinterpret_cast<int64_t*>(p) + wid * per;
     p += kAttemptWarps * per * 8;
@@ -681,6 +650,16 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
 #pragma unroll
       for (int j = 0; j < W; ++j) ssplit[j * KS + b] = P.split_key[j * P.cap + b];
     }
+  }
+  GenTabs gt{P.sys.hb_pair, P.sys.pair_ij};
+  if (attempt_stage_bytes<W, SYS>() > 0) {
+    int4* sp = reinterpret_cast<int4*>(att_smem + (size_t)KS * 8 * W);
+    uint16_t* sij = reinterpret_cast<uint16_t*>(att_smem + (size_t)KS * 8 * W + (size_t)kStagePairs * 16);
+    const int npp = P.sys.nspin * (P.sys.nspin - 1) / 2, nij = P.sys.nel * (P.sys.nel - 1) / 2;
+    for (int i = threadIdx.x; i < npp; i += blockDim.x) sp[i] = P.sys.hb_pair[i];
+    for (int i = threadIdx.x; i < nij; i += blockDim.x) sij[i] = P.sys.pair_ij[i];
+    gt.hb_pair = sp;
+    gt.pair_ij = sij;
   }
   __syncthreads();
   const uint64_t* split = split_on_chip ? ssplit : P.split_key;
@@ -755,13 +734,13 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       const Key<W> k = load_key<W>(key, P.cap, par);
       const uint8_t f = fl[par];
       const Words4 w = draw<W>(P.seed, P.replica, t, a, k);
-      const Excitation<W> ex = generate<W, SYS, true>(P.sys, k, w);
+      const Excitation<W> ex = generate<W, SYS>(P.sys, gt, k, w);
       if (ex.single) {
         single = true;
         word = w.w;
         ia = (uint16_t)(ex.si | (ex.sa << 8));
-      } else if (ex.ok && nonzero(ex.hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
-        amt = spawn_amount(P, ex.hij, ex.ct, w.w, f);
+      } else if (ex.ok && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
+        amt = spawn_amount(P, ex.famt, ex.hneg, w.w, f);
         child = ex.child;
         initf = (f & F_INIT) ? 1 : 0;
         have = amt != 0;

@@ -136,7 +136,7 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
     k_core_apply<<<nb, 256, 0, s>>>(P, cur);
   }
   mark(4);
-  k_attempt<W, SYS><<<E.attempt_grid, kAttemptThreads, attempt_smem_bytes<W>(), s>>>(P, cur);
+  k_attempt<W, SYS><<<E.attempt_grid, kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(P, cur);
   mark(5);
   int64_t* nbk = st_field_i64(st, offsetof(DevState, nbuckets));
   k_scan_reduce<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, nbk, P.part, st);
@@ -207,7 +207,7 @@ Ops make_ops() {
   o.merge_smem = &merge_smem_w<W>;
   o.merge_kernel = (const void*)&k_merge<W, SYS>;
   o.attempt_kernel = (const void*)&k_attempt<W, SYS>;
-  o.attempt_smem = attempt_smem_bytes<W>();
+  o.attempt_smem = attempt_smem_bytes<W, SYS>();
   return o;
 }
 

@@ -39,11 +39,17 @@ struct SysDev {
   const double* h1;
   const double* eri;
   double ecore;
-  // heat-bath tables per occupied pair index q(q-1)/2 + p
-  const int* hb_start;
-  const int* hb_len;
-  const uint16_t* hb_ab;   // a | b << 8
+  // heat-bath tables, per occupied spin-orbital pair index q(q-1)/2 + p (p < q):
+  // hb_pair = {first entry, entry count, guide offset, guide bits g}; per entry
+  // the cumulative threshold hb_cum (strictly increasing, the last 2^64 - 1) and
+  // hb_ent = {fixed-point spawn amount of |<pq||ab>| tau / p_gen,
+  // a | b << 8 | (<pq||ab> < 0) << 16}.  Guide: for t = 0 .. 2^g, the first
+  // entry whose threshold exceeds t 2^(64-g) (clamped to the last), so the entry
+  // drawn by word w lies in [guide[w >> (64-g)], guide[(w >> (64-g)) + 1]].
+  const int4* hb_pair;
   const uint64_t* hb_cum;
+  const ulonglong2* hb_ent;
+  const uint16_t* hb_guide;
   uint32_t psingle_thr;
   double p_single, p_double;
   // diagonal tables: orb_diag[k] = h_kk (molecule, spin orbitals) or |k|^2/2
@@ -54,21 +60,17 @@ struct SysDev {
   // spawn-weight factors ct = (tau inv_a) inv_b with 1/p_gen = inv_a inv_b, so that
   // tau |H| / p_gen = |H| ct; inv_a: 2N (Hubbard), C(N,2) M / {2, 1} (UEG, same /
   // opposite spins), N n_empty(spin) / p_s (molecular singles), C(N,2) / p_d
-  // (heat-bath doubles); inv_b: 2^64 / width per heat-bath entry (1 for a
-  // one-entry table), else 1.  Evaluated once on the host.
+  // (heat-bath doubles, folded into hb_ent); inv_b: 2^64 / width per heat-bath
+  // entry (1 for a one-entry table), else 1.  Evaluated once on the host.
   double c_hub;
   double c_ueg[2];
   double c_single[2];
-  const double* hb_c;
+  int half;   // spawn amounts rounded to nearest (real weights) or floored (integer walkers)
   // pair index P = j(j-1)/2 + i -> (i | j << 8), i < j < nel
   const uint16_t* pair_ij;
   // molecule: single-excitation terms G[(i*nspin + a)*nspin + k] = (ia|kk) - (ik|ka)
   // over spin orbitals (each the same one-rounding difference the sum adds)
   const double* single_g;
-  // heat-bath guide: for table t and g = 0..64, the first entry whose threshold
-  // exceeds g * 2^58 (clamped to len - 1): the search for word w starts in
-  // [guide[w >> 58], guide[(w >> 58) + 1]]
-  const uint16_t* hb_guide;
 };
 
 __device__ __forceinline__ int tri(int p, int q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
@@ -214,17 +216,24 @@ __device__ double h_elem(const SysDev& s, const Key<W>& src, const Key<W>& tgt) 
 
 template <int W>
 struct Excitation {
-  bool ok;
+  bool ok;               // a connected child with H != 0 was drawn
+  bool single;           // a molecular single: selected only (si, sa), evaluated later
+  bool hneg;             // H_child,parent < 0
+  int si, sa;
+  uint64_t famt;         // fixed-point amount of |H| tau / p_gen (floored or rounded)
   Key<W> child;
-  double hij;
-  double ct;             // tau / p_gen as (tau inv_a) inv_b
-  bool single;           // a molecular single selected but not evaluated (DEFER)
-  int si, sa;            // its hole and particle
+};
+
+// tables of the molecular generator read on every attempt; the kernel points
+// them at shared-memory copies when they fit
+struct GenTabs {
+  const int4* hb_pair;
+  const uint16_t* pair_ij;
 };
 
 // pair index P = j(j-1)/2 + i  ->  (i, j), i < j (tabulated)
-__device__ __forceinline__ void unrank_pair(const SysDev& s, uint64_t P, int& i, int& j) {
-  uint16_t v = __ldg(&s.pair_ij[P]);
+__device__ __forceinline__ void unrank_pair(const uint16_t* pair_ij, uint64_t P, int& i, int& j) {
+  uint16_t v = pair_ij[P];
   i = v & 0xff;
   j = v >> 8;
 }
@@ -243,13 +252,25 @@ __device__ __forceinline__ Key<W> spin_mask(int spin, int nspin) {
   return m;
 }
 
-// DEFER: a molecular single excitation is only selected (e.single, e.si, e.sa);
-// its matrix element is left to the caller (evaluated later by full warps).
-template <int W, int SYS, bool DEFER = false>
-__device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4& w) {
+template <int W>
+__device__ __forceinline__ void finish(Excitation<W>& e, const SysDev& s, double hij, double ct) {
+  if (!nonzero(hij)) return;
+  e.famt = fixed_amount(abs_bits(hij), dbl_bits(ct), s.half);
+  e.hneg = sign_bit(hij);
+  e.ok = true;
+}
+
+// One excitation drawn from Philox words w (Sec. 2.4 spawning): the child, the
+// sign of its matrix element and the fixed-point amount of |H| tau / p_gen.
+// A molecular single is only selected (e.single, e.si, e.sa); its O(N) matrix
+// element is left to the caller.
+template <int W, int SYS>
+__device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<W>& d, const Words4& w) {
   Excitation<W> e;
   e.ok = false;
   e.single = false;
+  e.hneg = false;
+  e.famt = 0;
   const int n = s.nel;
   if (SYS == SYS_HUBBARD) {
     int p = select_bit<W>(d, (int)draw_index(w.x, (uint64_t)n));
@@ -262,17 +283,15 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     }
     int q = 2 * ns + spin;
     if (key_bit<W>(d, q)) return e;
-    e.ct = s.c_hub;
-    e.hij = h_single<W, SYS>(s, d, p, q);
     e.child = d;
     key_flip<W>(e.child, p);
     key_flip<W>(e.child, q);
-    e.ok = true;
+    finish<W>(e, s, h_single<W, SYS>(s, d, p, q), s.c_hub);
     return e;
   } else if (SYS == SYS_UEG) {
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;
     int ii, jj;
-    unrank_pair(s, draw_index(w.y, npairs), ii, jj);
+    unrank_pair(gt.pair_ij, draw_index(w.y, npairs), ii, jj);
     int p = select_bit<W>(d, ii), q = select_bit<W>(d, jj);
     int A = (int)draw_index(w.z, (uint64_t)s.norb);
     int a = 2 * A + (p & 1);
@@ -283,15 +302,13 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
     if (B < 0) return e;
     int b = 2 * B + (q & 1);
     if (a == b || key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
-    e.ct = s.c_ueg[(p ^ q) & 1];
     int lo = a < b ? a : b, hi = a < b ? b : a;
-    e.hij = h_double<W, SYS>(s, d, p, q, lo, hi);
     e.child = d;
     key_flip<W>(e.child, p);
     key_flip<W>(e.child, q);
     key_flip<W>(e.child, a);
     key_flip<W>(e.child, b);
-    e.ok = true;
+    finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo, hi), s.c_ueg[(p ^ q) & 1]);
     return e;
   } else {
     if ((uint32_t)(w.x >> 32) < s.psingle_thr) {
@@ -303,49 +320,40 @@ __device__ Excitation<W> generate(const SysDev& s, const Key<W>& d, const Words4
 #pragma unroll
       for (int j = 0; j < W; ++j) ne += __popcll(empty.w[j]);
       if (ne == 0) return e;
-      int a = select_bit<W>(empty, (int)draw_index(w.z, (uint64_t)ne));
-      if (DEFER) {
-        e.single = true;
-        e.si = i;
-        e.sa = a;
-        return e;
-      }
-      e.ct = s.c_single[i & 1];
-      e.hij = h_single<W, SYS>(s, d, i, a);
-      e.child = d;
-      key_flip<W>(e.child, i);
-      key_flip<W>(e.child, a);
-      e.ok = true;
+      e.single = true;
+      e.si = i;
+      e.sa = select_bit<W>(empty, (int)draw_index(w.z, (uint64_t)ne));
       return e;
     }
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;
     int ii, jj;
-    unrank_pair(s, draw_index(w.y, npairs), ii, jj);
+    unrank_pair(gt.pair_ij, draw_index(w.y, npairs), ii, jj);
     int p = select_bit<W>(d, ii), q = select_bit<W>(d, jj);
-    int pidx = q * (q - 1) / 2 + p;
-    int len = __ldg(&s.hb_len[pidx]);
-    if (len == 0) return e;
-    int start = __ldg(&s.hb_start[pidx]);
-    // smallest k with w.z < cum[k] among the first len-1 entries, else the last
-    const uint16_t* gd = s.hb_guide + (size_t)pidx * 65;
-    const int gt = (int)(w.z >> 58);
-    int lo = __ldg(&gd[gt]), hi = __ldg(&gd[gt + 1]);
+    const int4 pr = gt.hb_pair[q * (q - 1) / 2 + p];   // {start, len, guide offset, guide bits}
+    if (pr.y == 0) return e;
+    // smallest k with w.z < cum[k] among the first len - 1 entries, else the last
+    const uint64_t t = w.z >> (64 - pr.w);
+    int lo = __ldg(&s.hb_guide[pr.z + t]), hi = __ldg(&s.hb_guide[pr.z + t + 1]);
     while (lo < hi) {
       int mid = (lo + hi) >> 1;
-      if (__ldg(&s.hb_cum[start + mid]) <= w.z) lo = mid + 1;
+      if (__ldg(&s.hb_cum[pr.x + mid]) <= w.z) lo = mid + 1;
       else hi = mid;
     }
-    int k = lo;
-    uint16_t ab = __ldg(&s.hb_ab[start + k]);
-    int a = ab & 0xff, b = ab >> 8;
+    const ulonglong2 ent = __ldg(&s.hb_ent[pr.x + lo]);
+    const int meta = (int)ent.y;
+    const int a = meta & 0xff, b = (meta >> 8) & 0xff;
     if (key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
-    e.ct = __ldg(&s.hb_c[start + k]);
-    e.hij = h_double<W, SYS>(s, d, p, q, a, b);
-    e.child = d;
-    key_flip<W>(e.child, p);
-    key_flip<W>(e.child, q);
-    key_flip<W>(e.child, a);
-    key_flip<W>(e.child, b);
+    // Slater-Condon sign of p -> a, then q -> b on the updated string
+    Key<W> tmp = d;
+    const int n1 = key_between<W>(tmp, p, a);
+    key_flip<W>(tmp, p);
+    key_flip<W>(tmp, a);
+    const int n2 = key_between<W>(tmp, q, b);
+    key_flip<W>(tmp, q);
+    key_flip<W>(tmp, b);
+    e.child = tmp;
+    e.famt = ent.x;
+    e.hneg = (((meta >> 16) ^ n1 ^ n2) & 1) != 0;
     e.ok = true;
     return e;
   }
