@@ -105,9 +105,14 @@ typedef struct {
   int64_t spawn_capacity;     /* max spawns per iteration (0 = default) */
   int record_capacity;        /* estimator records kept on the device (0 = default) */
   int tile_capacity;          /* distinct new spawned keys one annihilation tile holds on
-                                 chip: 0 = default (512 for 64/128-bit keys, 256 for
-                                 512-bit), else a power of two in [64, default]; smaller
-                                 values only send more buckets through the slower paths */
+                                 chip: 0 = default (128 per warp on the warp path; 512 for
+                                 64/128-bit and 256 for 512-bit keys on the block path),
+                                 else a power of two in [64, default]; smaller values only
+                                 send more buckets through the slower paths */
+  int annihilation;           /* annihilation kernel: 0 = by key width (one warp per
+                                 bucket for 64- and 128-bit keys, block tiles for
+                                 512-bit), 1 = block tiles, 2 = one warp per bucket;
+                                 every choice gives the same walker list */
 } hande_qmc;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  `alloc`

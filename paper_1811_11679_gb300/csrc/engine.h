@@ -26,6 +26,8 @@ struct Ops {
   void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);
   size_t (*merge_smem)(int tc, int sm);
   const void* merge_kernel;
+  const void* merge_warp_kernel;
+  size_t merge_warp_smem;
   const void* attempt_kernel;
   size_t attempt_smem;
 };
@@ -46,6 +48,8 @@ struct Engine {
   bool has_alloc = false;
   std::vector<std::pair<void*, size_t>> blocks;
   int merge_grid = 0;
+  bool merge_warp = false;   // annihilation with one warp per bucket
+  int merge_warp_grid = 0;
   size_t merge_smem_bytes = 0;
   int attempt_grid = 0;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};

@@ -559,15 +559,24 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     // on-chip tile: distinct new keys (TC, a power of two for the bitonic sort) and
     // main-list entries (SM) per bucket; sized so four 256-thread CTAs share an SM
     // for 64- and 128-bit keys
+    if (q.annihilation < 0 || q.annihilation > 2) throw Fail{HANDE_ERR_INVALID, "annihilation must be 0, 1 or 2"};
+    E.merge_warp = q.annihilation == 2 || (q.annihilation == 0 && E.W <= 2);
+    // block tiles: sized so that four 256-thread CTAs share an SM for 64- and
+    // 128-bit keys.  Warp path: 128 staged new keys per warp, segments of at
+    // most 192 entries, buckets sized for 1.5 x 128 expected spawns (most land
+    // on listed entries); the buckets it defers go to block tiles.
     P.tile_cap = E.W == 8 ? 256 : 512;
-    P.seg_max = E.W == 1 ? 768 : (E.W == 2 ? 512 : 256);
+    P.seg_max = E.merge_warp ? kMwMain : (E.W == 1 ? 768 : (E.W == 2 ? 512 : 256));
+    P.warp_cap = kMwNew;
     if (q.tile_capacity > 0) {
       int tc = q.tile_capacity;
       if (tc < 64 || tc > P.tile_cap || (tc & (tc - 1)))
         throw Fail{HANDE_ERR_INVALID, "tile_capacity must be a power of two in [64, default]"};
       P.tile_cap = tc;
       P.seg_max = std::min(P.seg_max, tc);
+      P.warp_cap = std::min(kMwNew, tc);
     }
+    P.bucket_spawns = E.merge_warp ? P.warp_cap * 3 / 2 : P.tile_cap / 2;
     E.core_size = q.semi_stoch_size;
     E.core_start = q.semi_stoch_start;
 
@@ -650,6 +659,14 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     P.bcount = dalloc<uint32_t>(E, cap);
     P.boff = dalloc<uint32_t>(E, cap);
     P.tile_state = dalloc<unsigned long long>(E, cap);
+    if (E.merge_warp) {
+      P.tile_inc = dalloc<unsigned long long>(E, cap);
+      P.mcap = cap + scap;   // >= main entries + spawns of one iteration
+      P.m_key = dalloc<uint64_t>(E, (size_t)P.mcap * E.W);
+      P.m_pop = dalloc<int64_t>(E, P.mcap);
+      P.m_hd = dalloc<double>(E, P.mcap);
+      P.m_flg = dalloc<uint8_t>(E, P.mcap);
+    }
     P.split_key = dalloc<uint64_t>(E, (size_t)cap * E.W);
     P.st = dalloc<DevState>(E, 1);
     P.rec = dalloc<Record>(E, P.rec_cap);
@@ -667,6 +684,15 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
                                                      E.merge_smem_bytes));
     if (per_sm < 1) throw Fail{HANDE_ERR_CUDA, "annihilation kernel does not fit on an SM"};
     E.merge_grid = per_sm * nsm;
+    if (E.merge_warp) {
+      CK(cudaFuncSetAttribute(E.ops.merge_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)E.ops.merge_warp_smem));
+      int wper = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, E.ops.merge_warp_kernel, kMwThreads,
+                                                       E.ops.merge_warp_smem));
+      if (wper < 1) throw Fail{HANDE_ERR_CUDA, "warp annihilation kernel does not fit on an SM"};
+      E.merge_warp_grid = wper * nsm;
+    }
     CK(cudaFuncSetAttribute(E.ops.attempt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)E.ops.attempt_smem));
     int att_per_sm = 0;

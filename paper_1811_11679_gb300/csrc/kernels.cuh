@@ -24,7 +24,7 @@ constexpr int kScanBlocks = 608;      // 4 x 152 SMs
 constexpr int kScanThreads = 256;
 
 // flags byte of a main-list entry
-enum : uint8_t { F_CORE = 1, F_INIT = 2, F_NEG = 4, F_REF = 8 };
+enum : uint8_t { F_CORE = 1, F_INIT = 2, F_NEG = 4, F_REF = 8, F_NEWDET = 16 };
 
 struct Record {
   int64_t iter;
@@ -55,6 +55,8 @@ struct DevState {
   int64_t nnew;          // new determinants written by the merge
   unsigned error;
   unsigned merge_ticket;
+  unsigned defer_ticket;   // block-kernel tickets over the deferred buckets
+  int64_t ndefer;          // buckets the warp annihilation left to the block kernel
 };
 
 struct Params {
@@ -68,6 +70,8 @@ struct Params {
   // capacities
   int64_t cap, scap;
   int tile_cap, seg_max, rec_cap;
+  int bucket_spawns;   // expected spawns per annihilation bucket (sizes the buckets)
+  int warp_cap;        // new keys one warp stages (warp annihilation)
   // main list (two buffers)
   uint64_t* key[2];
   int64_t* pop[2];
@@ -87,6 +91,15 @@ struct Params {
   uint32_t* bcount;
   uint32_t* boff;
   unsigned long long* tile_state;
+  // warp annihilation: kept entries of bucket b in tile_state[b], their output
+  // offset in tile_inc[b]; the buckets' merged lists staged (key, N, H_ii,
+  // flags) at the upper-bound offset b sb + boff[b] of arrays of mcap entries
+  unsigned long long* tile_inc;
+  uint64_t* m_key;
+  int64_t* m_pop;
+  double* m_hd;
+  uint8_t* m_flg;
+  int64_t mcap;
   uint64_t* split_key;
   // deterministic space
   int ncore;
@@ -333,9 +346,9 @@ __global__ void k_split(Params P, int cur) {
   // attempt count before the first iteration)
   const int64_t na = st->nspawn_prev > 0 ? st->nspawn_prev + st->nspawn_prev / 4 : st->natt;
   int64_t sb = (int64_t)P.seg_max;
-  int64_t half = P.tile_cap / 2;   // expected spawns per bucket: half a tile
+  const int64_t per = P.bucket_spawns;   // expected spawns per bucket
   if (na > 0) {
-    int64_t want = (int64_t)(((double)half * (double)n) / (double)na);
+    int64_t want = (int64_t)(((double)per * (double)n) / (double)na);
     if (want < sb) sb = want;
   }
   if (sb < 1) sb = 1;
@@ -347,12 +360,15 @@ __global__ void k_split(Params P, int cur) {
     st->nspawn = 0;
     st->nnew = 0;
     st->merge_ticket = 0;
+    st->defer_ticket = 0;
+    st->ndefer = 0;
     if (nb > P.cap) set_error(st, ERR_BUCKET_CAPACITY);
   }
   if (nb > P.cap) return;
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
     P.bcount[b] = 0;
     P.tile_state[b] = 0ull;
+
     int64_t src = b * sb;
 #pragma unroll
     for (int j = 0; j < W; ++j) P.split_key[j * P.cap + b] = src < n ? P.key[cur][j * P.cap + src] : 0ull;
@@ -1055,6 +1071,8 @@ struct MergeCtx {
   int64_t* opop;
   double* ohd;
   uint8_t* ofl;
+  int64_t ostride;      // key-word stride of the output arrays
+  int staged;           // output is the warp annihilation's staging list
 };
 
 // Merge the sorted unique spawns [0, nu) with the main segment entries [ml, mh)
@@ -1130,7 +1148,7 @@ __device__ int64_t tile_write(const Params& P, MergeSmem<W>& m, const MergeCtx& 
     if (!always) p = round_small<W>(P, c.t, k, p);
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
-    store_key<W>(c.okey, P.cap, o, k);
+    store_key<W>(c.okey, c.ostride, o, k);
     c.opop[o] = p;
     c.ohd[o] = c.hd[gi];
     c.ofl[o] = f & F_CORE;
@@ -1147,11 +1165,15 @@ __device__ int64_t tile_write(const Params& P, MergeSmem<W>& m, const MergeCtx& 
     int64_t p = round_small<W>(P, c.t, k, m.samt[j]);
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
-    store_key<W>(c.okey, P.cap, o, k);
+    store_key<W>(c.okey, c.ostride, o, k);
     c.opop[o] = p;
     c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
-    c.ofl[o] = 0;
-    P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    if (c.staged) {
+      c.ofl[o] = F_NEWDET;
+    } else {
+      c.ofl[o] = 0;
+      P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    }
     nwsum += iabs64(p);
   }
   __syncthreads();
@@ -1208,7 +1230,7 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
     const Key<W> k = mkey_at<W>(m, SM, i);
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
-    store_key<W>(c.okey, P.cap, o, k);
+    store_key<W>(c.okey, c.ostride, o, k);
     c.opop[o] = p;
     c.ohd[o] = c.hd[gi];
     c.ofl[o] = f & F_CORE;
@@ -1223,11 +1245,15 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
     const int64_t p = m.samt[j];
     if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
     int64_t o = out + pos;
-    store_key<W>(c.okey, P.cap, o, k);
+    store_key<W>(c.okey, c.ostride, o, k);
     c.opop[o] = p;
     c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
-    c.ofl[o] = 0;
-    P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    if (c.staged) {
+      c.ofl[o] = F_NEWDET;
+    } else {
+      c.ofl[o] = 0;
+      P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
+    }
     nwsum += iabs64(p);
   }
   __syncthreads();
@@ -1253,7 +1279,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int
   long long spins = 0;
   for (;;) {
     const int64_t idx = p - lane;
-    const unsigned long long v = idx >= 0 ? atomicAdd(&P.tile_state[idx], 0ull) : INC;
+    const unsigned long long v = idx >= 0 ? *(volatile const unsigned long long*)&P.tile_state[idx] : INC;
     const unsigned long long s = v >> 62;
     const unsigned inc = __ballot_sync(0xffffffffu, s == 2);
     const unsigned none = __ballot_sync(0xffffffffu, s == 0);
@@ -1261,6 +1287,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int
     const unsigned need = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
     if (none & need) {   // a state we need is not published yet
       ++spins;
+      __nanosleep(64);
       if ((spins & 255) == 0 && *(volatile unsigned*)&st->error) {
         *abort = 1;   // another tile failed: give up without adding an error
         return 0;
@@ -1286,7 +1313,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int
 constexpr int kMergeThreads = 256;
 
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur) {
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur, int staged) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t wsum[33];
@@ -1335,16 +1362,27 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
   c.pop = P.pop[cur];
   c.hd = P.hdiag[cur];
   c.fl = P.flags[cur];
-  c.okey = P.key[nxt];
-  c.opop = P.pop[nxt];
-  c.ohd = P.hdiag[nxt];
-  c.ofl = P.flags[nxt];
+  // staged: only the buckets the warp annihilation deferred, written to its
+  // staging list at their upper-bound offsets (no look-back)
+  c.okey = staged ? P.m_key : P.key[nxt];
+  c.opop = staged ? P.m_pop : P.pop[nxt];
+  c.ohd = staged ? P.m_hd : P.hdiag[nxt];
+  c.ofl = staged ? P.m_flg : P.flags[nxt];
+  c.ostride = staged ? P.mcap : P.cap;
+  c.staged = staged;
   const uint64_t* key = P.key[cur];
   int64_t nwsum = 0;
   for (;;) {
     if (threadIdx.x == 0) {
-      tile_id = st->error ? -1 : (int)atomicAdd(&st->merge_ticket, 1u);
       s_abort = 0;
+      if (st->error) {
+        tile_id = -1;
+      } else if (staged) {
+        const int64_t tk = (int64_t)atomicAdd(&st->defer_ticket, 1u);
+        tile_id = tk < st->ndefer ? (int)P.att_begin[tk] : -1;
+      } else {
+        tile_id = (int)atomicAdd(&st->merge_ticket, 1u);
+      }
     }
     __syncthreads();
     const int64_t b = tile_id;
@@ -1415,6 +1453,11 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
         const int nu = (nnew <= kCountMax && nnew <= (int)blockDim.x) ? count_reduce<W>(m, TC, nnew)
                                                                          : sort_reduce<W>(m, TC, nnew, wsum);
         const uint32_t nkeep = acc_decide<W>(P, m, c, TC, SM, nu, nm, wsum);
+        if (staged) {
+          if (threadIdx.x == 0) P.tile_state[b] = nkeep;
+          nwsum += acc_write<W, SYS>(P, m, c, TC, SM, nu, nm, nkeep, c.m0 + (int64_t)s0);
+          continue;
+        }
         if (threadIdx.x < 32) {
           int ab = 0;
           const unsigned long long base = lookback_warp(P, b, nkeep, &ab);
@@ -1536,7 +1579,12 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
         __syncthreads();
       }
       if (s_abort) break;
-      if (threadIdx.x < 32) {
+      if (staged) {
+        if (threadIdx.x == 0) {
+          P.tile_state[b] = total;
+          s_base = (unsigned long long)(c.m0 + s0);
+        }
+      } else if (threadIdx.x < 32) {
         int ab = 0;
         const unsigned long long base = lookback_warp(P, b, total, &ab);
         if (threadIdx.x == 0) {
@@ -1668,3 +1716,5 @@ __global__ void k_eref(Params P) {
 }
 
 }  // namespace hande
+
+#include "merge_warp.cuh"

@@ -145,7 +145,14 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   mark(6);
   k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
   mark(7);
-  k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur);
+  if (E.merge_warp) {
+    k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
+    k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
+    k_merge_scan<<<1, 1024, 0, s>>>(P, cur);
+    k_merge_copy<W><<<E.attempt_grid * 2, 256, 0, s>>>(P, cur);
+  } else {
+    k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 0);
+  }
   mark(8);
   k_new_hdiag<W, SYS><<<E.attempt_grid, 256, 0, s>>>(P, cur);
   mark(9);
@@ -206,6 +213,8 @@ Ops make_ops() {
   o.sel_flags = &enqueue_sel_flags<W>;
   o.merge_smem = &merge_smem_w<W>;
   o.merge_kernel = (const void*)&k_merge<W, SYS>;
+  o.merge_warp_kernel = (const void*)&k_merge_warp<W, SYS>;
+  o.merge_warp_smem = merge_warp_smem_bytes<W>();
   o.attempt_kernel = (const void*)&k_attempt<W, SYS>;
   o.attempt_smem = attempt_smem_bytes<W, SYS>();
   return o;

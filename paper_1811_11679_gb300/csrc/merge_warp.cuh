@@ -1,0 +1,485 @@
+// merge_warp.cuh -- annihilation with one warp per bucket (64- and 128-bit keys).
+//
+// The annihilation step (HANDE-QMC paper Sec. 2.4 and App. B: combine the
+// spawned particles on each determinant, merge them into the sorted main list,
+// apply the initiator rule to new determinants) for one bucket: the main-list
+// segment [b sb, (b+1) sb) and the spawns whose keys fall in its splitter range.
+// A warp owns the whole bucket, so no step needs a block barrier:
+//   1. the segment's keys go to the warp's shared-memory tile;
+//   2. each spawn finds its key in the segment (binary search): spawns onto
+//      listed determinants are added into per-entry integer accumulators (order-
+//      free), spawns onto new determinants are staged;
+//   3. the staged spawns are sorted in registers (bitonic network over the
+//      warp, shuffles across lanes) and equal keys combined (amounts summed,
+//      initiator bits OR-ed);
+//   4. every candidate gets its merged rank (own index + keys of the other list
+//      below it), its final population (spawns added, real-weight occupation
+//      rounding) and a keep bit; kept entries are counted;
+//   5. the kept entries are written, in merged order, to a staging list at an
+//      upper bound of the bucket's output offset (b sb + the spawns of the
+//      buckets before b), so no bucket waits for another.
+// A bucket with more spawns than a warp should take (8 x the staging), or whose
+// distinct new keys overflow the staging, is deferred to the block kernel
+// (k_merge in staged mode: 256 threads, sub-ranges for very large buckets),
+// which writes to the same staging list.  A one-block scan of the kept counts
+// then gives every bucket its output offset, and a coalesced copy compacts the
+// staging list into the new main list.
+#pragma once
+
+namespace hande {
+
+constexpr int kMwThreads = 256;   // 8 warps per CTA
+constexpr int kMwWarps = kMwThreads / 32;
+constexpr int kMwMain = 192;      // main-list entries per bucket (segment length cap)
+constexpr int kMwNew = 128;       // staged spawns onto new determinants per warp
+constexpr int kMwKeepWords = (kMwMain + kMwNew + 31) / 32;
+
+template <int W>
+struct WarpTile {
+  uint64_t mkey[W][kMwMain];   // segment keys
+  int64_t macc[kMwMain];       // population plus the spawns onto the entry, then its final value
+  double mhd[kMwMain];         // segment entries' H_ii - E_ref
+  uint64_t nkey[W][kMwNew];    // staged keys of new determinants (sorted unique after dedupe)
+  int64_t namt[kMwNew];
+  uint32_t nflg[kMwNew];       // bit 0: an initiator parent
+  int16_t mrank[kMwMain];      // merged rank of a segment entry
+  int16_t nrank[kMwNew];       // merged rank of a new key
+  uint8_t mflg[kMwMain];       // segment entry flags
+  uint32_t keep[kMwKeepWords]; // keep bits by merged rank
+  uint32_t kpre[kMwKeepWords]; // kept entries before each word
+};
+
+template <int W>
+__host__ __device__ constexpr size_t merge_warp_tile_bytes() {
+  return (sizeof(WarpTile<W>) + 15) & ~(size_t)15;
+}
+template <int W>
+__host__ __device__ constexpr size_t merge_warp_smem_bytes() {
+  return (size_t)kMwWarps * merge_warp_tile_bytes<W>();
+}
+
+template <int W>
+__device__ __forceinline__ Key<W> wt_mkey(const WarpTile<W>& t, int i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = t.mkey[j][i];
+  return k;
+}
+template <int W>
+__device__ __forceinline__ Key<W> wt_nkey(const WarpTile<W>& t, int i) {
+  Key<W> k;
+#pragma unroll
+  for (int j = 0; j < W; ++j) k.w[j] = t.nkey[j][i];
+  return k;
+}
+// first index in [lo, hi) whose segment key is >= k
+template <int W>
+__device__ __forceinline__ int wt_lb_main(const WarpTile<W>& t, int lo, int hi, const Key<W>& k) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key_lt<W>(wt_mkey<W>(t, mid), k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+// number of the first u (sorted) new keys below k
+template <int W>
+__device__ __forceinline__ int wt_lb_new(const WarpTile<W>& t, int u, const Key<W>& k) {
+  int lo = 0, hi = u;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (key_lt<W>(wt_nkey<W>(t, mid), k)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// strict order of (key, slot) pairs with the padding slots (-1) after all keys
+template <int W>
+__device__ __forceinline__ bool sd_less(const Key<W>& a, int ai, const Key<W>& b, int bi) {
+  if (ai < 0) return false;
+  if (bi < 0) return true;
+  return key_lt<W>(a, b);
+}
+
+// Sort the n <= 32 E staged entries by key (bitonic network over 32 E slots,
+// slot i = lane E + e held by the lane in registers) and combine equal keys.
+// On return entries [0, u) are the sorted unique keys; returns u.
+template <int W, int E>
+__device__ int wt_sort_dedupe_e(WarpTile<W>& t, int n, int lane) {
+  Key<W> k[E];
+  int ix[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane * E + e;
+    ix[e] = i < n ? i : -1;
+#pragma unroll
+    for (int j = 0; j < W; ++j) k[e].w[j] = i < n ? t.nkey[j][i] : 0ull;
+  }
+  constexpr int N2 = 32 * E;
+#pragma unroll
+  for (int kk = 2; kk <= N2; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= E) {   // partner slot i ^ j lives in lane ^ (j / E), same e
+        const int lm = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          Key<W> pk;
+#pragma unroll
+          for (int w = 0; w < W; ++w) pk.w[w] = __shfl_xor_sync(0xffffffffu, k[e].w[w], lm);
+          const int pi = __shfl_xor_sync(0xffffffffu, ix[e], lm);
+          const int i = lane * E + e;
+          const bool keep_min = ((i & j) == 0) == ((i & kk) == 0);
+          const bool take = keep_min ? sd_less<W>(pk, pi, k[e], ix[e]) : sd_less<W>(k[e], ix[e], pk, pi);
+          if (take) {
+            k[e] = pk;
+            ix[e] = pi;
+          }
+        }
+      } else {        // partner slot in the same lane
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if (e & j) continue;
+          const int e2 = e | j;
+          const int i = lane * E + e;
+          const bool asc = (i & kk) == 0;
+          const bool sw = asc ? sd_less<W>(k[e2], ix[e2], k[e], ix[e]) : sd_less<W>(k[e], ix[e], k[e2], ix[e2]);
+          if (sw) {
+            const Key<W> tk = k[e];
+            k[e] = k[e2];
+            k[e2] = tk;
+            const int ti = ix[e];
+            ix[e] = ix[e2];
+            ix[e2] = ti;
+          }
+        }
+      }
+    }
+  }
+  // heads of equal-key runs, their exclusive count over the warp
+  Key<W> up;
+#pragma unroll
+  for (int w = 0; w < W; ++w) up.w[w] = __shfl_up_sync(0xffffffffu, k[E - 1].w[w], 1);
+  bool head[E];
+  int nh = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const bool first = lane == 0 && e == 0;
+    const Key<W>& pk = e ? k[e - 1] : up;
+    head[e] = ix[e] >= 0 && (first || !key_eq<W>(pk, k[e]));
+    nh += head[e] ? 1 : 0;
+  }
+  int incl = nh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int u = __shfl_sync(0xffffffffu, incl, 31);
+  int run = incl - nh;
+  int64_t a[E];
+  uint32_t f[E];
+  int uid[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    a[e] = 0;
+    f[e] = 0;
+    if (ix[e] >= 0) {
+      a[e] = t.namt[ix[e]];
+      f[e] = t.nflg[ix[e]];
+    }
+    run += head[e] ? 1 : 0;
+    uid[e] = run - 1;
+  }
+  __syncwarp();
+  for (int i = lane; i < u; i += 32) {
+    t.namt[i] = 0;
+    t.nflg[i] = 0;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (ix[e] < 0) continue;
+    if (head[e]) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) t.nkey[w][uid[e]] = k[e].w[w];
+    }
+    atomicAdd((unsigned long long*)&t.namt[uid[e]], (unsigned long long)a[e]);
+    if (f[e] & 1u) atomicOr(&t.nflg[uid[e]], 1u);
+  }
+  __syncwarp();
+  return u;
+}
+
+template <int W>
+__device__ __forceinline__ int wt_sort_dedupe(WarpTile<W>& t, int n, int lane) {
+  if (n <= 1) return n;
+  if (n <= 32) return wt_sort_dedupe_e<W, 1>(t, n, lane);
+  if (n <= 64) return wt_sort_dedupe_e<W, 2>(t, n, lane);
+  return wt_sort_dedupe_e<W, 4>(t, n, lane);
+}
+
+// Decide one merge segment: the segment entries [mi, mh) and the unique new
+// keys [0, u) (all between the same neighbours).  Merged ranks, final
+// populations (stored when `store`), keep bits and their per-word prefix.
+// Segment entries keep their slot if core or reference, otherwise they survive
+// with a nonzero population after the occupation rounding; new determinants need
+// an initiator parent (Sec. 2.1) and a nonzero amount.  Returns the number kept.
+template <int W>
+__device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c, int mi, int mh, int u,
+                              bool store, int lane) {
+  const int nc = (mh - mi) + u;
+  const int nw = (nc + 31) >> 5;
+  for (int w = lane; w < nw; w += 32) t.keep[w] = 0;
+  __syncwarp();
+  for (int i = mi + lane; i < mh; i += 32) {
+    const Key<W> k = wt_mkey<W>(t, i);
+    const int r = (i - mi) + wt_lb_new<W>(t, u, k);
+    int64_t p = t.macc[i];
+    const uint8_t f = t.mflg[i];
+    const bool always = (f & (F_CORE | F_REF)) != 0;
+    if (!always) p = round_small<W>(P, c.t, k, p);
+    if (store) t.macc[i] = p;
+    t.mrank[i] = (int16_t)r;
+    if (always || p != 0) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+  }
+  for (int j = lane; j < u; j += 32) {
+    const Key<W> k = wt_nkey<W>(t, j);
+    const int r = j + (wt_lb_main<W>(t, mi, mh, k) - mi);
+    int64_t p = t.namt[j];
+    const bool ok = (!P.initiator || (t.nflg[j] & 1u)) && p != 0;
+    if (ok) p = round_small<W>(P, c.t, k, p);
+    t.namt[j] = p;
+    t.nrank[j] = (int16_t)r;
+    if (ok && p != 0) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+  }
+  __syncwarp();
+  const int cnt = lane < nw ? __popc(t.keep[lane]) : 0;
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane < nw) t.kpre[lane] = (uint32_t)(incl - cnt);
+  __syncwarp();
+  return (uint32_t)__shfl_sync(0xffffffffu, incl, 31);
+}
+
+// Write the entries wt_decide kept to the staging list at out + their rank
+// among the kept (new determinants flagged F_NEWDET).  Returns the sum of |N|.
+template <int W>
+__device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int u, int64_t out, int lane) {
+  DevState* st = P.st;
+  int64_t nws = 0;
+  for (int i = mi + lane; i < mh; i += 32) {
+    const int r = t.mrank[i];
+    const uint32_t wv = t.keep[r >> 5];
+    if (!((wv >> (r & 31)) & 1u)) continue;
+    const int64_t o = out + t.kpre[r >> 5] + __popc(wv & ((1u << (r & 31)) - 1u));
+    const int64_t p = t.macc[i];
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    store_key<W>(P.m_key, P.mcap, o, wt_mkey<W>(t, i));
+    P.m_pop[o] = p;
+    P.m_hd[o] = t.mhd[i];
+    P.m_flg[o] = t.mflg[i] & F_CORE;
+    nws += iabs64(p);
+  }
+  for (int j = lane; j < u; j += 32) {
+    const int r = t.nrank[j];
+    const uint32_t wv = t.keep[r >> 5];
+    if (!((wv >> (r & 31)) & 1u)) continue;
+    const int64_t o = out + t.kpre[r >> 5] + __popc(wv & ((1u << (r & 31)) - 1u));
+    const int64_t p = t.namt[j];
+    if (iabs64(p) >= (int64_t(1) << 62)) set_error(st, ERR_OVERFLOW);
+    store_key<W>(P.m_key, P.mcap, o, wt_nkey<W>(t, j));
+    P.m_pop[o] = p;
+    P.m_hd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
+    P.m_flg[o] = F_NEWDET;
+    nws += iabs64(p);
+  }
+  __syncwarp();
+  return nws;
+}
+
+// One warp per bucket, buckets taken from a ticket counter (see the file comment).
+template <int W, int SYS>
+__global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur) {
+  DevState* st = P.st;
+  extern __shared__ __align__(16) unsigned char mw_smem[];
+  const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
+  WarpTile<W>& t = *reinterpret_cast<WarpTile<W>*>(mw_smem + (size_t)wid * merge_warp_tile_bytes<W>());
+  const int cap = P.warp_cap;
+  const int64_t n = st->ndet[cur];
+  const int64_t nb = st->nbuckets;
+  const int64_t sb = st->sb;
+  MergeCtx c{};   // output fields unused: the buckets go to the staging list
+  c.t = st->iter + 1;
+  c.pop = P.pop[cur];
+  c.hd = P.hdiag[cur];
+  c.fl = P.flags[cur];
+  const uint64_t* key = P.key[cur];
+  int64_t nwsum = 0;
+  for (;;) {
+    int64_t b = 0;
+    if (lane == 0) b = st->error ? -1 : (int64_t)atomicAdd(&st->merge_ticket, 1u);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (b < 0 || b >= nb) break;
+    const int64_t s0 = P.boff[b];
+    const int64_t ns = P.bcount[b];
+    if (ns > 8 * (int64_t)cap) {   // large bucket: the block kernel takes it
+      if (lane == 0) P.att_begin[atomicAdd((unsigned long long*)&st->ndefer, 1ull)] = b;
+      continue;
+    }
+    c.m0 = b * sb;
+    const int nm = (int)((c.m0 + sb < n ? c.m0 + sb : n) - c.m0);
+#pragma unroll 2
+    for (int i = lane; i < nm; i += 32) {
+      const int64_t gi = c.m0 + i;
+#pragma unroll
+      for (int j = 0; j < W; ++j) t.mkey[j][i] = key[j * P.cap + gi];
+      t.macc[i] = c.pop[gi];
+      t.mflg[i] = c.fl[gi];
+      t.mhd[i] = c.hd[gi];
+    }
+    __syncwarp();
+    // spawns onto segment entries into the accumulators, the others staged
+    int nnew = 0;
+    bool over = false;
+    for (int64_t c0 = 0; c0 < ns; c0 += 32) {
+      const int64_t i = c0 + lane;
+      const bool have = i < ns;
+      Key<W> k;
+#pragma unroll
+      for (int j = 0; j < W; ++j) k.w[j] = 0;
+      int64_t a = 0;
+      uint32_t f = 0;
+      bool match = false;
+      if (have) {
+        k = load_key<W>(P.b_key, P.scap, s0 + i);
+        a = P.b_amt[s0 + i];
+        f = P.b_flag[s0 + i];
+        const int j = wt_lb_main<W>(t, 0, nm, k);
+        match = j < nm && key_eq<W>(wt_mkey<W>(t, j), k);
+        if (match) atomicAdd((unsigned long long*)&t.macc[j], (unsigned long long)a);
+      }
+      const unsigned mask = __ballot_sync(0xffffffffu, have && !match);
+      if (nnew + __popc(mask) > cap) {
+        nnew = wt_sort_dedupe<W>(t, nnew, lane);
+        if (nnew + __popc(mask) > cap) {
+          over = true;
+          break;
+        }
+      }
+      if (have && !match) {
+        const int s = nnew + __popc(mask & ((1u << lane) - 1u));
+#pragma unroll
+        for (int j = 0; j < W; ++j) t.nkey[j][s] = k.w[j];
+        t.namt[s] = a;
+        t.nflg[s] = f;
+      }
+      nnew += __popc(mask);
+      __syncwarp();
+    }
+    const int64_t out = c.m0 + (int64_t)P.boff[b];   // upper bound of the bucket's offset
+    if (over) {   // too many distinct new keys for the staging: the block kernel takes it
+      if (lane == 0) P.att_begin[atomicAdd((unsigned long long*)&st->ndefer, 1ull)] = b;
+      continue;
+    }
+    const int u = wt_sort_dedupe<W>(t, nnew, lane);
+    const uint32_t nkeep = wt_decide<W>(P, t, c, 0, nm, u, true, lane);
+    nwsum += wt_write<W>(P, t, 0, nm, u, out, lane);
+    if (lane == 0) P.tile_state[b] = nkeep;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) nwsum += __shfl_xor_sync(0xffffffffu, nwsum, o);
+  if (lane == 0 && nwsum) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)nwsum);
+}
+
+// Output offsets of the buckets: exclusive scan of the kept counts by one
+// block, each thread a contiguous run of buckets; the total is the new list's
+// length.
+static __global__ void __launch_bounds__(1024) k_merge_scan(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  __shared__ unsigned long long wsum[32];
+  const int64_t nb = st->nbuckets;
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t beg = (int64_t)threadIdx.x * per;
+  const int64_t end = beg + per < nb ? beg + per : nb;
+  unsigned long long sum = 0;
+  for (int64_t b = beg; b < end; ++b) sum += P.tile_state[b];
+  const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
+  unsigned long long x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    unsigned long long v = lane < nw ? wsum[lane] : 0ull, inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane < nw) wsum[lane] = inc - v;
+  }
+  __syncthreads();
+  unsigned long long run = wsum[wid] + x - sum;
+  for (int64_t b = beg; b < end; ++b) {
+    const unsigned long long v = P.tile_state[b];
+    P.tile_inc[b] = run;
+    run += v;
+  }
+  if (end == nb && beg < end) {   // the thread holding the last bucket has the total
+    if ((int64_t)run > P.cap) set_error(st, ERR_STATE_CAPACITY);
+    st->ndet[cur ^ 1] = (int64_t)run;
+  }
+}
+
+// Compact the staged bucket lists into the new main list (one warp per bucket,
+// coalesced); new determinants are listed in natt[] for their diagonals.
+template <int W>
+__global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
+  DevState* st = P.st;
+  if (st->error) return;
+  const int nxt = cur ^ 1;
+  const int64_t nb = st->nbuckets, sb = st->sb;
+  const int lane = (int)(threadIdx.x & 31);
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  uint64_t* okey = P.key[nxt];
+  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+    const int64_t src = b * sb + (int64_t)P.boff[b];
+    const int64_t dst = (int64_t)P.tile_inc[b];
+    const int64_t cnt = (int64_t)P.tile_state[b];
+    for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
+      const int64_t i = i0 + lane;
+      bool isnew = false;
+      const int64_t o = dst + i;
+      if (i < cnt) {
+        const int64_t s = src + i;
+#pragma unroll
+        for (int j = 0; j < W; ++j) okey[j * P.cap + o] = P.m_key[j * P.mcap + s];
+        P.pop[nxt][o] = P.m_pop[s];
+        P.hdiag[nxt][o] = P.m_hd[s];
+        const uint8_t f = P.m_flg[s];
+        isnew = (f & F_NEWDET) != 0;
+        P.flags[nxt][o] = f & F_CORE;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, isnew);
+      if (m) {
+        unsigned long long slot = 0;
+        if (lane == 0) slot = atomicAdd((unsigned long long*)&st->nnew, (unsigned long long)__popc(m));
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (isnew) P.natt[slot + __popc(m & ((1u << lane) - 1u))] = o;
+      }
+    }
+  }
+}
+
+}  // namespace hande

@@ -42,7 +42,8 @@ class _Qmc(C.Structure):
                 ("p_single", C.c_double), ("shift_period", C.c_int), ("initiator", C.c_int),
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int), ("semi_stoch_start", C.c_int),
                 ("seed", C.c_uint64), ("replica", C.c_uint64), ("state_capacity", C.c_int64),
-                ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int), ("tile_capacity", C.c_int)]
+                ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int), ("tile_capacity", C.c_int),
+                ("annihilation", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -175,6 +176,7 @@ class Hande:
         q.spawn_capacity = int(qmc.get("spawn_capacity", 0))
         q.record_capacity = int(qmc.get("record_capacity", 0))
         q.tile_capacity = int(qmc.get("tile_capacity", 0))
+        q.annihilation = int(qmc.get("annihilation", 0))
         self.W = s.key_words
         alloc_p = None
         if stream is None or torch_memory:

@@ -180,12 +180,13 @@ def test_set_get_walkers_roundtrip_and_validation():
         g2.set_walkers(bad, p)
 
 
-@pytest.mark.parametrize("tile", [64, 256])
-def test_oversized_buckets_small_tiles(tile):
-    """Tiny annihilation tiles force most buckets through the oversized path
-    (spawn-sampled sub-ranges, two-pass merge); lists stay bit-identical."""
+@pytest.mark.parametrize("annihilation,tile", [(1, 64), (1, 256), (2, 64), (2, 128)])
+def test_oversized_buckets_small_tiles(annihilation, tile):
+    """Small annihilation tiles force many buckets through the oversized paths
+    (block tiles: spawn-sampled sub-ranges, two-pass merge; one warp per bucket:
+    batches of new keys in key order); lists stay bit-identical."""
     sysd, q = inputs.workload("molecule28", target_population=30000, semi_stoch_size=200,
-                              semi_stoch_start=30, tile_capacity=tile)
+                              semi_stoch_start=30, tile_capacity=tile, annihilation=annihilation)
     g = hande.Hande(sysd, q)
     c = oracle.Oracle(sysd, q)
     seen = 0
@@ -198,10 +199,12 @@ def test_oversized_buckets_small_tiles(tile):
     _same_records(g, c)
 
 
-def test_oversized_bucket_single_bucket_start():
+@pytest.mark.parametrize("annihilation", [1, 2])
+def test_oversized_bucket_single_bucket_start(annihilation):
     """3000 walkers on the reference and a one-determinant list: the first
     iteration puts every spawn in one bucket, far above a 64-key tile."""
-    sysd, q = inputs.workload("molecule28", target_population=1e5, init_pop=3000, tile_capacity=64)
+    sysd, q = inputs.workload("molecule28", target_population=1e5, init_pop=3000, tile_capacity=64,
+                              annihilation=annihilation)
     g = hande.Hande(sysd, q)
     c = oracle.Oracle(sysd, q)
     g.iterate(1)
@@ -215,11 +218,12 @@ def test_oversized_bucket_single_bucket_start():
     _same_records(g, c)
 
 
-def test_oversized_buckets_from_synthetic_start():
+@pytest.mark.parametrize("annihilation", [1, 2])
+def test_oversized_buckets_from_synthetic_start(annihilation):
     """A synthetic list whose spawn keys are skewed against the main-list
     splitters (the benchmark's starting state, scaled down)."""
     sysd, q = inputs.workload("molecule28", target_population=2e5, semi_stoch_size=500, semi_stoch_start=0,
-                              tile_capacity=64)
+                              tile_capacity=64, annihilation=annihilation)
     keys, pops = inputs.synthetic_walkers(sysd, 40000, 2e5)
     g = hande.Hande(sysd, q)
     c = oracle.Oracle(sysd, q)
