@@ -300,6 +300,75 @@ static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* t
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) part[i] = buf[i];
   if (threadIdx.x == 0) *total = tot;
 }
+// Exclusive scan of in[0, *n_ptr) into out by one block of 1024 threads, for
+// short arrays (bucket counts): chunks of 4096 loaded coalesced into shared
+// memory, 4 contiguous values per thread, block scan of the thread sums.  The
+// total goes to *total; above cap_check (if >= 0) it sets the state-capacity error.
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, const int64_t* n_ptr, int64_t* total,
+                                                    int64_t cap_check, DevState* st) {
+  if (st->error) return;
+  constexpr int kPer = 4, kChunk = 1024 * kPer;
+  __shared__ unsigned long long buf[kChunk];
+  __shared__ unsigned long long wsum[32];
+  const int64_t n = *n_ptr;
+  const int tid = (int)threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  unsigned long long carry = 0;
+  for (int64_t base = 0; base < n; base += kChunk) {
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int64_t i = base + k * 1024 + tid;
+      buf[k * 1024 + tid] = i < n ? (unsigned long long)in[i] : 0ull;
+    }
+    __syncthreads();
+    unsigned long long v[kPer], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      v[k] = buf[tid * kPer + k];
+      sum += v[k];
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      const unsigned long long w0 = wsum[lane];
+      unsigned long long inc = w0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      wsum[lane] = inc - w0;
+    }
+    __syncthreads();
+    unsigned long long run = carry + wsum[wid] + x - sum;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      buf[tid * kPer + k] = run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (wid == 31 && lane == 31) wsum[0] = run;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int64_t i = base + k * 1024 + tid;
+      if (i < n) out[i] = (Tout)buf[k * 1024 + tid];
+    }
+    __syncthreads();
+    carry = wsum[0];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *total = (int64_t)carry;
+    if (cap_check >= 0 && (int64_t)carry > cap_check) set_error(st, ERR_STATE_CAPACITY);
+  }
+}
+
 // out[i] = exclusive prefix of in over the block's chunk + part[block]
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,

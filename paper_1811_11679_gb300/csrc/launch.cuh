@@ -139,16 +139,16 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   k_attempt<W, SYS><<<E.attempt_grid, kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(P, cur);
   mark(5);
   int64_t* nbk = st_field_i64(st, offsetof(DevState, nbuckets));
-  k_scan_reduce<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, nbk, P.part, st);
-  k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, scan_total)), st);
-  k_scan_apply<uint32_t><<<kScanBlocks, kScanThreads, 0, s>>>(P.bcount, P.boff, nbk, P.part, st);
+  k_scan_one<uint32_t, uint32_t><<<1, 1024, 0, s>>>(P.bcount, P.boff, nbk,
+                                                    st_field_i64(st, offsetof(DevState, scan_total)), -1, st);
   mark(6);
   k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
   mark(7);
   if (E.merge_warp) {
     k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
     k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
-    k_merge_scan<<<1, 1024, 0, s>>>(P, cur);
+    k_scan_one<unsigned long long, unsigned long long><<<1, 1024, 0, s>>>(
+        P.tile_state, P.tile_inc, nbk, st_field_i64(st, offsetof(DevState, ndet) + 8 * (cur ^ 1)), P.cap, st);
     k_merge_copy<W><<<E.attempt_grid * 2, 256, 0, s>>>(P, cur);
   } else {
     k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 0);

@@ -22,8 +22,8 @@
 // distinct new keys overflow the staging, is deferred to the block kernel
 // (k_merge in staged mode: 256 threads, sub-ranges for very large buckets),
 // which writes to the same staging list.  A one-block scan of the kept counts
-// then gives every bucket its output offset, and a coalesced copy compacts the
-// staging list into the new main list.
+// (k_scan_one) then gives every bucket its output offset, and a coalesced copy
+// compacts the staging list into the new main list.
 #pragma once
 
 namespace hande {
@@ -397,51 +397,6 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
   if (lane == 0 && nwsum) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)nwsum);
 }
 
-// Output offsets of the buckets: exclusive scan of the kept counts by one
-// block, each thread a contiguous run of buckets; the total is the new list's
-// length.
-static __global__ void __launch_bounds__(1024) k_merge_scan(Params P, int cur) {
-  DevState* st = P.st;
-  if (st->error) return;
-  __shared__ unsigned long long wsum[32];
-  const int64_t nb = st->nbuckets;
-  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
-  const int64_t beg = (int64_t)threadIdx.x * per;
-  const int64_t end = beg + per < nb ? beg + per : nb;
-  unsigned long long sum = 0;
-  for (int64_t b = beg; b < end; ++b) sum += P.tile_state[b];
-  const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
-  unsigned long long x = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = (int)(blockDim.x >> 5);
-    unsigned long long v = lane < nw ? wsum[lane] : 0ull, inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane < nw) wsum[lane] = inc - v;
-  }
-  __syncthreads();
-  unsigned long long run = wsum[wid] + x - sum;
-  for (int64_t b = beg; b < end; ++b) {
-    const unsigned long long v = P.tile_state[b];
-    P.tile_inc[b] = run;
-    run += v;
-  }
-  if (end == nb && beg < end) {   // the thread holding the last bucket has the total
-    if ((int64_t)run > P.cap) set_error(st, ERR_STATE_CAPACITY);
-    st->ndet[cur ^ 1] = (int64_t)run;
-  }
-}
-
 // Compact the staged bucket lists into the new main list (one warp per bucket,
 // coalesced); new determinants are listed in natt[] for their diagonals.
 template <int W>
@@ -457,26 +412,41 @@ __global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
     const int64_t src = b * sb + (int64_t)P.boff[b];
     const int64_t dst = (int64_t)P.tile_inc[b];
     const int64_t cnt = (int64_t)P.tile_state[b];
-    for (int64_t i0 = 0; i0 < cnt; i0 += 32) {
-      const int64_t i = i0 + lane;
-      bool isnew = false;
-      const int64_t o = dst + i;
-      if (i < cnt) {
-        const int64_t s = src + i;
+    // four groups of 32 entries per step: all loads first, then the stores
+    for (int64_t i0 = 0; i0 < cnt; i0 += 128) {
+      Key<W> kk[4];
+      int64_t pp[4];
+      double hh[4];
+      uint8_t ff[4];
 #pragma unroll
-        for (int j = 0; j < W; ++j) okey[j * P.cap + o] = P.m_key[j * P.mcap + s];
-        P.pop[nxt][o] = P.m_pop[s];
-        P.hdiag[nxt][o] = P.m_hd[s];
-        const uint8_t f = P.m_flg[s];
-        isnew = (f & F_NEWDET) != 0;
-        P.flags[nxt][o] = f & F_CORE;
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * 32 + lane;
+        if (i < cnt) {
+          kk[u] = load_key<W>(P.m_key, P.mcap, src + i);
+          pp[u] = P.m_pop[src + i];
+          hh[u] = P.m_hd[src + i];
+          ff[u] = P.m_flg[src + i];
+        }
       }
-      const unsigned m = __ballot_sync(0xffffffffu, isnew);
-      if (m) {
-        unsigned long long slot = 0;
-        if (lane == 0) slot = atomicAdd((unsigned long long*)&st->nnew, (unsigned long long)__popc(m));
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (isnew) P.natt[slot + __popc(m & ((1u << lane) - 1u))] = o;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + u * 32 + lane;
+        const int64_t o = dst + i;
+        bool isnew = false;
+        if (i < cnt) {
+          store_key<W>(okey, P.cap, o, kk[u]);
+          P.pop[nxt][o] = pp[u];
+          P.hdiag[nxt][o] = hh[u];
+          P.flags[nxt][o] = ff[u] & F_CORE;
+          isnew = (ff[u] & F_NEWDET) != 0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, isnew);
+        if (m) {
+          unsigned long long slot = 0;
+          if (lane == 0) slot = atomicAdd((unsigned long long*)&st->nnew, (unsigned long long)__popc(m));
+          slot = __shfl_sync(0xffffffffu, slot, 0);
+          if (isnew) P.natt[slot + __popc(m & ((1u << lane) - 1u))] = o;
+        }
       }
     }
   }
