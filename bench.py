@@ -134,7 +134,33 @@ def _phase_bytes(rec, W):
         "scatter": ns * (K + 16) + ns * (K + 9),
         # main list read, populations/flags/attempt counts written
         "det_pass": nd_pre * (K + 17) + nd_pre * (8 + 1 + 8),
+        # annihilation as a whole: spawns sorted (read + write) and merged (read),
+        # main list read, new list written
+        "annihilation": 3 * ns * (K + 9) + nd_pre * (K + 17) + nd_post * (K + 17),
+        # whole iteration: the spawn and death phase (main list read, populations
+        # and flags written, spawns written) plus the annihilation
+        "iteration": nd_pre * (K + 17) + nd_pre * 9 + ns * (K + 9)
+                     + 3 * ns * (K + 9) + nd_pre * (K + 17) + nd_post * (K + 17),
     }
+
+
+# Spawning kernel (k_attempt) issue-slot roofline.  Warp instructions issued
+# per spawn attempt and DRAM bytes per attempt, from one ncu capture of the
+# kernel on the profile case (profiles/kernels_molecule28_profile_case.md);
+# the peak is 4 warp instructions per cycle per SM (one per sub-partition) on
+# 152 SMs at the maximum SM clock.
+ATTEMPT_INST_PER_ATTEMPT = 279725927 / 7571203
+ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.008128e6 + 6.956288e6) / 7571203
+N_SM = 152
+
+
+def _issue_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+    except (OSError, KeyError, ValueError):
+        mhz = 2070.0
+    return 4 * N_SM * mhz * 1e6 / 1e9, mhz
 
 
 def run_ours(args, rank, world):
@@ -190,12 +216,26 @@ def run_ours(args, rank, world):
     peak, peak_kind = _peaks()
     byt = _phase_bytes(per, W)
     roof = {}
-    for k in ("merge", "scatter", "det_pass"):
-        t_s = ph[k] / args.steps / 1e3
+    t_phase = {k: ph[k] / args.steps for k in ph}
+    t_phase["annihilation"] = t_phase["bucket_scan"] + t_phase["scatter"] + t_phase["merge"]
+    t_phase["iteration"] = t_max / args.steps
+    for k in ("annihilation", "merge", "scatter", "det_pass", "iteration"):
+        t_s = t_phase[k] / 1e3
         ach = byt[k] / t_s / 1e9
         roof[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                    "frac": round(ach / peak, 4), "traffic": None, "bytes_per_launch": int(byt[k]),
-                   "ms_per_launch": round(ph[k] / args.steps, 4), "peak_source": peak_kind}
+                   "ms_per_launch": round(t_phase[k], 4), "peak_source": peak_kind}
+    ipeak, imhz = _issue_peak()
+    att_launch = attempts / args.steps / world
+    t_att = ph["attempt"] / args.steps / 1e3
+    ach_i = ATTEMPT_INST_PER_ATTEMPT * att_launch / t_att / 1e9
+    roof_attempt = {"bound": "alu", "achieved": round(ach_i, 1), "peak": round(ipeak, 1),
+                    "unit": "G warp-instructions/s", "frac": round(ach_i / ipeak, 4),
+                    "traffic": int(ATTEMPT_DRAM_BYTES_PER_ATTEMPT * att_launch),
+                    "ms_per_launch": round(ph["attempt"] / args.steps, 4),
+                    "kernel": "k_attempt (spawning: Philox draw, excitation, spawn amount, bucket)",
+                    "per_unit": f"{ATTEMPT_INST_PER_ATTEMPT:.1f} warp instructions per attempt (ncu)",
+                    "peak_source": f"4 warp instructions/cycle/SM x {N_SM} SMs x {imhz:.0f} MHz"}
 
     # end to end through the C ABI with host buffers: upload, iterate, download
     e2e_steps = min(args.steps, 3)
@@ -227,13 +267,14 @@ def run_ours(args, rank, world):
                    "mean_spawns_per_step": float(rec["nspawn"].mean()),
                    "first_timed_iteration": int(rec["iter"][0]), "grow_seconds": round(t_grow, 2),
                    "l2": "inputs larger than L2 (no flush)", "parallelism": f"independent replicas x{world}"},
-        "roofline": dict(roof["merge"], kernel="k_merge (annihilation: tile sort + merge)"),
+        "roofline": roof_attempt,
         "roofline_phases": roof,
+        "annihilated_keys_per_s": float(rec2["nspawn"].sum()) / (t_phase["annihilation"] * args.steps / 1e3),
         "phase_ms_per_step": {k: round(v / args.steps, 4) for k, v in ph.items()},
         "phase_share": {k: round(v, 4) for k, v in share.items()},
         "dominant_phase": dominant,
         "e2e": e2e,
-        "gpu_launches": int(args.steps * 15),
+        "gpu_launches": int(args.steps * eng.launches_per_iteration()),
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -314,7 +355,7 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

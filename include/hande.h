@@ -198,6 +198,8 @@ typedef struct {
   int64_t max_bucket_spawns;  /* largest number of spawns that fell in one bucket */
   int64_t tile_capacity;      /* distinct spawned keys one bucket can hold on chip */
   int64_t ncore;              /* deterministic-space size */
+  int64_t launches_per_iteration; /* kernels one iteration launches (current settings) */
+  int64_t deferred_buckets;   /* buckets the warp annihilation left to block tiles */
 } hande_diag;
 hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out);
 

@@ -63,7 +63,8 @@ class _Estimate(C.Structure):
 class _Diag(C.Structure):
     _fields_ = [("error_bits", C.c_uint32), ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64),
                 ("nbuckets", C.c_int64), ("bucket_main", C.c_int64), ("max_bucket_spawns", C.c_int64),
-                ("tile_capacity", C.c_int64), ("ncore", C.c_int64)]
+                ("tile_capacity", C.c_int64), ("ncore", C.c_int64),
+                ("launches_per_iteration", C.c_int64), ("deferred_buckets", C.c_int64)]
 
 
 # names declared in include/hande.h, in order
@@ -223,6 +224,10 @@ class Hande:
         d = _Diag()
         self._check(self._lib.hande_diagnostics(self._h, C.byref(d)), "hande_diagnostics")
         return {name: getattr(d, name) for name, _ in _Diag._fields_}
+
+    def launches_per_iteration(self) -> int:
+        """Kernels one iteration launches with the current settings."""
+        return int(self.diagnostics()["launches_per_iteration"])
 
     def synchronize(self) -> None:
         self._check(self._lib.hande_synchronize(self._h), "hande_synchronize")
