@@ -303,10 +303,12 @@ static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* t
 // Exclusive scan of in[0, *n_ptr) into out by one block of 1024 threads, for
 // short arrays (bucket counts): chunks of 4096 loaded coalesced into shared
 // memory, 4 contiguous values per thread, block scan of the thread sums.  The
-// total goes to *total; above cap_check (if >= 0) it sets the state-capacity error.
+// total goes to *total; above cap_check (if >= 0) it sets the state-capacity
+// error.  With total_hi the values are two packed 32-bit counts, the totals of
+// the low and high halves go to *total and *total_hi.
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, const int64_t* n_ptr, int64_t* total,
-                                                    int64_t cap_check, DevState* st) {
+                                                    int64_t cap_check, DevState* st, int64_t* total_hi = nullptr) {
   if (st->error) return;
   constexpr int kPer = 4, kChunk = 1024 * kPer;
   __shared__ unsigned long long buf[kChunk];
@@ -364,8 +366,11 @@ __global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, con
     __syncthreads();
   }
   if (tid == 0) {
-    *total = (int64_t)carry;
-    if (cap_check >= 0 && (int64_t)carry > cap_check) set_error(st, ERR_STATE_CAPACITY);
+    // total_hi: the values are two packed 32-bit counts (sums stay below 2^32)
+    const int64_t lo = total_hi ? (int64_t)(carry & 0xffffffffull) : (int64_t)carry;
+    if (total_hi) *total_hi = (int64_t)(carry >> 32);
+    *total = lo;
+    if (cap_check >= 0 && lo > cap_check) set_error(st, ERR_STATE_CAPACITY);
   }
 }
 
@@ -1142,6 +1147,7 @@ struct MergeCtx {
   uint8_t* ofl;
   int64_t ostride;      // key-word stride of the output arrays
   int staged;           // output is the warp annihilation's staging list
+  int64_t bucket;       // staged: the bucket (its count word gets the new determinants)
 };
 
 // Merge the sorted unique spawns [0, nu) with the main segment entries [ml, mh)
@@ -1239,6 +1245,7 @@ __device__ int64_t tile_write(const Params& P, MergeSmem<W>& m, const MergeCtx& 
     c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
     if (c.staged) {
       c.ofl[o] = F_NEWDET;
+      atomicAdd(&P.tile_state[c.bucket], 1ull << 32);
     } else {
       c.ofl[o] = 0;
       P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
@@ -1319,6 +1326,7 @@ __device__ int64_t acc_write(const Params& P, MergeSmem<W>& m, const MergeCtx& c
     c.ohd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
     if (c.staged) {
       c.ofl[o] = F_NEWDET;
+      atomicAdd(&P.tile_state[c.bucket], 1ull << 32);
     } else {
       c.ofl[o] = 0;
       P.natt[atomicAdd((unsigned long long*)&st->nnew, 1ull)] = o;
@@ -1459,6 +1467,7 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
     const int64_t s0 = P.boff[b];
     const int64_t ns = P.bcount[b];
     c.m0 = b * sb;
+    c.bucket = b;
     const int nm = (int)((c.m0 + sb < n ? c.m0 + sb : n) - c.m0);
     for (int i = threadIdx.x; i < nm; i += blockDim.x) {
 #pragma unroll
@@ -1523,7 +1532,7 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
                                                                          : sort_reduce<W>(m, TC, nnew, wsum);
         const uint32_t nkeep = acc_decide<W>(P, m, c, TC, SM, nu, nm, wsum);
         if (staged) {
-          if (threadIdx.x == 0) P.tile_state[b] = nkeep;
+          if (threadIdx.x == 0) atomicAdd(&P.tile_state[b], (unsigned long long)nkeep);
           nwsum += acc_write<W, SYS>(P, m, c, TC, SM, nu, nm, nkeep, c.m0 + (int64_t)s0);
           continue;
         }
@@ -1650,7 +1659,7 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
       if (s_abort) break;
       if (staged) {
         if (threadIdx.x == 0) {
-          P.tile_state[b] = total;
+          atomicAdd(&P.tile_state[b], (unsigned long long)total);
           s_base = (unsigned long long)(c.m0 + s0);
         }
       } else if (threadIdx.x < 32) {

@@ -148,7 +148,8 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
     k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
     k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
     k_scan_one<unsigned long long, unsigned long long><<<1, 1024, 0, s>>>(
-        P.tile_state, P.tile_inc, nbk, st_field_i64(st, offsetof(DevState, ndet) + 8 * (cur ^ 1)), P.cap, st);
+        P.tile_state, P.tile_inc, nbk, st_field_i64(st, offsetof(DevState, ndet) + 8 * (cur ^ 1)), P.cap, st,
+        st_field_i64(st, offsetof(DevState, nnew)));
     k_merge_copy<W><<<E.attempt_grid * 2, 256, 0, s>>>(P, cur);
   } else {
     k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 0);

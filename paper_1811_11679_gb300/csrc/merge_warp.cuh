@@ -268,9 +268,12 @@ __device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c
 }
 
 // Write the entries wt_decide kept to the staging list at out + their rank
-// among the kept (new determinants flagged F_NEWDET).  Returns the sum of |N|.
+// among the kept (new determinants flagged F_NEWDET, counted in *nnew_out, all lanes).
+// Returns the sum of |N|.
 template <int W>
-__device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int u, int64_t out, int lane) {
+__device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int u, int64_t out, int lane,
+                            uint32_t* nnew_out) {
+  uint32_t nn = 0;
   DevState* st = P.st;
   int64_t nws = 0;
   for (int i = mi + lane; i < mh; i += 32) {
@@ -298,8 +301,11 @@ __device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int
     P.m_hd[o] = 0.0;   // H_ii - E_ref follows in k_new_hdiag
     P.m_flg[o] = F_NEWDET;
     nws += iabs64(p);
+    ++nn;
   }
-  __syncwarp();
+#pragma unroll
+  for (int o = 16; o; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+  *nnew_out = nn;
   return nws;
 }
 
@@ -389,8 +395,9 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
     }
     const int u = wt_sort_dedupe<W>(t, nnew, lane);
     const uint32_t nkeep = wt_decide<W>(P, t, c, 0, nm, u, true, lane);
-    nwsum += wt_write<W>(P, t, 0, nm, u, out, lane);
-    if (lane == 0) P.tile_state[b] = nkeep;
+    uint32_t nnw = 0;
+    nwsum += wt_write<W>(P, t, 0, nm, u, out, lane, &nnw);
+    if (lane == 0) P.tile_state[b] = (unsigned long long)nkeep | ((unsigned long long)nnw << 32);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) nwsum += __shfl_xor_sync(0xffffffffu, nwsum, o);
@@ -398,7 +405,9 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
 }
 
 // Compact the staged bucket lists into the new main list (one warp per bucket,
-// coalesced); new determinants are listed in natt[] for their diagonals.
+// coalesced) and list the new determinants (natt[]) for their diagonals.  The
+// bucket's packed scan result gives both its output offset (low 32 bits) and
+// its offset in the new-determinant list (high 32 bits).
 template <int W>
 __global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
   DevState* st = P.st;
@@ -410,8 +419,9 @@ __global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
   uint64_t* okey = P.key[nxt];
   for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
     const int64_t src = b * sb + (int64_t)P.boff[b];
-    const int64_t dst = (int64_t)P.tile_inc[b];
-    const int64_t cnt = (int64_t)P.tile_state[b];
+    const int64_t dst = (int64_t)(P.tile_inc[b] & 0xffffffffull);   // output offset
+    int64_t nslot = (int64_t)(P.tile_inc[b] >> 32);                  // offset in the new-determinant list
+    const int64_t cnt = (int64_t)(P.tile_state[b] & 0xffffffffull);
     // four groups of 32 entries per step: all loads first, then the stores
     for (int64_t i0 = 0; i0 < cnt; i0 += 128) {
       Key<W> kk[4];
@@ -441,12 +451,8 @@ __global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
           isnew = (ff[u] & F_NEWDET) != 0;
         }
         const unsigned m = __ballot_sync(0xffffffffu, isnew);
-        if (m) {
-          unsigned long long slot = 0;
-          if (lane == 0) slot = atomicAdd((unsigned long long*)&st->nnew, (unsigned long long)__popc(m));
-          slot = __shfl_sync(0xffffffffu, slot, 0);
-          if (isnew) P.natt[slot + __popc(m & ((1u << lane) - 1u))] = o;
-        }
+        if (isnew) P.natt[nslot + __popc(m & ((1u << lane) - 1u))] = o;
+        nslot += __popc(m);
       }
     }
   }
