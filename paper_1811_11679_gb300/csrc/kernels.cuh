@@ -576,10 +576,37 @@ __device__ __forceinline__ int64_t spawn_amount(const Params& P, uint64_t famt, 
   return neg ? -(int64_t)q : (int64_t)q;
 }
 
+// Bucket search of the spawning kernel: every r-th splitter (coarse, in shared
+// memory when the kernel stages them) then at most r - 1 splitters in global
+// memory.  bucket(k) = number of splitters s_j (1 <= j < nb) with s_j <= k.
+struct SplitIdx {
+  const uint64_t* coarse;   // coarse[c] = s_{c r}, c < nc
+  int64_t cstride, nc, r;
+  const uint64_t* fine;     // all splitters
+  int64_t fstride, nb;
+};
+
+template <int W>
+__device__ __forceinline__ uint32_t find_bucket(const SplitIdx& sx, const Key<W>& k) {
+  int64_t lo = 1, hi = sx.nc;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (key_le<W>(load_key<W>(sx.coarse, sx.cstride, mid), k)) lo = mid + 1;
+    else hi = mid;
+  }
+  const int64_t c = lo - 1;   // s_{c r} <= k < s_{(c+1) r}
+  int64_t blo = c * sx.r + 1, bhi = c * sx.r + sx.r < sx.nb ? c * sx.r + sx.r : sx.nb;
+  while (blo < bhi) {
+    const int64_t mid = (blo + bhi) >> 1;
+    if (key_le<W>(load_key<W>(sx.fine, sx.fstride, mid), k)) blo = mid + 1;
+    else bhi = mid;
+  }
+  return (uint32_t)(blo - 1);
+}
+
 // the top `take` queued spawns of this warp: bucket, rank, staging slot
 template <int W>
-__device__ void flush_spawns(const Params& P, const AttemptQueues& Q, int& pq_n, int take, int64_t nb,
-                             const uint64_t* split, int64_t split_stride) {
+__device__ void flush_spawns(const Params& P, const AttemptQueues& Q, int& pq_n, int take, const SplitIdx& sx) {
   DevState* st = P.st;
   const int lane = (int)warp_lane();
   const bool have = lane < take;
@@ -593,15 +620,7 @@ __device__ void flush_spawns(const Params& P, const AttemptQueues& Q, int& pq_n,
     for (int j = 0; j < W; ++j) child.w[j] = Q.pq_key[j * kQueue + e];
     amt = Q.pq_amt[e];
     initf = Q.pq_flg[e];
-    // bucket = number of splitters s_j (j >= 1) with s_j <= child
-    int64_t blo = 1, bhi = nb;
-    while (blo < bhi) {
-      int64_t mid = (blo + bhi) >> 1;
-      Key<W> sk = load_key<W>(split, split_stride, mid);
-      if (key_le<W>(sk, child)) blo = mid + 1;
-      else bhi = mid;
-    }
-    bkt = (uint32_t)(blo - 1);
+    bkt = find_bucket<W>(sx, child);
   }
   const unsigned want = __ballot_sync(0xffffffffu, have);
   int64_t base = 0;
@@ -625,8 +644,7 @@ __device__ void flush_spawns(const Params& P, const AttemptQueues& Q, int& pq_n,
 
 template <int W>
 __device__ __forceinline__ void push_spawn(const Params& P, const AttemptQueues& Q, int& pq_n, bool have,
-                                           const Key<W>& child, int64_t amt, uint8_t initf, int64_t nb,
-                                           const uint64_t* split, int64_t split_stride) {
+                                           const Key<W>& child, int64_t amt, uint8_t initf, const SplitIdx& sx) {
   const unsigned m = __ballot_sync(0xffffffffu, have);
   if (have) {
     const int e = pq_n + __popc(m & ((1u << warp_lane()) - 1u));
@@ -637,14 +655,13 @@ __device__ __forceinline__ void push_spawn(const Params& P, const AttemptQueues&
   }
   pq_n += __popc(m);
   __syncwarp();
-  if (pq_n >= 32) flush_spawns<W>(P, Q, pq_n, 32, nb, split, split_stride);
+  if (pq_n >= 32) flush_spawns<W>(P, Q, pq_n, 32, sx);
 }
 
 // the top `take` queued molecular singles: H_ia, core test, weight, rounding
 template <int W, int SYS>
 __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n, int& pq_n, int take,
-                              const uint64_t* key, const uint8_t* fl, int64_t nb, const uint64_t* split,
-                              int64_t split_stride) {
+                              const uint64_t* key, const uint8_t* fl, const SplitIdx& sx) {
   const int lane = (int)warp_lane();
   bool have = false;
   Key<W> child;
@@ -670,7 +687,7 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
   }
   sq_n -= take;
   __syncwarp();
-  push_spawn<W>(P, Q, pq_n, have, child, amt, initf, nb, split, split_stride);
+  push_spawn<W>(P, Q, pq_n, have, child, amt, initf, sx);
 }
 
 // largest i < n with a[i] <= x, given a[known] <= x (a non-decreasing):
@@ -733,13 +750,18 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
   const int64_t t = st->iter + 1;
   const uint64_t* key = P.key[cur];
   const uint8_t* fl = P.flags[cur];
-  // splitter keys staged in shared memory when they fit (bucket search on chip)
-  const bool split_on_chip = nb <= KS;
-  if (split_on_chip) {
-    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+  // every r-th splitter staged in shared memory (all of them when nb <= KS)
+  SplitIdx sx;
+  sx.r = (nb + KS - 1) / KS;
+  sx.nc = (nb + sx.r - 1) / sx.r;
+  sx.fine = P.split_key;
+  sx.fstride = P.cap;
+  sx.nb = nb;
+  sx.coarse = ssplit;
+  sx.cstride = KS;
+  for (int64_t c = threadIdx.x; c < sx.nc; c += blockDim.x) {
 #pragma unroll
-      for (int j = 0; j < W; ++j) ssplit[j * KS + b] = P.split_key[j * P.cap + b];
-    }
+    for (int j = 0; j < W; ++j) ssplit[j * KS + c] = P.split_key[j * P.cap + c * sx.r];
   }
   GenTabs gt{P.sys.hb_pair, P.sys.pair_ij};
   if (attempt_stage_bytes<W, SYS>() > 0) {
@@ -752,8 +774,6 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
     gt.pair_ij = sij;
   }
   __syncthreads();
-  const uint64_t* split = split_on_chip ? ssplit : P.split_key;
-  const int64_t split_stride = split_on_chip ? KS : P.cap;
   const int lane = (int)warp_lane();
   const int64_t total_warps = (int64_t)gridDim.x * kAttemptWarps;
   int sq_n = 0, pq_n = 0;   // warp-uniform queue lengths
@@ -847,13 +867,13 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       sq_n += __popc(sm);
       __syncwarp();
     }
-    push_spawn<W>(P, Q, pq_n, have, child, amt, initf, nb, split, split_stride);
+    push_spawn<W>(P, Q, pq_n, have, child, amt, initf, sx);
     if (SYS == SYS_MOLECULE && sq_n >= 32)
-      flush_singles<W, SYS>(P, Q, sq_n, pq_n, 32, key, fl, nb, split, split_stride);
+      flush_singles<W, SYS>(P, Q, sq_n, pq_n, 32, key, fl, sx);
   }
   if (SYS == SYS_MOLECULE && sq_n > 0)
-    flush_singles<W, SYS>(P, Q, sq_n, pq_n, sq_n, key, fl, nb, split, split_stride);
-  if (pq_n > 0) flush_spawns<W>(P, Q, pq_n, pq_n, nb, split, split_stride);
+    flush_singles<W, SYS>(P, Q, sq_n, pq_n, sq_n, key, fl, sx);
+  if (pq_n > 0) flush_spawns<W>(P, Q, pq_n, pq_n, sx);
 }
 
 template <int W>
