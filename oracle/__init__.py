@@ -74,7 +74,7 @@ def _load():
         lib.orc_philox.argtypes = [u64p, u64p, u64p]
         lib.orc_log.argtypes = [C.c_double]
         lib.orc_log.restype = C.c_double
-        lib.orc_to_fixed.argtypes = [C.c_double, i64p, u64p]
+        lib.orc_fixed_term.argtypes = [C.c_int64, C.c_double, i64p, u64p]
         lib.orc_fixed_product.argtypes = [C.c_double, C.c_double, C.c_int]
         lib.orc_fixed_product.restype = C.c_uint64
         lib.orc_create.argtypes = [C.POINTER(_System), C.POINTER(_Qmc)]
@@ -133,10 +133,10 @@ def log(x: float) -> float:
     return _load().orc_log(float(x))
 
 
-def to_fixed(x: float) -> int:
-    """round(x * 2^16) as a Python int (the 128-bit fixed-point term)."""
+def fixed_term(n: int, h: float) -> int:
+    """round_half_even(n h 2^16) of the exact product, as a Python int (the 128-bit term)."""
     hi, lo = C.c_int64(), C.c_uint64()
-    _load().orc_to_fixed(float(x), C.byref(hi), C.byref(lo))
+    _load().orc_fixed_term(int(n), float(h), C.byref(hi), C.byref(lo))
     return (hi.value << 64) | lo.value
 
 

@@ -135,21 +135,37 @@ double own_log(double x) {
 }
 
 /* ------------------------------------------------------------------ */
-/* 128-bit fixed point: value * 2^16, used so that sums of FP64 terms  */
-/* are exact and independent of summation order.                       */
+/* 128-bit fixed point: value * 2^16, used so that sums of products   */
+/* N h (population times matrix element) are exact and independent of  */
+/* summation order.  Each term is the exact product rounded once,       */
+/* half to even, to a multiple of 2^-16; magnitudes at or above 2^126   */
+/* saturate (matrix elements that large do not occur).                 */
 /* ------------------------------------------------------------------ */
-const double FX_SCALE = 65536.0;       /* 2^16 */
 const double FX_UNSCALE = 0x1p-16;
 
-i128 to_fixed(double term) {
-    double v = term * FX_SCALE;                 /* exact: power-of-two scaling */
-    double a = fabs(v);
-    double hi = floor(a * 0x1p-64);             /* exact */
-    double rem = a - hi * 18446744073709551616.0; /* exact: low bits of a */
-    uint64_t lo = (uint64_t)rint(rem);
-    u128 u = ((u128)(uint64_t)hi << 64) | (u128)lo;
-    i128 r = (i128)u;
-    return v < 0.0 ? -r : r;
+i128 fixed_term(int64_t n, double h) {
+    if (n == 0 || h == 0.0) return 0;
+    int e;
+    double f = frexp(fabs(h), &e);                   /* |h| = f 2^e, f in [1/2, 1) */
+    u128 m = (u128)(uint64_t)ldexp(f, 53);           /* exact 53-bit integer */
+    u128 a = (u128)(n < 0 ? (uint64_t)0 - (uint64_t)n : (uint64_t)n);
+    u128 p = m * a;                                  /* |n h| 2^16 = p 2^(e - 37) */
+    const u128 cap = (u128)1 << 126;
+    u128 q;
+    int sh = e - 37;
+    if (sh >= 0) {
+        q = (sh >= 126 || (p >> (126 - sh)) != 0) ? cap : p << sh;
+    } else if (-sh >= 128) {
+        q = 0;                                       /* p < 2^117 < half a unit */
+    } else {
+        int r = -sh;
+        q = p >> r;
+        u128 rem = p & (((u128)1 << r) - 1);
+        u128 half = (u128)1 << (r - 1);
+        if (rem > half || (rem == half && (q & 1))) q += 1;
+    }
+    i128 v = (i128)q;
+    return ((n < 0) != (h < 0.0)) ? -v : v;
 }
 
 double from_fixed(i128 s) {
@@ -679,7 +695,7 @@ void iterate_once(Ctx& c) {
         }
         if (wk.pop == 0 || exc_level(c, c.d0, wk.key) > 2) continue;
         double h0j = h_elem(c, wk.key, c.d0);
-        num += to_fixed((double)wk.pop * h0j);
+        num += fixed_term(wk.pop, h0j);
     }
     rec.num_hi = (int64_t)(num >> 64);
     rec.num_lo = (uint64_t)num;
@@ -784,7 +800,7 @@ void iterate_once(Ctx& c) {
             for (size_t k = 0; k < c.core_rows[r].size(); ++k) {
                 int col = c.core_rows[r][k].first;
                 double h = c.core_rows[r][k].second;
-                acc += to_fixed((double)c.main[pos[col]].pop * h);
+                acc += fixed_term(c.main[pos[col]].pop, h);
             }
             double y = from_fixed(acc);
             int64_t pr = c.main[pos[r]].pop;
@@ -929,8 +945,8 @@ typedef struct {
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
 double orc_log(double x) { return own_log(x); }
 uint64_t orc_fixed_product(double a, double b, int round) { return fixed_product(a, b, round); }
-void orc_to_fixed(double x, int64_t* hi, uint64_t* lo) {
-    i128 v = to_fixed(x);
+void orc_fixed_term(int64_t n, double h, int64_t* hi, uint64_t* lo) {
+    i128 v = fixed_term(n, h);
     *hi = (int64_t)(v >> 64);
     *lo = (uint64_t)v;
 }

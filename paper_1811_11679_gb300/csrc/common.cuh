@@ -254,25 +254,76 @@ __device__ __forceinline__ double log_series(double x) {
 }
 
 // ------------------------------------------------------------------ exact sums
-// term -> round_half_even(term * 2^16) as a signed 128-bit integer (lo, hi words)
+// round_half_even(n h 2^16) of the exact product of an int64 population n and
+// a double h, as a signed 128-bit integer (lo, hi words): the 53-bit
+// significand times |n| on the integer pipe, one rounding; magnitudes at or
+// above 2^126 saturate.  Sums of these terms are exact and order-free.
 struct I128 {
   uint64_t lo;
   int64_t hi;
 };
-__device__ __forceinline__ I128 fixed_from_double(double term) {
-  double v = __dmul_rn(term, 65536.0);
-  double a = fabs(v);
-  double h = floor(__dmul_rn(a, 0x1p-64));
-  double rem = __dsub_rn(a, __dmul_rn(h, 18446744073709551616.0));
-  uint64_t lo = __double2ull_rn(rem);
-  uint64_t hi = (uint64_t)h;
-  if (v < 0.0) {  // two's complement negate
-    lo = ~lo;
-    hi = ~hi;
-    lo += 1;
-    if (lo == 0) hi += 1;
+__device__ __forceinline__ I128 fixed_term(int64_t n, double h) {
+  const uint64_t hb = (uint64_t)__double_as_longlong(h);
+  if (n == 0 || (hb << 1) == 0) return {0ull, 0ll};
+  int e = (int)((hb >> 52) & 0x7ff);
+  uint64_t m = hb & ((1ull << 52) - 1);
+  if (e) m |= 1ull << 52;
+  else e = 1;
+  const uint64_t a = n < 0 ? 0ull - (uint64_t)n : (uint64_t)n;
+  const uint64_t lo = a * m, hi = __umul64hi(a, m);   // |n h| 2^16 = (hi:lo) 2^(e - 1059)
+  const int sh = e - 1059;
+  uint64_t qlo, qhi;
+  if (sh >= 0) {
+    bool sat;
+    if (sh >= 126) {
+      sat = true;
+    } else {
+      const int k = 126 - sh;   // (hi:lo) >> k != 0 ?
+      sat = k >= 64 ? (hi >> (k - 64)) != 0 : (hi != 0 || (lo >> k) != 0);
+    }
+    if (sat) {
+      qhi = 1ull << 62;
+      qlo = 0;
+    } else if (sh == 0) {
+      qhi = hi;
+      qlo = lo;
+    } else if (sh >= 64) {
+      qhi = lo << (sh - 64);
+      qlo = 0;
+    } else {
+      qhi = (hi << sh) | (lo >> (64 - sh));
+      qlo = lo << sh;
+    }
+  } else if (-sh >= 128) {
+    qhi = 0;
+    qlo = 0;
+  } else {
+    const int s = -sh;
+    if (s >= 64) {
+      qlo = hi >> (s - 64);
+      qhi = 0;
+    } else {
+      qlo = (lo >> s) | (hi << (64 - s));
+      qhi = hi >> s;
+    }
+    // half to even: round bit (bit s-1) and any lower bit
+    const int rb = s - 1;
+    const uint64_t rbit = rb >= 64 ? (hi >> (rb - 64)) & 1ull : (lo >> rb) & 1ull;
+    bool sticky;
+    if (rb >= 64) sticky = lo != 0 || (rb > 64 && (hi & ((1ull << (rb - 64)) - 1)) != 0);
+    else sticky = rb > 0 && (lo & ((1ull << rb) - 1)) != 0;
+    if (rbit && (sticky || (qlo & 1ull))) {
+      qlo += 1;
+      if (qlo == 0) qhi += 1;
+    }
   }
-  return {lo, (int64_t)hi};
+  if ((n < 0) != ((hb >> 63) != 0)) {   // two's complement negate
+    qlo = ~qlo;
+    qhi = ~qhi;
+    qlo += 1;
+    if (qlo == 0) qhi += 1;
+  }
+  return {qlo, (int64_t)qhi};
 }
 __device__ __forceinline__ void i128_add(I128& a, const I128& b) {
   uint64_t lo = a.lo + b.lo;

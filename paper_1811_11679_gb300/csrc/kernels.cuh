@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) {
       st->n0 = p;
     } else if (p != 0 && key_popc_xor<W>(k, d0) <= 4) {
       double h0j = h_elem<W, SYS>(P.sys, k, d0);
-      i128_add(num, fixed_from_double(__dmul_rn((double)p, h0j)));
+      i128_add(num, fixed_term(p, h0j));
     }
     bool init = !P.initiator || mag > P.init_thr || is0 || core;
     int64_t na = 0;
@@ -498,7 +498,7 @@ static __global__ void k_core_spmv(Params P, int cur) {
   I128 acc{0, 0};
   for (int64_t e = P.core_rowptr[r] + lane; e < P.core_rowptr[r + 1]; e += 32) {
     int64_t pc = pop[P.core_pos[P.core_col[e]]];
-    i128_add(acc, fixed_from_double(__dmul_rn((double)pc, P.core_val[e])));
+    i128_add(acc, fixed_term(pc, P.core_val[e]));
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {

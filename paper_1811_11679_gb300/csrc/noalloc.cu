@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) k_est_partials(SysDev sys, Ke
     if (key_eq<W>(k, d0)) {
       n0 += p;
     } else if (p != 0 && key_popc_xor<W>(k, d0) <= 4) {
-      i128_add(num, fixed_from_double(__dmul_rn((double)p, h_elem<W, SYS>(sys, k, d0))));
+      i128_add(num, fixed_term(p, h_elem<W, SYS>(sys, k, d0)));
     }
   }
   int64_t a = block_sum<int64_t>(nw, sh64);

@@ -74,18 +74,24 @@ def test_own_log_special_values():
 
 
 # --------------------------------------------------------------------------- fixed point
-def test_fixed_point_is_round_half_even_of_scaled_value():
+def test_fixed_point_term_is_round_half_even_of_the_exact_product():
+    """Each estimator / deterministic-space term is round_half_even(n h 2^16) of
+    the exact product of an int64 population and a double (checked with Fractions)."""
     rng = np.random.default_rng(3)
-    vals = list(rng.normal(0, 1, 2000) * 10.0 ** rng.integers(-8, 20, 2000))
-    vals += [0.5 / 65536, 1.5 / 65536, 2.5 / 65536, -0.5 / 65536, -1.5 / 65536, 0.0, 2.0 ** 70,
-             -(2.0 ** 70) - 2.0 ** 30]
-    for v in vals:
-        exact = Fraction(float(v)) * 65536
+    ns = [int(x) for x in rng.integers(-(2 ** 62), 2 ** 62, 2000)]
+    ns += [int(x) for x in rng.integers(-(2 ** 33), 2 ** 33, 2000)]
+    hs = list(rng.normal(0, 1, 4000) * 10.0 ** rng.integers(-12, 4, 4000))
+    # exact ties (n h 2^16 = k + 1/2), subnormal and tiny h, zero, extremes
+    ns += [1, 3, -1, -3, 5, 7, 2 ** 62 - 1, -(2 ** 62), 1, 123456789, 0, 1]
+    hs += [2.0 ** -17, 2.0 ** -17, 2.0 ** -17, 2.0 ** -17, 0.1, 2.5 * 2.0 ** -16, 3.75, -0.001,
+           5e-324, 2.2e-308, 1.0, 0.0]
+    for n, h in zip(ns, hs):
+        exact = Fraction(n) * Fraction(float(h)) * 65536
         fl = math.floor(exact)
         rem = exact - fl
         if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
             fl += 1
-        assert oracle.to_fixed(float(v)) == fl, v
+        assert oracle.fixed_term(n, float(h)) == fl, (n, h)
 
 
 def test_spawn_amount_is_one_rounding_of_the_exact_product():
