@@ -47,6 +47,7 @@ struct WarpTile {
   uint8_t mflg[kMwMain];       // segment entry flags
   uint32_t keep[kMwKeepWords]; // keep bits by merged rank
   uint32_t kpre[kMwKeepWords]; // kept entries before each word
+  int16_t rq[kMwMain + kMwNew];  // entries awaiting their occupation-rounding draw
 };
 
 template <int W>
@@ -222,37 +223,65 @@ __device__ __forceinline__ int wt_sort_dedupe(WarpTile<W>& t, int n, int lane) {
 
 // Decide one merge segment: the segment entries [mi, mh) and the unique new
 // keys [0, u) (all between the same neighbours).  Merged ranks, final
-// populations (stored when `store`), keep bits and their per-word prefix.
-// Segment entries keep their slot if core or reference, otherwise they survive
-// with a nonzero population after the occupation rounding; new determinants need
-// an initiator parent (Sec. 2.1) and a nonzero amount.  Returns the number kept.
+// populations, keep bits and their per-word prefix.  Segment entries keep their
+// slot if core or reference, otherwise they survive with a nonzero population
+// after the occupation rounding; new determinants need an initiator parent
+// (Sec. 2.1) and a nonzero amount.  Entries that need the rounding draw
+// (0 < |N| < 1 walker, real weights) are queued and drawn 32 at a time, so the
+// Philox rounds run on full warps.  Returns the number kept.
 template <int W>
-__device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c, int mi, int mh, int u,
-                              bool store, int lane) {
+__device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c, int mi, int mh, int u, int lane) {
   const int nc = (mh - mi) + u;
   const int nw = (nc + 31) >> 5;
   for (int w = lane; w < nw; w += 32) t.keep[w] = 0;
   __syncwarp();
-  for (int i = mi + lane; i < mh; i += 32) {
-    const Key<W> k = wt_mkey<W>(t, i);
-    const int r = (i - mi) + wt_lb_new<W>(t, u, k);
-    int64_t p = t.macc[i];
-    const uint8_t f = t.mflg[i];
-    const bool always = (f & (F_CORE | F_REF)) != 0;
-    if (!always) p = round_small<W>(P, c.t, k, p);
-    if (store) t.macc[i] = p;
-    t.mrank[i] = (int16_t)r;
-    if (always || p != 0) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+  const unsigned below = (1u << lane) - 1u;
+  int qn = 0;
+  for (int i0 = mi; i0 < mh; i0 += 32) {
+    const int i = i0 + lane;
+    bool need = false;
+    if (i < mh) {
+      const int r = (i - mi) + wt_lb_new<W>(t, u, wt_mkey<W>(t, i));
+      const int64_t p = t.macc[i];
+      const bool always = (t.mflg[i] & (F_CORE | F_REF)) != 0;
+      need = !always && P.real_amp && p != 0 && iabs64(p) < kOne;
+      t.mrank[i] = (int16_t)r;
+      if (always || (p != 0 && !need)) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (need) t.rq[qn + __popc(m & below)] = (int16_t)i;
+    qn += __popc(m);
   }
-  for (int j = lane; j < u; j += 32) {
-    const Key<W> k = wt_nkey<W>(t, j);
-    const int r = j + (wt_lb_main<W>(t, mi, mh, k) - mi);
-    int64_t p = t.namt[j];
-    const bool ok = (!P.initiator || (t.nflg[j] & 1u)) && p != 0;
-    if (ok) p = round_small<W>(P, c.t, k, p);
-    t.namt[j] = p;
-    t.nrank[j] = (int16_t)r;
-    if (ok && p != 0) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+  for (int j0 = 0; j0 < u; j0 += 32) {
+    const int j = j0 + lane;
+    bool need = false;
+    if (j < u) {
+      const int r = j + (wt_lb_main<W>(t, mi, mh, wt_nkey<W>(t, j)) - mi);
+      const int64_t p = t.namt[j];
+      const bool ok = (!P.initiator || (t.nflg[j] & 1u)) && p != 0;
+      need = ok && P.real_amp && iabs64(p) < kOne;
+      t.nrank[j] = (int16_t)r;
+      if (ok && !need) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+      if (!ok) t.namt[j] = 0;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, need);
+    if (need) t.rq[qn + __popc(m & below)] = (int16_t)(kMwMain + j);
+    qn += __popc(m);
+  }
+  __syncwarp();
+  // occupation rounding (R-13) of the queued entries, full warps
+  for (int q0 = 0; q0 < qn; q0 += 32) {
+    if (q0 + lane < qn) {
+      const int x = t.rq[q0 + lane];
+      const bool isnew = x >= kMwMain;
+      const int idx = isnew ? x - kMwMain : x;
+      const Key<W> k = isnew ? wt_nkey<W>(t, idx) : wt_mkey<W>(t, idx);
+      const int64_t p = round_small<W>(P, c.t, k, isnew ? t.namt[idx] : t.macc[idx]);
+      if (isnew) t.namt[idx] = p;
+      else t.macc[idx] = p;
+      const int r = isnew ? t.nrank[idx] : t.mrank[idx];
+      if (p != 0) atomicOr(&t.keep[r >> 5], 1u << (r & 31));
+    }
   }
   __syncwarp();
   const int cnt = lane < nw ? __popc(t.keep[lane]) : 0;
@@ -394,7 +423,7 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
       continue;
     }
     const int u = wt_sort_dedupe<W>(t, nnew, lane);
-    const uint32_t nkeep = wt_decide<W>(P, t, c, 0, nm, u, true, lane);
+    const uint32_t nkeep = wt_decide<W>(P, t, c, 0, nm, u, lane);
     uint32_t nnw = 0;
     nwsum += wt_write<W>(P, t, 0, nm, u, out, lane, &nnw);
     if (lane == 0) P.tile_state[b] = (unsigned long long)nkeep | ((unsigned long long)nnw << 32);
