@@ -163,6 +163,17 @@ def _issue_peak():
     return 4 * N_SM * mhz * 1e6 / 1e9, mhz
 
 
+def aggregate_ranks(ms: float, attempts: float, device: str):
+    """Whole-job figures over the ranks of the process group: the slowest
+    rank's timed region (max) and the attempts of all ranks (sum)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    a = torch.tensor([attempts], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(a, op=torch.distributed.ReduceOp.SUM)
+    return float(t[0]), float(a[0])
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -198,11 +209,7 @@ def run_ours(args, rank, world):
     attempts = float(rec["natt"].sum())
     t_max = ms
     if world > 1:
-        t = torch.tensor([ms, attempts], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        t_max, attempts = float(tmax[0]), float(t[1])
+        t_max, attempts = aggregate_ranks(ms, attempts, "cuda")
     value = attempts / (t_max / 1e3)
 
     # per-phase device time (kernel-by-kernel launches with events), same stream
