@@ -108,12 +108,27 @@ __device__ __forceinline__ int key_between(const Key<W>& k, int p, int q) {
   }
   return n;
 }
-// position of the r-th (0-based) set bit of a 64-bit word
+// position of the r-th (0-based) set bit of x (r < popcount(x)): bisection of
+// the word with popcounts of its lower halves, 32 down to 1 bit
 __device__ __forceinline__ int select64(uint64_t x, int r) {
-  unsigned lo = (unsigned)x, hi = (unsigned)(x >> 32);
-  int c = __popc(lo);
-  if (r < c) return __fns(lo, 0, r + 1);
-  return 32 + __fns(hi, 0, r - c + 1);
+  int pos = 0;
+  int c = __popc((unsigned)x);
+  if (r >= c) {
+    r -= c;
+    x >>= 32;
+    pos = 32;
+  }
+  unsigned w = (unsigned)x;
+#pragma unroll
+  for (int width = 16; width; width >>= 1) {
+    c = __popc(w & ((1u << width) - 1u));
+    if (r >= c) {
+      r -= c;
+      w >>= width;
+      pos += width;
+    }
+  }
+  return pos;
 }
 // position of the r-th set bit of a multiword mask
 template <int W>
