@@ -21,6 +21,7 @@ struct Ops {
   void (*csr_count)(Engine& E, int32_t* rowcnt, cudaStream_t s);
   void (*csr_fill)(Engine& E, cudaStream_t s);
   void (*sel_gather)(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s);
+  void (*core_hash)(Engine& E, uint32_t* table, cudaStream_t s);
   void (*sel_hist)(Engine& E, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist,
                    cudaStream_t s);
   void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);
@@ -64,6 +65,8 @@ struct Engine {
   int32_t* core_col = nullptr;
   double* core_val = nullptr;
   int64_t nnz_cap = 0, ncore_cap = 0;
+  uint32_t* core_table = nullptr;   // core membership hash table
+  int64_t core_table_cap = 0;
   double e_ref = 0.0;
   bool failed = false;
   unsigned err_bits = 0;

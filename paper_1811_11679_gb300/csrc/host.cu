@@ -438,6 +438,18 @@ void select_core(Engine& E) {
   E.ops.sel_gather(E, cur, E.core_key, ncore, E.stream);
   P.ncore = (int)ncore;
   P.core_key = E.core_key;
+  // membership hash table: a power of two >= 4 ncore slots
+  int64_t tsize = 64;
+  while (tsize < 4 * ncore) tsize <<= 1;
+  if (tsize > E.core_table_cap) {
+    E.core_table = dalloc<uint32_t>(E, tsize);
+    E.core_table_cap = tsize;
+  }
+  CK(cudaMemsetAsync(E.core_table, 0, (size_t)tsize * 4, E.stream));
+  P.core_hmask = (uint32_t)(tsize - 1);
+  P.core_hash = E.core_table;
+  if (ncore > 0) E.ops.core_hash(E, E.core_table, E.stream);
+  CK(cudaGetLastError());
   // CSR of H' restricted to the core
   int32_t* rowcnt = dalloc<int32_t>(E, ncore);
   E.ops.csr_count(E, rowcnt, E.stream);

@@ -104,6 +104,8 @@ struct Params {
   // deterministic space
   int ncore;
   const uint64_t* core_key;
+  const uint32_t* core_hash;   // open-addressing table of core indices + 1 (0 = empty)
+  uint32_t core_hmask;         // table size - 1 (a power of two >= 4 ncore)
   int64_t* core_pos;
   const int64_t* core_rowptr;
   const int32_t* core_col;
@@ -461,16 +463,36 @@ __device__ __forceinline__ int64_t lower_bound_main(const uint64_t* key, int64_t
   }
   return lo;
 }
+// Fibonacci hash of the XOR-folded key words
+template <int W>
+__device__ __forceinline__ uint32_t key_hash(const Key<W>& k) {
+  uint64_t x = k.w[0];
+#pragma unroll
+  for (int j = 1; j < W; ++j) x ^= k.w[j] * 0xC2B2AE3D27D4EB4Full + (uint64_t)j;
+  return (uint32_t)((x * 0x9E3779B97F4A7C15ull) >> 32);
+}
+// membership in the deterministic space: linear probing of the core hash table
 template <int W>
 __device__ __forceinline__ bool in_core(const Params& P, const Key<W>& k) {
-  int lo = 0, hi = P.ncore;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    Key<W> m = load_key<W>(P.core_key, P.ncore, mid);
-    if (key_lt<W>(m, k)) lo = mid + 1;
-    else hi = mid;
+  uint32_t h = key_hash<W>(k) & P.core_hmask;
+  for (uint32_t probe = 0; probe <= P.core_hmask; ++probe) {
+    const uint32_t v = __ldg(&P.core_hash[h]);
+    if (v == 0) return false;
+    if (key_eq<W>(load_key<W>(P.core_key, P.ncore, (int64_t)v - 1), k)) return true;
+    h = (h + 1) & P.core_hmask;
   }
-  return lo < P.ncore && key_eq<W>(load_key<W>(P.core_key, P.ncore, lo), k);
+  return false;
+}
+// insert every core key (table zeroed, at most a quarter full)
+template <int W>
+__global__ void k_core_hash(Params P, uint32_t* table) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.ncore) return;
+  uint32_t h = key_hash<W>(load_key<W>(P.core_key, P.ncore, r)) & P.core_hmask;
+  for (uint32_t probe = 0; probe <= P.core_hmask; ++probe) {
+    if (atomicCAS(&table[h], 0u, (uint32_t)r + 1u) == 0u) return;
+    h = (h + 1) & P.core_hmask;
+  }
 }
 template <int W>
 __global__ void k_core_locate(Params P, int cur) {

@@ -192,6 +192,10 @@ void enqueue_sel_flags(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int 
   k_sel_flags<W><<<4 * 152, 256, 0, s>>>(E.P, cur, vstar, need_eq, stage);
 }
 template <int W>
+void enqueue_core_hash(Engine& E, uint32_t* table, cudaStream_t s) {
+  k_core_hash<W><<<(E.P.ncore + 255) / 256, 256, 0, s>>>(E.P, table);
+}
+template <int W>
 void enqueue_sel_gather(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s) {
   k_sel_gather<W><<<4 * 152, 256, 0, s>>>(E.P, cur, core_key, ncore);
 }
@@ -210,6 +214,7 @@ Ops make_ops() {
   o.csr_count = &enqueue_csr_count<W, SYS>;
   o.csr_fill = &enqueue_csr_fill<W, SYS>;
   o.sel_gather = &enqueue_sel_gather<W>;
+  o.core_hash = &enqueue_core_hash<W>;
   o.sel_hist = &enqueue_sel_hist<W>;
   o.sel_flags = &enqueue_sel_flags<W>;
   o.merge_smem = &merge_smem_w<W>;
