@@ -433,6 +433,7 @@ void select_core(Engine& E) {
     E.ncore_cap = ncore;
     P.core_pos = dalloc<int64_t>(E, ncore);
     P.core_delta = dalloc<int64_t>(E, ncore);
+    P.core_x = dalloc<int64_t>(E, ncore);
     E.core_rowptr = dalloc<int64_t>(E, ncore + 1);
   }
   E.ops.sel_gather(E, cur, E.core_key, ncore, E.stream);

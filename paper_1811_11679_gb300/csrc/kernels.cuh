@@ -111,6 +111,7 @@ struct Params {
   const int32_t* core_col;
   const double* core_val;
   int64_t* core_delta;
+  int64_t* core_x;      // the core determinants' populations N(t-1), gathered by k_core_locate
   // state
   DevState* st;
   Record* rec;
@@ -508,6 +509,7 @@ __global__ void k_core_locate(Params P, int cur) {
     pos = 0;
   }
   P.core_pos[r] = pos;
+  P.core_x[r] = P.pop[cur][pos];
 }
 // one warp per core row: y_r = sum_c H'_rc N_c exactly, dN_r = -rint(tau (y_r - S N_r))
 static __global__ void k_core_spmv(Params P, int cur) {
@@ -516,10 +518,9 @@ static __global__ void k_core_spmv(Params P, int cur) {
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (r >= P.ncore) return;
-  const int64_t* pop = P.pop[cur];
   I128 acc{0, 0};
   for (int64_t e = P.core_rowptr[r] + lane; e < P.core_rowptr[r + 1]; e += 32) {
-    int64_t pc = pop[P.core_pos[P.core_col[e]]];
+    int64_t pc = P.core_x[P.core_col[e]];
     i128_add(acc, fixed_term(pc, P.core_val[e]));
   }
 #pragma unroll
@@ -529,7 +530,7 @@ static __global__ void k_core_spmv(Params P, int cur) {
   }
   if (lane == 0) {
     double y = fixed_to_double(acc);
-    int64_t pr = pop[P.core_pos[r]];
+    int64_t pr = P.core_x[r];
     double v = __dsub_rn(y, __dmul_rn(st->shift, (double)pr));
     double x = __dmul_rn(P.tau, v);
     P.core_delta[r] = -__double2ll_rn(x);
