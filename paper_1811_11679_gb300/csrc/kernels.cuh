@@ -377,23 +377,53 @@ __global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, con
   }
 }
 
-// out[i] = exclusive prefix of in over the block's chunk + part[block]
+// out[i] = exclusive prefix of in over the block's chunk + part[block]; each
+// round takes 4 consecutive values per thread (4 x blockDim per round)
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,
                                                              const int64_t* part, DevState* st) {
   if (st->error) return;
-  __shared__ T tile[kScanThreads];
+  constexpr int kItems = 4;
   __shared__ T wsum[33];
   int64_t beg, end;
   block_chunk(*n_ptr, beg, end);
+  const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5);
   T carry = (T)part[blockIdx.x];
-  for (int64_t base = beg; base < end; base += blockDim.x) {
-    int64_t i = base + threadIdx.x;
-    tile[threadIdx.x] = i < end ? in[i] : T(0);
+  for (int64_t base = beg; base < end; base += (int64_t)blockDim.x * kItems) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
+    T v[kItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      v[k] = i0 + k < end ? in[i0 + k] : T(0);
+      sum += v[k];
+    }
+    T x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
     __syncthreads();
-    T tot = block_scan_excl<T>(tile, blockDim.x, wsum);
-    if (i < end) out[i] = carry + tile[threadIdx.x];
-    carry += tot;
+    if (wid == 0) {
+      const T w0 = lane < nw ? wsum[lane] : T(0);
+      T inc = w0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane < nw) wsum[lane] = inc - w0;
+      if (lane == 31) wsum[32] = inc;
+    }
+    __syncthreads();
+    T run = carry + wsum[wid] + x - sum;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      if (i0 + k < end) out[i0 + k] = run;
+      run += v[k];
+    }
+    carry += wsum[32];
     __syncthreads();
   }
 }
