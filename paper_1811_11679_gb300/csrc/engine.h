@@ -45,6 +45,8 @@ struct Engine {
   int W = 1, kind = 0, nalpha = 0, nbeta = 0;
   cudaStream_t stream = nullptr;      // caller's stream
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  cudaStream_t aux_stream = nullptr;  // second branch of a captured iteration
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   hande_allocator alloc{};
   bool has_alloc = false;
   std::vector<std::pair<void*, size_t>> blocks;

@@ -74,6 +74,13 @@ void release_all(Engine& E) {
     cudaStreamDestroy(E.cap_stream);
     E.cap_stream = nullptr;
   }
+  if (E.aux_stream) {
+    cudaStreamDestroy(E.aux_stream);
+    E.aux_stream = nullptr;
+  }
+  if (E.ev_fork) cudaEventDestroy(E.ev_fork);
+  if (E.ev_join) cudaEventDestroy(E.ev_join);
+  E.ev_fork = E.ev_join = nullptr;
 }
 
 // ---------------------------------------------------------------- system tables
@@ -545,6 +552,9 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     }
     E.ops = E.W == 1 ? ops_w1(s.kind) : (E.W == 2 ? ops_w2(s.kind) : ops_w8(s.kind));
     CK(cudaStreamCreateWithFlags(&E.cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&E.aux_stream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&E.ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&E.ev_join, cudaEventDisableTiming));
 
     Params& P = E.P;
     P.W = E.W;

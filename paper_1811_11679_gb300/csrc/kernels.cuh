@@ -449,9 +449,10 @@ __global__ void k_split(Params P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t n = st->ndet[cur];
-  // expected spawns: the previous iteration's count with 25% headroom (the
-  // attempt count before the first iteration)
-  const int64_t na = st->nspawn_prev > 0 ? st->nspawn_prev + st->nspawn_prev / 4 : st->natt;
+  // expected spawns: the previous iteration's count with 25% headroom (twice
+  // the determinants before the first iteration; this kernel may run beside the
+  // det pass and the attempt scan, so it reads nothing they write)
+  const int64_t na = st->nspawn_prev > 0 ? st->nspawn_prev + st->nspawn_prev / 4 : 2 * n;
   int64_t sb = (int64_t)P.seg_max;
   const int64_t per = P.bucket_spawns;   // expected spawns per bucket
   if (na > 0) {

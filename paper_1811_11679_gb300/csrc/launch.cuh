@@ -120,20 +120,43 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   auto mark = [&](int k) {
     if (ev) cudaEventRecord(ev[k], s);
   };
-  mark(0);
-  k_det_pass<W, SYS><<<kScanBlocks, kScanThreads, 0, s>>>(P, cur);
-  mark(1);
-  k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, natt)), st);
-  k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, s>>>(
-      P.natt, P.att_begin, st_field_i64(st, offsetof(DevState, ndet) + 8 * cur), P.part, st);
-  mark(2);
-  k_split<W><<<kScanBlocks, 256, 0, s>>>(P, cur);
-  mark(3);
-  if (core && P.ncore > 0) {
-    int nb = (P.ncore + 255) / 256;
-    k_core_locate<W><<<nb, 256, 0, s>>>(P, cur);
-    k_core_spmv<<<(int)(((int64_t)P.ncore * 32 + 255) / 256), 256, 0, s>>>(P, cur);
-    k_core_apply<<<nb, 256, 0, s>>>(P, cur);
+  const bool with_core = core && P.ncore > 0;
+  const int ncb = (P.ncore + 255) / 256;
+  if (!ev && E.aux_stream) {
+    // captured iteration: the bucket split and the deterministic-space product
+    // (they read only keys, the core populations and the CSR) run on a second
+    // branch beside the det pass and the attempt scan; the core update waits
+    // for both (the det pass reads the core populations).  A failing record or
+    // wait invalidates the capture, which ending the capture reports.
+    (void)(cudaEventRecord(E.ev_fork, s));
+    (void)(cudaStreamWaitEvent(E.aux_stream, E.ev_fork, 0));
+    k_split<W><<<kScanBlocks, 256, 0, E.aux_stream>>>(P, cur);
+    if (with_core) {
+      k_core_locate<W><<<ncb, 256, 0, E.aux_stream>>>(P, cur);
+      k_core_spmv<<<(int)(((int64_t)P.ncore * 32 + 255) / 256), 256, 0, E.aux_stream>>>(P, cur);
+    }
+    (void)(cudaEventRecord(E.ev_join, E.aux_stream));
+    k_det_pass<W, SYS><<<kScanBlocks, kScanThreads, 0, s>>>(P, cur);
+    k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, natt)), st);
+    k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, s>>>(
+        P.natt, P.att_begin, st_field_i64(st, offsetof(DevState, ndet) + 8 * cur), P.part, st);
+    (void)(cudaStreamWaitEvent(s, E.ev_join, 0));
+    if (with_core) k_core_apply<<<ncb, 256, 0, s>>>(P, cur);
+  } else {
+    mark(0);
+    k_det_pass<W, SYS><<<kScanBlocks, kScanThreads, 0, s>>>(P, cur);
+    mark(1);
+    k_scan_partials_i64<<<1, 1024, 0, s>>>(P.part, kScanBlocks, st_field_i64(st, offsetof(DevState, natt)), st);
+    k_scan_apply<int64_t><<<kScanBlocks, kScanThreads, 0, s>>>(
+        P.natt, P.att_begin, st_field_i64(st, offsetof(DevState, ndet) + 8 * cur), P.part, st);
+    mark(2);
+    k_split<W><<<kScanBlocks, 256, 0, s>>>(P, cur);
+    mark(3);
+    if (with_core) {
+      k_core_locate<W><<<ncb, 256, 0, s>>>(P, cur);
+      k_core_spmv<<<(int)(((int64_t)P.ncore * 32 + 255) / 256), 256, 0, s>>>(P, cur);
+      k_core_apply<<<ncb, 256, 0, s>>>(P, cur);
+    }
   }
   mark(4);
   k_attempt<W, SYS><<<E.attempt_grid, kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(P, cur);
