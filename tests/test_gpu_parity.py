@@ -81,11 +81,20 @@ def test_ueg_128bit_initiator_real_weights():
     assert max(sizes) > 1000
 
 
-def test_ueg_512bit_keys():
+@pytest.mark.parametrize("annihilation", [0, 2])
+def test_ueg_512bit_keys(annihilation):
+    """512-bit keys: block tiles by default, and the warp-per-bucket path on request."""
     sysd = inputs.ueg_system(14, 38, 1.0, key_words=8)
     q = inputs.qmc_params(tau=0.002, target_population=5000, initiator=1, real_amplitudes=1,
                           spawn_cutoff=0.1, init_pop=100, seed=7)
+    q["annihilation"] = annihilation
     _run_parity(sysd, q, 80)
+
+
+def test_ueg_128bit_block_annihilation():
+    """128-bit keys on the block-tile annihilation (the default there is one warp per bucket)."""
+    sysd, q = inputs.workload("ueg14", target_population=20000, init_pop=1000, annihilation=1)
+    _run_parity(sysd, q, 60)
 
 
 def test_ueg_64bit_keys_19_orbitals():
