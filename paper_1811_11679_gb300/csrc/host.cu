@@ -971,10 +971,10 @@ hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out) {
     out->tile_capacity = E.P.tile_cap;
     out->ncore = E.P.ncore;
     // det pass, attempt scan (2), split, attempts, bucket scan, scatter,
-    // annihilation (1, or 4 on the warp path), new diagonals, finalize, and the
+    // annihilation (1, or 5 on the warp path), new diagonals, finalize, and the
     // deterministic-space projection (3) once it is active
-    out->launches_per_iteration = 10 + (E.merge_warp ? 3 : 0) + (E.core_active && E.P.ncore > 0 ? 3 : 0);
-    out->deferred_buckets = hs.ndefer;
+    out->launches_per_iteration = 10 + (E.merge_warp ? 4 : 0) + (E.core_active && E.P.ncore > 0 ? 3 : 0);
+    out->deferred_buckets = hs.ndefer + hs.nbig;
     int64_t nb = std::min<int64_t>(hs.nbuckets, E.P.cap);
     if (nb > 0) {
       std::vector<uint32_t> cnt((size_t)nb);

@@ -56,6 +56,8 @@ struct DevState {
   unsigned error;
   unsigned merge_ticket;
   unsigned defer_ticket;   // block-kernel tickets over the deferred buckets
+  unsigned big_ticket;     // block-kernel tickets over all buckets (large-bucket pass)
+  int64_t nbig;            // large buckets taken by block tiles
   int64_t ndefer;          // buckets the warp annihilation left to the block kernel
 };
 
@@ -469,6 +471,8 @@ __global__ void k_split(Params P, int cur) {
     st->nnew = 0;
     st->merge_ticket = 0;
     st->defer_ticket = 0;
+    st->big_ticket = 0;
+    st->nbig = 0;
     st->ndefer = 0;
     if (nb > P.cap) set_error(st, ERR_BUCKET_CAPACITY);
   }
@@ -1528,7 +1532,15 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
       s_abort = 0;
       if (st->error) {
         tile_id = -1;
-      } else if (staged) {
+      } else if (staged == 2) {   // the large buckets (more spawns than a warp takes)
+        const int64_t lim = 8 * (int64_t)P.warp_cap;
+        int64_t tk;
+        do {
+          tk = (int64_t)atomicAdd(&st->big_ticket, 1u);
+        } while (tk < st->nbuckets && (int64_t)P.bcount[tk] <= lim);
+        tile_id = tk < st->nbuckets ? (int)tk : -1;
+        if (tk < st->nbuckets) atomicAdd((unsigned long long*)&st->nbig, 1ull);
+      } else if (staged) {        // the buckets the warp kernel deferred
         const int64_t tk = (int64_t)atomicAdd(&st->defer_ticket, 1u);
         tile_id = tk < st->ndefer ? (int)P.att_begin[tk] : -1;
       } else {

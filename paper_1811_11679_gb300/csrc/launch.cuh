@@ -168,8 +168,19 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
   mark(7);
   if (E.merge_warp) {
-    k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
-    k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
+    if (!ev && E.aux_stream) {   // large buckets on block tiles beside the warp kernel
+      (void)cudaEventRecord(E.ev_fork, s);
+      (void)cudaStreamWaitEvent(E.aux_stream, E.ev_fork, 0);
+      k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, E.aux_stream>>>(P, cur, 2);
+      (void)cudaEventRecord(E.ev_join, E.aux_stream);
+      k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
+      k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
+      (void)cudaStreamWaitEvent(s, E.ev_join, 0);
+    } else {
+      k_merge_warp<W, SYS><<<E.merge_warp_grid, kMwThreads, E.ops.merge_warp_smem, s>>>(P, cur);
+      k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 2);
+      k_merge<W, SYS><<<E.merge_grid, kMergeThreads, E.merge_smem_bytes, s>>>(P, cur, 1);
+    }
     k_scan_one<unsigned long long, unsigned long long><<<1, 1024, 0, s>>>(
         P.tile_state, P.tile_inc, nbk, st_field_i64(st, offsetof(DevState, ndet) + 8 * (cur ^ 1)), P.cap, st,
         st_field_i64(st, offsetof(DevState, nnew)));

@@ -18,10 +18,11 @@
 //   5. the kept entries are written, in merged order, to a staging list at an
 //      upper bound of the bucket's output offset (b sb + the spawns of the
 //      buckets before b), so no bucket waits for another.
-// A bucket with more spawns than a warp should take (8 x the staging), or whose
-// distinct new keys overflow the staging, is deferred to the block kernel
-// (k_merge in staged mode: 256 threads, sub-ranges for very large buckets),
-// which writes to the same staging list.  A one-block scan of the kept counts
+// A bucket with more spawns than a warp should take (8 x the staging) goes to
+// the block kernel (k_merge in staged mode 2: 256 threads, sub-ranges for very
+// large buckets), which runs beside this kernel; a bucket whose distinct new
+// keys overflow the staging is deferred to a second block-kernel pass after it
+// (staged mode 1).  Both write to the same staging list.  A one-block scan of the kept counts
 // (k_scan_one) then gives every bucket its output offset, and a coalesced copy
 // compacts the staging list into the new main list.
 #pragma once
@@ -363,10 +364,7 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
     if (b < 0 || b >= nb) break;
     const int64_t s0 = P.boff[b];
     const int64_t ns = P.bcount[b];
-    if (ns > 8 * (int64_t)cap) {   // large bucket: the block kernel takes it
-      if (lane == 0) P.att_begin[atomicAdd((unsigned long long*)&st->ndefer, 1ull)] = b;
-      continue;
-    }
+    if (ns > 8 * (int64_t)cap) continue;   // large bucket: block tiles take it (k_merge, staged 2)
     c.m0 = b * sb;
     const int nm = (int)((c.m0 + sb < n ? c.m0 + sb : n) - c.m0);
 #pragma unroll 2
