@@ -246,7 +246,9 @@ def run_ours(args, rank, world):
 
     # end to end through the C ABI with host buffers: upload, iterate, download
     e2e_steps = min(args.steps, 3)
-    k_h, p_h, h_h, _ = eng.walkers()
+    nd_now = int(eng.diagnostics()["ndet"])
+    bufs = eng.host_buffers(int(nd_now * 1.5) + 1024)   # page-locked, reused every step
+    k_h, p_h, h_h, _ = eng.walkers(out=bufs)
     h2d = d2h = 0
     att_e2e = 0.0
     t0 = time.perf_counter()
@@ -254,7 +256,7 @@ def run_ours(args, rank, world):
         eng.set_walkers(k_h, p_h, h_h)
         h2d += k_h.nbytes + p_h.nbytes + h_h.nbytes
         eng.iterate(1)
-        k_h, p_h, h_h, f_h = eng.walkers()
+        k_h, p_h, h_h, f_h = eng.walkers(out=bufs)
         r = eng.estimators()
         d2h += k_h.nbytes + p_h.nbytes + h_h.nbytes + f_h.nbytes + 88 * len(r["iter"])
         att_e2e += float(r["natt"].sum())

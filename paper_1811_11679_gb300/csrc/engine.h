@@ -22,6 +22,9 @@ struct Ops {
   void (*csr_fill)(Engine& E, cudaStream_t s);
   void (*sel_gather)(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s);
   void (*core_hash)(Engine& E, uint32_t* table, cudaStream_t s);
+  void (*check_keys)(Engine& E, const uint64_t* aos, int64_t n, unsigned* out, cudaStream_t s);
+  void (*keys_to_soa)(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, cudaStream_t s);
+  void (*keys_to_aos)(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, cudaStream_t s);
   void (*sel_hist)(Engine& E, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist,
                    cudaStream_t s);
   void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);
@@ -68,6 +71,7 @@ struct Engine {
   double* core_val = nullptr;
   int64_t nnz_cap = 0, ncore_cap = 0;
   uint32_t* core_table = nullptr;   // core membership hash table
+  unsigned* check_word = nullptr;   // result word of the walker-list checks
   int64_t core_table_cap = 0;
   double e_ref = 0.0;
   bool failed = false;

@@ -692,6 +692,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     }
     P.split_key = dalloc<uint64_t>(E, (size_t)cap * E.W);
     P.st = dalloc<DevState>(E, 1);
+    E.check_word = dalloc<unsigned>(E, 4);
     P.rec = dalloc<Record>(E, P.rec_cap);
     P.ncore = 0;
 
@@ -879,16 +880,16 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
     if (nd == 0) return HANDE_OK;
     if (!keys || !pops) return HANDE_ERR_INVALID;
     const int W = E.W;
-    std::vector<uint64_t> soa((size_t)nd * W);
-    for (int j = 0; j < W; ++j)
-      CK(cudaMemcpyAsync(soa.data() + (size_t)j * nd, E.P.key[cur] + (size_t)j * E.P.cap, nd * 8,
-                         cudaMemcpyDeviceToHost, E.stream));
+    // keys transposed on the device into the other list buffer (free between
+    // iterations), then one copy
+    uint64_t* stage = E.P.key[cur ^ 1];
+    E.ops.keys_to_aos(E, E.P.key[cur], stage, nd, E.stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(keys, stage, (size_t)nd * W * 8, cudaMemcpyDeviceToHost, E.stream));
     CK(cudaMemcpyAsync(pops, E.P.pop[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
     if (hdiag) CK(cudaMemcpyAsync(hdiag, E.P.hdiag[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
     if (flags) CK(cudaMemcpyAsync(flags, E.P.flags[cur], nd, cudaMemcpyDeviceToHost, E.stream));
     CK(cudaStreamSynchronize(E.stream));
-    for (int64_t i = 0; i < nd; ++i)
-      for (int j = 0; j < W; ++j) keys[i * W + j] = soa[(size_t)j * nd + i];
     if (flags)
       for (int64_t i = 0; i < nd; ++i) flags[i] &= F_CORE;
     return HANDE_OK;
@@ -903,39 +904,22 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
   return run_guarded(&E, [&]() -> hande_status {
     const int W = E.W;
     if (n > E.P.cap) throw Fail{HANDE_ERR_CAPACITY, "more walkers than state_capacity"};
-    bool has_ref = false;
-    const int nspin = E.P.sys.nspin;
-    for (int64_t i = 0; i < n; ++i) {
-      int na = 0, nb = 0;
-      for (int j = 0; j < W; ++j) {
-        uint64_t w = keys[i * W + j];
-        int lo = 64 * j;
-        if (nspin - lo < 64 && (nspin - lo <= 0 ? w != 0 : (w >> (nspin - lo)) != 0))
-          throw Fail{HANDE_ERR_INVALID, "a key has bits beyond the spin orbitals"};
-        na += __builtin_popcountll(w & 0x5555555555555555ull);
-        nb += __builtin_popcountll(w & 0xAAAAAAAAAAAAAAAAull);
-      }
-      if (na != E.nalpha || nb != E.nbeta) throw Fail{HANDE_ERR_INVALID, "a key has the wrong electron numbers"};
-      bool eq = true;
-      for (int j = 0; j < W; ++j) eq &= keys[i * W + j] == E.P.d0[j];
-      has_ref |= eq;
-      if (i > 0) {
-        int c = 0;
-        for (int j = W - 1; j >= 0 && c == 0; --j) {
-          uint64_t a = keys[(i - 1) * W + j], b = keys[i * W + j];
-          c = a < b ? -1 : (a > b ? 1 : 0);
-        }
-        if (c >= 0) throw Fail{HANDE_ERR_INVALID, "keys must be strictly ascending"};
-      }
-    }
-    if (!has_ref) throw Fail{HANDE_ERR_INVALID, "the reference determinant must be in the list"};
+    // the keys go to the other list buffer (free between iterations), are
+    // checked there and transposed into the list's layout
     const int cur = E.cur;
-    std::vector<uint64_t> soa((size_t)n * W);
-    for (int64_t i = 0; i < n; ++i)
-      for (int j = 0; j < W; ++j) soa[(size_t)j * n + i] = keys[i * W + j];
-    for (int j = 0; j < W; ++j)
-      CK(cudaMemcpyAsync(E.P.key[cur] + (size_t)j * E.P.cap, soa.data() + (size_t)j * n, n * 8,
-                         cudaMemcpyHostToDevice, E.stream));
+    uint64_t* stage = E.P.key[cur ^ 1];
+    CK(cudaMemcpyAsync(stage, keys, (size_t)n * W * 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemsetAsync(E.check_word, 0, sizeof(unsigned), E.stream));
+    E.ops.check_keys(E, stage, n, E.check_word, E.stream);
+    CK(cudaGetLastError());
+    unsigned bits = 0;
+    CK(cudaMemcpyAsync(&bits, E.check_word, sizeof bits, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    if (bits & 1u) throw Fail{HANDE_ERR_INVALID, "a key has bits beyond the spin orbitals"};
+    if (bits & 2u) throw Fail{HANDE_ERR_INVALID, "a key has the wrong electron numbers"};
+    if (bits & 4u) throw Fail{HANDE_ERR_INVALID, "keys must be strictly ascending"};
+    if (!(bits & 8u)) throw Fail{HANDE_ERR_INVALID, "the reference determinant must be in the list"};
+    E.ops.keys_to_soa(E, stage, E.P.key[cur], n, E.stream);
     CK(cudaMemcpyAsync(E.P.pop[cur], pops, n * 8, cudaMemcpyHostToDevice, E.stream));
     CK(cudaMemsetAsync(E.P.flags[cur], 0, n, E.stream));
     CK(cudaMemcpyAsync((char*)E.P.st + offsetof(DevState, ndet) + 8 * cur, &n, 8, cudaMemcpyHostToDevice, E.stream));

@@ -234,6 +234,67 @@ void enqueue_sel_gather(Engine& E, int cur, uint64_t* core_key, int64_t ncore, c
   k_sel_gather<W><<<4 * 152, 256, 0, s>>>(E.P, cur, core_key, ncore);
 }
 
+// ------------------------------------------------------------------ walker-list transfer
+// keys of a host-supplied list (array of structures, word j of key i at i W + j):
+// bit 0 a bit beyond the spin orbitals, bit 1 wrong electron numbers, bit 2 not
+// strictly ascending, bit 3 the reference present
+template <int W>
+__global__ void k_check_keys(const uint64_t* aos, int64_t n, int nspin, int nalpha, int nbeta, Key<W> d0,
+                             unsigned* out) {
+  unsigned bits = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    Key<W> k;
+    int na = 0, nb = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      k.w[j] = aos[i * W + j];
+      const int lo = 64 * j;
+      if (nspin - lo < 64 && (nspin - lo <= 0 ? k.w[j] != 0 : (k.w[j] >> (nspin - lo)) != 0)) bits |= 1u;
+      na += __popcll(k.w[j] & 0x5555555555555555ull);
+      nb += __popcll(k.w[j] & 0xAAAAAAAAAAAAAAAAull);
+    }
+    if (na != nalpha || nb != nbeta) bits |= 2u;
+    if (key_eq<W>(k, d0)) bits |= 8u;
+    if (i > 0) {
+      Key<W> pk;
+#pragma unroll
+      for (int j = 0; j < W; ++j) pk.w[j] = aos[(i - 1) * W + j];
+      if (!key_lt<W>(pk, k)) bits |= 4u;
+    }
+  }
+  if (bits) atomicOr(out, bits);
+}
+// array of structures <-> the list's structure of arrays (key word j at j cap + i)
+template <int W>
+__global__ void k_keys_to_soa(const uint64_t* aos, uint64_t* soa, int64_t n, int64_t cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) soa[(size_t)j * cap + i] = aos[i * W + j];
+  }
+}
+template <int W>
+__global__ void k_keys_to_aos(const uint64_t* soa, uint64_t* aos, int64_t n, int64_t cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) aos[i * W + j] = soa[(size_t)j * cap + i];
+  }
+}
+template <int W>
+void enqueue_check_keys(Engine& E, const uint64_t* aos, int64_t n, unsigned* out, cudaStream_t s) {
+  Key<W> d0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) d0.w[j] = E.P.d0[j];
+  k_check_keys<W><<<4 * 152, 256, 0, s>>>(aos, n, E.P.sys.nspin, E.nalpha, E.nbeta, d0, out);
+}
+template <int W>
+void enqueue_keys_to_soa(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, cudaStream_t s) {
+  k_keys_to_soa<W><<<4 * 152, 256, 0, s>>>(aos, soa, n, E.P.cap);
+}
+template <int W>
+void enqueue_keys_to_aos(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, cudaStream_t s) {
+  k_keys_to_aos<W><<<4 * 152, 256, 0, s>>>(soa, aos, n, E.P.cap);
+}
+
 template <int W>
 size_t merge_smem_w(int tc, int sm) {
   return merge_smem_bytes<W>(tc, sm);
@@ -248,6 +309,9 @@ Ops make_ops() {
   o.csr_count = &enqueue_csr_count<W, SYS>;
   o.csr_fill = &enqueue_csr_fill<W, SYS>;
   o.sel_gather = &enqueue_sel_gather<W>;
+  o.check_keys = &enqueue_check_keys<W>;
+  o.keys_to_soa = &enqueue_keys_to_soa<W>;
+  o.keys_to_aos = &enqueue_keys_to_aos<W>;
   o.core_hash = &enqueue_core_hash<W>;
   o.sel_hist = &enqueue_sel_hist<W>;
   o.sel_flags = &enqueue_sel_flags<W>;

@@ -23,6 +23,16 @@ STATUS = {0: "HANDE_OK", -1: "HANDE_ERR_INVALID", -2: "HANDE_ERR_NOMEM", -3: "HA
           -4: "HANDE_ERR_OVERFLOW", -5: "HANDE_ERR_CUDA", -6: "HANDE_ERR_TIMEOUT", -7: "HANDE_ERR_STATE"}
 
 
+def _pinned_array(shape, dtype):
+    """A numpy array over page-locked host memory (allocated through PyTorch)."""
+    import torch
+    dt = np.dtype(dtype)
+    count = int(np.prod(shape))
+    buf = torch.empty(max(count * dt.itemsize, 1), dtype=torch.uint8, pin_memory=True)
+    arr = buf.numpy()[:count * dt.itemsize].view(dt).reshape(shape)
+    return arr
+
+
 class HandeError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS.get(status, status)}: {message}")
@@ -250,16 +260,30 @@ class Hande:
         arr = np.ctypeslib.as_array(buf)[: n.value]
         return {name: np.array(arr[name]) for name, _ in _Estimate._fields_}
 
-    def walkers(self):
+    def host_buffers(self, capacity: int, pinned: bool = True):
+        """Host arrays (keys, populations, H_ii - E_ref, flags) for `capacity`
+        determinants, page-locked by default, for reuse with walkers(out=...)."""
+        alloc = _pinned_array if pinned else (lambda shape, dt: np.zeros(shape, dtype=dt))
+        return (alloc((capacity, self.W), np.uint64), alloc((capacity,), np.int64),
+                alloc((capacity,), np.float64), alloc((capacity,), np.uint8))
+
+    def walkers(self, out=None):
+        """The walker list (keys, populations, H_ii - E_ref, core flags) in host
+        memory: new arrays, or views of the given host_buffers(...) when they are
+        large enough (page-locked buffers make the copies direct DMA)."""
         n = C.c_int64()
         rc = self._lib.hande_get_walkers(self._h, None, None, None, None, 0, C.byref(n))
         if rc not in (0, -3):
             self._check(rc, "hande_get_walkers")
         cap = n.value
-        keys = np.zeros((cap, self.W), dtype=np.uint64)
-        pops = np.zeros(cap, dtype=np.int64)
-        hd = np.zeros(cap, dtype=np.float64)
-        fl = np.zeros(cap, dtype=np.uint8)
+        if out is not None and len(out[1]) >= cap:
+            keys, pops, hd, fl = out
+            cap = len(pops)
+        else:
+            keys = np.zeros((cap, self.W), dtype=np.uint64)
+            pops = np.zeros(cap, dtype=np.int64)
+            hd = np.zeros(cap, dtype=np.float64)
+            fl = np.zeros(cap, dtype=np.uint8)
         self._check(self._lib.hande_get_walkers(self._h, keys.ctypes.data_as(C.POINTER(C.c_uint64)),
                                                 pops.ctypes.data_as(C.POINTER(C.c_int64)),
                                                 hd.ctypes.data_as(C.POINTER(C.c_double)),
