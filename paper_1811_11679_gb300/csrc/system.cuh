@@ -162,11 +162,31 @@ __device__ double h_single(const SysDev& s, const Key<W>& d, int i, int a) {
   } else if (SYS == SYS_UEG) {
     return 0.0;
   } else {
+    // sum over occupied k != i in ascending order; the row entries are loaded
+    // four at a time ahead of the (ordered) additions
     double acc = 0.0;
     const double* row = s.single_g + ((size_t)i * s.nspin + a) * s.nspin;
-    HANDE_FOR_OCC(W, d, k, {
-      if (k != i) acc = __dadd_rn(acc, __ldg(&row[k]));
-    })
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      uint64_t m = d.w[j];
+      if ((i >> 6) == j) m &= ~(1ull << (i & 63));
+      while (m) {
+        double v4[4];
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (m) {
+            const int k = j * 64 + __ffsll((long long)m) - 1;
+            m &= m - 1;
+            v4[u] = __ldg(&row[k]);
+            cnt = u + 1;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < cnt) acc = __dadd_rn(acc, v4[u]);
+      }
+    }
     v = __dadd_rn(h1_so(s, i, a), acc);
   }
   return (key_between<W>(d, i, a) & 1) ? -v : v;
