@@ -10,14 +10,15 @@
 namespace hande {
 
 // ------------------------------------------------------------------ CSR of H' inside the core
-// H'_rc = <D_r|H|D_c> off the diagonal, H_rr - E_ref on it; zero elements omitted.
+// H'_rc = <D_r|H|D_c> off the diagonal, H_rr - E_ref on it, for every pair that
+// differs in at most two spin orbitals (an element that is exactly zero is kept:
+// it adds nothing to the exact product).
 template <int W, int SYS>
 __device__ __forceinline__ double core_elem(const Params& P, int r, int c, const Key<W>& kr, const Key<W>& kc) {
-  if (key_popc_xor<W>(kr, kc) > 4) return 0.0;
   if (r == c) return __dsub_rn(h_diag<W, SYS>(P.sys, kr), P.st->e_ref);
   return h_elem<W, SYS>(P.sys, kc, kr);
 }
-template <int W, int SYS>
+template <int W>
 __global__ void k_csr_count(Params P, int32_t* rowcnt) {
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
@@ -27,10 +28,7 @@ __global__ void k_csr_count(Params P, int32_t* rowcnt) {
   for (int c0 = 0; c0 < P.ncore; c0 += 32) {
     int c = c0 + lane;
     bool nz = false;
-    if (c < P.ncore) {
-      Key<W> kc = load_key<W>(P.core_key, P.ncore, c);
-      nz = core_elem<W, SYS>(P, r, c, kr, kc) != 0.0;
-    }
+    if (c < P.ncore) nz = key_popc_xor<W>(kr, load_key<W>(P.core_key, P.ncore, c)) <= 4;
     cnt += __popc(__ballot_sync(0xffffffffu, nz));
   }
   if (lane == 0) rowcnt[r] = cnt;
@@ -44,18 +42,19 @@ __global__ void k_csr_fill(Params P, int64_t* rowptr, int32_t* col, double* val)
   int64_t o = rowptr[r];
   for (int c0 = 0; c0 < P.ncore; c0 += 32) {
     int c = c0 + lane;
-    double h = 0.0;
+    bool conn = false;
+    Key<W> kc;
     if (c < P.ncore) {
-      Key<W> kc = load_key<W>(P.core_key, P.ncore, c);
-      h = core_elem<W, SYS>(P, r, c, kr, kc);
+      kc = load_key<W>(P.core_key, P.ncore, c);
+      conn = key_popc_xor<W>(kr, kc) <= 4;
     }
-    unsigned nzm = __ballot_sync(0xffffffffu, h != 0.0);
-    if (h != 0.0) {
-      int64_t e = o + __popc(nzm & ((1u << lane) - 1u));
+    unsigned m = __ballot_sync(0xffffffffu, conn);
+    if (conn) {
+      int64_t e = o + __popc(m & ((1u << lane) - 1u));
       col[e] = c;
-      val[e] = h;
+      val[e] = core_elem<W, SYS>(P, r, c, kr, kc);
     }
-    o += __popc(nzm);
+    o += __popc(m);
   }
 }
 // ------------------------------------------------------------------ selection of the core
@@ -209,7 +208,7 @@ void enqueue_eref(Engine& E, cudaStream_t s) {
 template <int W, int SYS>
 void enqueue_csr_count(Engine& E, int32_t* rowcnt, cudaStream_t s) {
   int blocks = (int)(((int64_t)E.P.ncore * 32 + 255) / 256);
-  k_csr_count<W, SYS><<<blocks, 256, 0, s>>>(E.P, rowcnt);
+  k_csr_count<W><<<blocks, 256, 0, s>>>(E.P, rowcnt);
 }
 template <int W, int SYS>
 void enqueue_csr_fill(Engine& E, cudaStream_t s) {
