@@ -164,7 +164,7 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   k_scan_one<uint32_t, uint32_t><<<1, 1024, 0, s>>>(P.bcount, P.boff, nbk,
                                                     st_field_i64(st, offsetof(DevState, scan_total)), -1, st);
   mark(6);
-  k_scatter<W><<<E.attempt_grid, 256, 0, s>>>(P);
+  k_scatter<W><<<E.attempt_grid * 4, 256, 0, s>>>(P);
   mark(7);
   if (E.merge_warp) {
     if (!ev && E.aux_stream) {   // large buckets on block tiles beside the warp kernel
