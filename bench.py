@@ -149,8 +149,8 @@ def _phase_bytes(rec, W):
 # kernel on the profile case (profiles/kernels_molecule28_profile_case.md);
 # the peak is 4 warp instructions per cycle per SM (one per sub-partition) on
 # 152 SMs at the maximum SM clock.
-ATTEMPT_INST_PER_ATTEMPT = 241611507 / 7571203
-ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.547520e6 + 7.121152e6) / 7571203
+ATTEMPT_INST_PER_ATTEMPT = 246563229 / 7571203
+ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.644800e6 + 7.361024e6) / 7571203
 N_SM = 152
 
 
