@@ -366,6 +366,68 @@ def run_profile_case(args):
     eng.close()
 
 
+def run_batched(args):
+    """Batched replicas (inputs.batched_replicas: UEG 14e in 38/66 orbitals, four
+    r_s, targets log-uniform in [1e4, 1e6]) advanced together through
+    hande_batch_iterate, against the same replicas advanced one after another
+    (each run alone on the GPU, as separate plain runs would be)."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande, inputs
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    systems, qmcs = inputs.batched_replicas(args.batched)
+    b = hande.HandeBatch(systems, qmcs)
+    t_grow = time.perf_counter()
+    _grow(b.iterate, lambda: b.replicas[0].iterations(), args.batched_grow)
+    b.iterate(args.warmup)
+    b.synchronize()
+    t_grow = time.perf_counter() - t_grow
+    for v in b.replicas:
+        v.estimators()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        w0 = time.perf_counter()
+        e0.record(stream)
+        b.iterate(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    ms = e0.elapsed_time(e1)
+    recs = [v.estimators() for v in b.replicas]
+    attempts = float(sum(r["natt"].sum() for r in recs))
+    walkers = float(sum(r["nw_post"].mean() for r in recs)) / 2 ** 32
+    dets = float(sum(r["ndet"].mean() for r in recs))
+    # the same replicas one at a time: each replica's steps, then the next one
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    for v in b.replicas:
+        v.iterate(args.steps)
+        v.synchronize()
+    seq_wall = time.perf_counter() - s0
+    seq_attempts = float(sum(v.estimators()["natt"].sum() for v in b.replicas))
+    launches = sum(v.launches_per_iteration() for v in b.replicas) * args.steps
+    b.close()
+    return {"metric": "FCIQMC spawn attempts/s, batched replicas", "value": attempts / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.batched} UEG replicas: 14 electrons in 38 or 66 spatial orbitals "
+                                   "(128- or 512-bit keys), r_s 0.5/1/2/5, targets log-uniform in [1e4, 1e6], "
+                                   "initiator, real weights, tau=0.002",
+                       "replicas": args.batched, "grow_iterations": args.batched_grow,
+                       "grow_seconds": round(t_grow, 2), "mean_walkers_total": walkers,
+                       "mean_determinants_total": dets, "l2": "inputs larger than L2 (no flush)"},
+            "wall_value": attempts / wall,
+            "sequential": {"value": seq_attempts / seq_wall, "unit": UNIT,
+                           "ms_per_step": seq_wall * 1e3 / args.steps,
+                           "how": "each replica iterated alone for the same steps, then synchronised, "
+                                  "one replica after another (host wall clock)"},
+            "gpu_launches": launches, "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,12 +437,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="small synthetic-start case for ncu captures (no timing output)")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="time this many batched UEG replicas instead of the molecule workload")
+    ap.add_argument("--batched-grow", type=int, default=600,
+                    help="iterations before the timed region in --batched mode")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.batched > 0:
+        print(json.dumps(run_batched(args)), flush=True)
         return
     if args.impl == "reference":
         if rank == 0:

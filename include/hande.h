@@ -236,6 +236,49 @@ void hande_destroy(hande_ctx* ctx);
 /* Last error message of the context ("" if none); static text for NULL. */
 const char* hande_last_error(const hande_ctx* ctx);
 
+/* ---------------------------------------------------------------- batches
+ * Independent replicas advanced together.  The paper runs one calculation at a
+ * time (its statistical analysis of several runs, section 3, combines runs
+ * made one after another); a batch advances many of them on one GPU.  Replica r
+ * is exactly the run hande_init_system(&sys[r], &qmc[r], ...) would make: its
+ * walker lists and estimator records are bit-identical, so distinct seeds (or
+ * distinct qmc.replica words) give independent Markov chains.
+ *
+ * Each replica owns a non-blocking CUDA stream created by the batch.  A batch
+ * iteration is stream-ordered with respect to `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream): every replica stream waits for the work
+ * already queued on it, one CUDA-graph launch per replica follows, and
+ * `cuda_stream` then waits for all replicas.  Small replicas thereby run
+ * concurrently on the GPU. */
+typedef struct hande_batch hande_batch;
+
+/* Build n >= 1 replicas from the caller-owned arrays sys[n] and qmc[n]
+ * (copied).  `allocator` may be NULL and serves every replica.  On failure
+ * nothing is left allocated and, if err_replica is not NULL, *err_replica is
+ * the index of the replica that failed (-1 for a failure of the batch itself). */
+hande_status hande_batch_init(const hande_system* sys, const hande_qmc* qmc, int n, const hande_allocator* allocator,
+                              void* cuda_stream, hande_batch** out, int* err_replica);
+
+/* Advance every replica by n_iterations >= 0 iterations (asynchronous, iteration
+ * by iteration across the replicas).  On a replica error the remaining launches
+ * are skipped, `cuda_stream` still waits for what was launched, and the error of
+ * the first failing replica is returned (its context holds the message). */
+hande_status hande_batch_iterate(hande_batch* b, int n_iterations);
+
+/* Number of replicas (0 for NULL). */
+int hande_batch_size(const hande_batch* b);
+
+/* Context of replica r, owned by the batch (NULL when r is out of range).  All
+ * single-context calls apply to it; hande_iterate on it advances that replica
+ * alone, on its own stream. */
+hande_ctx* hande_batch_replica(hande_batch* b, int r);
+
+/* Synchronise every replica and report the first latched device error. */
+hande_status hande_batch_synchronize(hande_batch* b);
+
+/* Free all replicas, their streams and the batch (safe on NULL). */
+void hande_batch_destroy(hande_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,7 +79,9 @@ class _Diag(C.Structure):
 
 # names declared in include/hande.h, in order
 EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
-           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error"]
+           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
+           "hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize",
+           "hande_batch_destroy"]
 
 _lib = None
 _lock = threading.Lock()
@@ -122,6 +124,17 @@ def load(build_if_needed: bool = True):
         lib.hande_estimate_noalloc.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
         for name in EXPORTS[:10]:
             getattr(lib, name).restype = C.c_int
+        lib.hande_batch_init.argtypes = [C.POINTER(_System), C.POINTER(_Qmc), C.c_int, C.POINTER(_Allocator), P,
+                                         C.POINTER(P), C.POINTER(C.c_int)]
+        lib.hande_batch_iterate.argtypes = [P, C.c_int]
+        lib.hande_batch_size.argtypes = [P]
+        lib.hande_batch_replica.argtypes = [P, C.c_int]
+        lib.hande_batch_replica.restype = P
+        lib.hande_batch_synchronize.argtypes = [P]
+        lib.hande_batch_destroy.argtypes = [P]
+        lib.hande_batch_destroy.restype = None
+        for name in ("hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_synchronize"):
+            getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
 
@@ -143,6 +156,64 @@ def _torch_allocator(device):
     return _ALLOC_FN(alloc), _FREE_FN(free)
 
 
+def _structs(system: dict, qmc: dict):
+    """The C structs of one run (and the arrays they point into, to keep alive)."""
+    s = _System()
+    s.kind = _KIND[system["kind"]]
+    s.key_words = int(system["key_words"])
+    s.norb = int(system["norb"])
+    s.nalpha = int(system["nalpha"])
+    s.nbeta = int(system["nbeta"])
+    s.periodic = int(system.get("periodic", 0))
+    s.t = float(system.get("t", 0.0))
+    s.U = float(system.get("U", 0.0))
+    s.rs = float(system.get("rs", 0.0))
+    s.ecore = float(system.get("ecore", 0.0))
+    keep = []
+    if s.kind == 2:
+        h1 = np.ascontiguousarray(system["h1"], dtype=np.float64)
+        eri = np.ascontiguousarray(system["eri"], dtype=np.float64)
+        keep += [h1, eri]
+        s.h1 = h1.ctypes.data_as(C.POINTER(C.c_double))
+        s.eri = eri.ctypes.data_as(C.POINTER(C.c_double))
+    q = _Qmc()
+    q.tau = float(qmc["tau"])
+    q.target_population = float(qmc["target_population"])
+    q.shift_damping = float(qmc.get("shift_damping", 0.05))
+    q.spawn_cutoff = float(qmc.get("spawn_cutoff", 0.0))
+    q.init_pop = float(qmc["init_pop"])
+    q.initiator_threshold = float(qmc.get("initiator_threshold", 3.0))
+    q.p_single = float(qmc.get("p_single", 0.1))
+    q.shift_period = int(qmc.get("shift_period", 1))
+    q.initiator = int(qmc.get("initiator", 0))
+    q.real_amplitudes = int(qmc.get("real_amplitudes", 0))
+    q.semi_stoch_size = int(qmc.get("semi_stoch_size", 0))
+    q.semi_stoch_start = int(qmc.get("semi_stoch_start", 0))
+    q.seed = int(qmc["seed"])
+    q.replica = int(qmc.get("replica", 0))
+    q.state_capacity = int(qmc.get("state_capacity", 0))
+    q.spawn_capacity = int(qmc.get("spawn_capacity", 0))
+    q.record_capacity = int(qmc.get("record_capacity", 0))
+    q.tile_capacity = int(qmc.get("tile_capacity", 0))
+    q.annihilation = int(qmc.get("annihilation", 0))
+    return s, q, keep
+
+
+def _stream_and_allocator(stream, torch_memory):
+    """The CUDA stream handle (PyTorch's current stream by default) and the
+    allocator struct routing device memory through PyTorch (or None)."""
+    alloc, fns = None, None
+    if stream is None or torch_memory:
+        import torch
+        dev = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        if torch_memory:
+            fns = _torch_allocator(dev)
+            alloc = _Allocator(fns[0], fns[1], None)
+    return int(stream), alloc, fns
+
+
 class Hande:
     """One FCIQMC run on the current CUDA device (see include/hande.h)."""
 
@@ -150,57 +221,11 @@ class Hande:
         lib = load()
         self._lib = lib
         self._h = C.c_void_p()
-        s = _System()
-        s.kind = _KIND[system["kind"]]
-        s.key_words = int(system["key_words"])
-        s.norb = int(system["norb"])
-        s.nalpha = int(system["nalpha"])
-        s.nbeta = int(system["nbeta"])
-        s.periodic = int(system.get("periodic", 0))
-        s.t = float(system.get("t", 0.0))
-        s.U = float(system.get("U", 0.0))
-        s.rs = float(system.get("rs", 0.0))
-        s.ecore = float(system.get("ecore", 0.0))
-        self._keep = []
-        if s.kind == 2:
-            h1 = np.ascontiguousarray(system["h1"], dtype=np.float64)
-            eri = np.ascontiguousarray(system["eri"], dtype=np.float64)
-            self._keep += [h1, eri]
-            s.h1 = h1.ctypes.data_as(C.POINTER(C.c_double))
-            s.eri = eri.ctypes.data_as(C.POINTER(C.c_double))
-        q = _Qmc()
-        q.tau = float(qmc["tau"])
-        q.target_population = float(qmc["target_population"])
-        q.shift_damping = float(qmc.get("shift_damping", 0.05))
-        q.spawn_cutoff = float(qmc.get("spawn_cutoff", 0.0))
-        q.init_pop = float(qmc["init_pop"])
-        q.initiator_threshold = float(qmc.get("initiator_threshold", 3.0))
-        q.p_single = float(qmc.get("p_single", 0.1))
-        q.shift_period = int(qmc.get("shift_period", 1))
-        q.initiator = int(qmc.get("initiator", 0))
-        q.real_amplitudes = int(qmc.get("real_amplitudes", 0))
-        q.semi_stoch_size = int(qmc.get("semi_stoch_size", 0))
-        q.semi_stoch_start = int(qmc.get("semi_stoch_start", 0))
-        q.seed = int(qmc["seed"])
-        q.replica = int(qmc.get("replica", 0))
-        q.state_capacity = int(qmc.get("state_capacity", 0))
-        q.spawn_capacity = int(qmc.get("spawn_capacity", 0))
-        q.record_capacity = int(qmc.get("record_capacity", 0))
-        q.tile_capacity = int(qmc.get("tile_capacity", 0))
-        q.annihilation = int(qmc.get("annihilation", 0))
+        self._batch = None
+        s, q, self._keep = _structs(system, qmc)
         self.W = s.key_words
-        alloc_p = None
-        if stream is None or torch_memory:
-            import torch
-            dev = torch.cuda.current_device()
-            if stream is None:
-                stream = torch.cuda.current_stream(dev).cuda_stream
-            if torch_memory:
-                fa, ff = _torch_allocator(dev)
-                self._alloc = _Allocator(fa, ff, None)
-                self._alloc_fns = (fa, ff)
-                alloc_p = C.byref(self._alloc)
-        self.stream = int(stream)
+        self.stream, self._alloc, self._alloc_fns = _stream_and_allocator(stream, torch_memory)
+        alloc_p = C.byref(self._alloc) if self._alloc is not None else None
         rc = lib.hande_init_system(C.byref(s), C.byref(q), alloc_p, C.c_void_p(self.stream), C.byref(self._h))
         if rc != 0:
             raise HandeError(rc, "hande_init_system failed")
@@ -305,8 +330,76 @@ class Hande:
                     "hande_set_walkers")
 
     def close(self) -> None:
-        if self._h:
+        if self._h and self._batch is None:   # a batch's replica is freed with its batch
             self._lib.hande_destroy(self._h)
+        self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class HandeBatch:
+    """Independent replicas advanced together on the current CUDA device
+    (include/hande.h, batches).  `replicas[r]` is a Hande view of replica r
+    (owned by the batch): walkers, estimators and diagnostics as for one run."""
+
+    def __init__(self, systems, qmcs, stream: int | None = None, torch_memory: bool = True):
+        systems, qmcs = list(systems), list(qmcs)
+        if len(systems) != len(qmcs) or not systems:
+            raise ValueError("one system and one qmc dict per replica")
+        lib = load()
+        self._lib = lib
+        self._h = C.c_void_p()
+        n = len(systems)
+        S, Q, self._keep = (_System * n)(), (_Qmc * n)(), []
+        for r in range(n):
+            s, q, keep = _structs(systems[r], qmcs[r])
+            S[r], Q[r] = s, q
+            self._keep += keep
+        self.stream, self._alloc, self._alloc_fns = _stream_and_allocator(stream, torch_memory)
+        alloc_p = C.byref(self._alloc) if self._alloc is not None else None
+        bad = C.c_int(-1)
+        rc = lib.hande_batch_init(S, Q, n, alloc_p, C.c_void_p(self.stream), C.byref(self._h), C.byref(bad))
+        if rc != 0:
+            raise HandeError(rc, f"hande_batch_init failed (replica {bad.value})")
+        self.replicas = []
+        for r in range(n):
+            v = object.__new__(Hande)
+            v._lib, v._batch, v._keep = lib, self, []
+            v._h = C.c_void_p(lib.hande_batch_replica(self._h, r))
+            v.W = int(systems[r]["key_words"])
+            v.stream, v._alloc, v._alloc_fns = None, None, None
+            self.replicas.append(v)
+
+    def __len__(self) -> int:
+        return int(self._lib.hande_batch_size(self._h))
+
+    def iterate(self, n: int = 1) -> None:
+        rc = self._lib.hande_batch_iterate(self._h, int(n))
+        if rc != 0:
+            msgs = [f"replica {r}: {v._lib.hande_last_error(v._h).decode()}"
+                    for r, v in enumerate(self.replicas) if v._lib.hande_last_error(v._h)]
+            raise HandeError(rc, "hande_batch_iterate: " + "; ".join(msgs))
+
+    def synchronize(self) -> None:
+        rc = self._lib.hande_batch_synchronize(self._h)
+        if rc != 0:
+            raise HandeError(rc, "hande_batch_synchronize")
+
+    def close(self) -> None:
+        if self._h:
+            for v in self.replicas:
+                v._h = C.c_void_p()
+            self._lib.hande_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

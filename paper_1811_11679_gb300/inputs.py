@@ -107,6 +107,29 @@ WORKLOADS = {
 }
 
 
+def batched_replicas(n: int = 256, seed: int = 13):
+    """(systems, qmcs) of n independent replicas: UEG 14 electrons in 38 or 66
+    spatial orbitals (128- or 512-bit keys), r_s in {0.5, 1, 2, 5}, 32 seeds per
+    (basis, r_s) pair for n = 256, cycled for other n; initiator real-weight
+    FCIQMC at tau = 0.002; target populations log-uniform in [1e4, 1e6] drawn
+    from numpy's Philox generator with the given seed.  Each replica starts
+    with half its target on the reference determinant, so the population
+    reaches the target within a few hundred iterations."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    targets = np.exp(rng.uniform(np.log(1e4), np.log(1e6), n))
+    systems, qmcs = [], []
+    for r in range(n):
+        norb = (38, 66)[r % 2]
+        rs = (0.5, 1.0, 2.0, 5.0)[(r // 2) % 4]
+        tgt = float(targets[r])
+        systems.append(ueg_system(14, norb, rs))
+        qmcs.append(qmc_params(tau=0.002, target_population=tgt, initiator=1, real_amplitudes=1,
+                               spawn_cutoff=0.1, init_pop=0.5 * tgt, seed=100 + r // 8, replica=r,
+                               state_capacity=int(1.5 * tgt) + (1 << 16),
+                               spawn_capacity=int(3 * tgt) + (1 << 17)))
+    return systems, qmcs
+
+
 def workload(name: str, **overrides):
     """(system, qmc) dicts for a named workload, qmc keys overridable."""
     sysf, qf = WORKLOADS[name]

@@ -57,3 +57,18 @@ def test_python_binding_has_no_cpu_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(hande._build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         hande.load(build_if_needed=False)
+
+
+def test_batch_arguments_rejected_before_any_device_call():
+    lib = hande.load()
+    out = C.c_void_p()
+    bad = C.c_int(7)
+    s, q = hande._System(), hande._Qmc()
+    assert lib.hande_batch_init(None, None, 1, None, None, C.byref(out), C.byref(bad)) == -1
+    assert bad.value == -1
+    assert lib.hande_batch_init(C.byref(s), C.byref(q), 0, None, None, C.byref(out), None) == -1
+    assert lib.hande_batch_iterate(None, 1) == -1
+    assert lib.hande_batch_synchronize(None) == -1
+    assert lib.hande_batch_size(None) == 0
+    assert lib.hande_batch_replica(None, 0) is None
+    lib.hande_batch_destroy(None)

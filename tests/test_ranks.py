@@ -49,3 +49,20 @@ def test_replicas_are_independent_and_reproducible():
     for x, y in zip(runs["b"], runs["c"]):
         assert np.array_equal(x, y)
     assert not all(np.array_equal(x, y) for x, y in zip(runs["a"], runs["b"]))
+
+
+def test_batched_replica_recipe():
+    """256 replicas: 2 bases x 4 r_s x 32 seeds, distinct Philox keys, targets in [1e4, 1e6]."""
+    systems, qmcs = inputs.batched_replicas(256)
+    assert len(systems) == len(qmcs) == 256
+    combos = {}
+    for s, q in zip(systems, qmcs):
+        combos.setdefault((s["norb"], s["rs"]), []).append(q["seed"])
+        assert s["key_words"] == (2 if s["norb"] == 38 else 8)
+        assert 1e4 <= q["target_population"] <= 1e6
+        assert q["state_capacity"] > 1.5 * q["target_population"]
+    assert sorted(combos) == [(n, r) for n in (38, 66) for r in (0.5, 1.0, 2.0, 5.0)]
+    assert all(sorted(v) == list(range(100, 132)) for v in combos.values())
+    assert len({(q["seed"], q["replica"]) for q in qmcs}) == 256
+    t = np.log10([q["target_population"] for q in qmcs])
+    assert 4.8 < t.mean() < 5.2
