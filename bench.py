@@ -379,7 +379,7 @@ def run_batched(args):
     systems, qmcs = inputs.batched_replicas(args.batched)
     b = hande.HandeBatch(systems, qmcs)
     t_grow = time.perf_counter()
-    _grow(b.iterate, lambda: b.replicas[0].iterations(), args.batched_grow)
+    _grow(b.iterate, lambda: b.replicas[0].iterations, args.batched_grow)
     b.iterate(args.warmup)
     b.synchronize()
     t_grow = time.perf_counter() - t_grow

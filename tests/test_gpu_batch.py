@@ -52,7 +52,7 @@ def test_mixed_batch_equals_oracle_per_replica():
             c.iterate(step)
         done += step
         for r, (g, c) in enumerate(zip(b.replicas, cs)):
-            assert g.iterations() == done
+            assert g.iterations == done
             _same_lists(g, c, f"{done} (replica {r})")
     for g, c in zip(b.replicas, cs):
         _same_records(g, c)
@@ -73,7 +73,7 @@ def test_batch_replica_equals_single_run_and_advances_alone():
     b.replicas[0].iterate(10)
     b.iterate(20)
     one.iterate(30)
-    assert b.replicas[0].iterations() == 30 and b.replicas[1].iterations() == 20
+    assert b.replicas[0].iterations == 30 and b.replicas[1].iterations == 20
     _same_lists(b.replicas[0], one, 30)
     e0, e1 = b.replicas[0].estimators(), one.estimators()
     for k in e1:
