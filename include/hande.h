@@ -109,9 +109,9 @@ typedef struct {
                                  64/128-bit and 256 for 512-bit keys on the block path),
                                  else a power of two in [64, default]; smaller values only
                                  send more buckets through the slower paths */
-  int annihilation;           /* annihilation kernel: 0 = by key width (one warp per
-                                 bucket for 64- and 128-bit keys, block tiles for
-                                 512-bit), 1 = block tiles, 2 = one warp per bucket;
+  int annihilation;           /* annihilation kernel: 0 = default (one warp per
+                                 bucket), 1 = block tiles, 2 = one warp per bucket (large
+                                 or overflowing buckets go to block tiles on that path);
                                  every choice gives the same walker list */
 } hande_qmc;
 

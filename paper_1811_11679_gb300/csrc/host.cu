@@ -583,7 +583,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     // main-list entries (SM) per bucket; sized so four 256-thread CTAs share an SM
     // for 64- and 128-bit keys
     if (q.annihilation < 0 || q.annihilation > 2) throw Fail{HANDE_ERR_INVALID, "annihilation must be 0, 1 or 2"};
-    E.merge_warp = q.annihilation == 2 || (q.annihilation == 0 && E.W <= 2);
+    E.merge_warp = q.annihilation != 1;
     // block tiles: sized so that four 256-thread CTAs share an SM for 64- and
     // 128-bit keys.  Warp path: 128 staged new keys per warp, segments of at
     // most 192 entries, buckets sized for 1.5 x 128 expected spawns (most land

@@ -81,9 +81,9 @@ def test_ueg_128bit_initiator_real_weights():
     assert max(sizes) > 1000
 
 
-@pytest.mark.parametrize("annihilation", [0, 2])
+@pytest.mark.parametrize("annihilation", [1, 2])
 def test_ueg_512bit_keys(annihilation):
-    """512-bit keys: block tiles by default, and the warp-per-bucket path on request."""
+    """512-bit keys on block tiles and on the warp-per-bucket path (the default)."""
     sysd = inputs.ueg_system(14, 38, 1.0, key_words=8)
     q = inputs.qmc_params(tau=0.002, target_population=5000, initiator=1, real_amplitudes=1,
                           spawn_cutoff=0.1, init_pop=100, seed=7)
