@@ -600,6 +600,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
       P.warp_cap = std::min(kMwNew, tc);
     }
     P.bucket_spawns = E.merge_warp ? P.warp_cap * 3 / 2 : P.tile_cap / 2;
+    P.bucket_new = E.merge_warp ? P.warp_cap / 2 : 0;
     E.core_size = q.semi_stoch_size;
     E.core_start = q.semi_stoch_start;
 

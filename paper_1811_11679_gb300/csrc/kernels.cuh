@@ -53,6 +53,8 @@ struct DevState {
   int64_t scan_total;
   int64_t nspawn_prev;   // spawns of the previous iteration (bucket sizing)
   int64_t nnew;          // new determinants written by the merge
+  int64_t nuniq;         // distinct spawned keys the warp merge found off the list
+  int64_t nuniq_prev;    // the same count of the previous iteration (bucket sizing)
   unsigned error;
   unsigned merge_ticket;
   unsigned defer_ticket;   // block-kernel tickets over the deferred buckets
@@ -73,6 +75,7 @@ struct Params {
   int64_t cap, scap;
   int tile_cap, seg_max, rec_cap;
   int bucket_spawns;   // expected spawns per annihilation bucket (sizes the buckets)
+  int bucket_new;      // expected distinct new keys per bucket (0 = not used)
   int warp_cap;        // new keys one warp stages (warp annihilation)
   // main list (two buffers)
   uint64_t* key[2];
@@ -461,6 +464,13 @@ __global__ void k_split(Params P, int cur) {
     int64_t want = (int64_t)(((double)per * (double)n) / (double)na);
     if (want < sb) sb = want;
   }
+  // lists whose spawns mostly land off the list (many new keys per bucket)
+  // get smaller buckets, so that the warp staging rarely overflows
+  const int64_t nu = st->nuniq_prev;
+  if (P.bucket_new > 0 && nu > 0) {
+    int64_t want = (int64_t)(((double)P.bucket_new * (double)n) / (double)nu);
+    if (want < sb) sb = want;
+  }
   if (sb < 1) sb = 1;
   int64_t nb = (n + sb - 1) / sb;
   if (nb < 1) nb = 1;
@@ -469,6 +479,7 @@ __global__ void k_split(Params P, int cur) {
     st->sb = sb;
     st->nspawn = 0;
     st->nnew = 0;
+    st->nuniq = 0;
     st->merge_ticket = 0;
     st->defer_ticket = 0;
     st->big_ticket = 0;
@@ -1818,6 +1829,7 @@ static __global__ void k_finalize(Params P, int cur) {
   r.natt = st->natt;
   r.nspawn = st->nspawn;
   st->nspawn_prev = st->nspawn;
+  st->nuniq_prev = st->nuniq;
   I128 num{(uint64_t)st->num[0], (int64_t)st->num[1]};
   r.num_lo = num.lo;
   r.num_hi = num.hi;

@@ -417,10 +417,14 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur)
     }
     const int64_t out = c.m0 + (int64_t)P.boff[b];   // upper bound of the bucket's offset
     if (over) {   // too many distinct new keys for the staging: the block kernel takes it
-      if (lane == 0) P.att_begin[atomicAdd((unsigned long long*)&st->ndefer, 1ull)] = b;
+      if (lane == 0) {
+        P.att_begin[atomicAdd((unsigned long long*)&st->ndefer, 1ull)] = b;
+        atomicAdd((unsigned long long*)&st->nuniq, (unsigned long long)(cap + 1));   // at least
+      }
       continue;
     }
     const int u = wt_sort_dedupe<W>(t, nnew, lane);
+    if (lane == 0) atomicAdd((unsigned long long*)&st->nuniq, (unsigned long long)u);
     const uint32_t nkeep = wt_decide<W>(P, t, c, 0, nm, u, lane);
     uint32_t nnw = 0;
     nwsum += wt_write<W>(P, t, 0, nm, u, out, lane, &nnw);
