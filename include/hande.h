@@ -237,9 +237,10 @@ void hande_destroy(hande_ctx* ctx);
 const char* hande_last_error(const hande_ctx* ctx);
 
 /* ---------------------------------------------------------------- batches
- * Independent replicas advanced together.  The paper runs one calculation at a
- * time (its statistical analysis of several runs, section 3, combines runs
- * made one after another); a batch advances many of them on one GPU.  Replica r
+ * Independent replicas advanced together.  The paper has no batched form: a
+ * calculation is one run whose error bar comes from reblocking its own
+ * autocorrelated series (Sec. 3.1); only DMQMC averages over independent
+ * calculations.  A batch advances many independent runs on one GPU.  Replica r
  * is exactly the run hande_init_system(&sys[r], &qmc[r], ...) would make: its
  * walker lists and estimator records are bit-identical, so distinct seeds (or
  * distinct qmc.replica words) give independent Markov chains.
