@@ -105,7 +105,8 @@ typedef struct {
   int64_t spawn_capacity;     /* max spawns per iteration (0 = default) */
   int record_capacity;        /* estimator records kept on the device (0 = default) */
   int tile_capacity;          /* distinct new spawned keys one annihilation tile holds on
-                                 chip: 0 = default (128 per warp on the warp path; 512 for
+                                 chip: 0 = default (128 per warp on the warp path, 64 for
+                                 512-bit keys; 512 for
                                  64/128-bit and 256 for 512-bit keys on the block path),
                                  else a power of two in [64, default]; smaller values only
                                  send more buckets through the slower paths */

@@ -32,6 +32,7 @@ struct Ops {
   const void* merge_kernel;
   const void* merge_warp_kernel;
   size_t merge_warp_smem;
+  int merge_warp_main, merge_warp_new;   // warp tile: segment entries, staged new keys
   const void* attempt_kernel;
   size_t attempt_smem;
 };

@@ -585,19 +585,20 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (q.annihilation < 0 || q.annihilation > 2) throw Fail{HANDE_ERR_INVALID, "annihilation must be 0, 1 or 2"};
     E.merge_warp = q.annihilation != 1;
     // block tiles: sized so that four 256-thread CTAs share an SM for 64- and
-    // 128-bit keys.  Warp path: 128 staged new keys per warp, segments of at
-    // most 192 entries, buckets sized for 1.5 x 128 expected spawns (most land
-    // on listed entries); the buckets it defers go to block tiles.
+    // 128-bit keys.  Warp path: 128 staged new keys per warp and segments of
+    // at most 192 entries (64 and 96 for 512-bit keys), buckets sized for 1.5 x
+    // the staging in expected spawns (most land on listed entries) and for half
+    // the staging in distinct new keys; the buckets it defers go to block tiles.
     P.tile_cap = E.W == 8 ? 256 : 512;
-    P.seg_max = E.merge_warp ? kMwMain : (E.W == 1 ? 768 : (E.W == 2 ? 512 : 256));
-    P.warp_cap = kMwNew;
+    P.seg_max = E.merge_warp ? E.ops.merge_warp_main : (E.W == 1 ? 768 : (E.W == 2 ? 512 : 256));
+    P.warp_cap = E.ops.merge_warp_new;
     if (q.tile_capacity > 0) {
       int tc = q.tile_capacity;
       if (tc < 64 || tc > P.tile_cap || (tc & (tc - 1)))
         throw Fail{HANDE_ERR_INVALID, "tile_capacity must be a power of two in [64, default]"};
       P.tile_cap = tc;
       P.seg_max = std::min(P.seg_max, tc);
-      P.warp_cap = std::min(kMwNew, tc);
+      P.warp_cap = std::min(E.ops.merge_warp_new, tc);
     }
     P.bucket_spawns = E.merge_warp ? P.warp_cap * 3 / 2 : P.tile_cap / 2;
     P.bucket_new = E.merge_warp ? P.warp_cap / 2 : 0;

@@ -318,6 +318,8 @@ Ops make_ops() {
   o.merge_kernel = (const void*)&k_merge<W, SYS>;
   o.merge_warp_kernel = (const void*)&k_merge_warp<W, SYS>;
   o.merge_warp_smem = merge_warp_smem_bytes<W>();
+  o.merge_warp_main = MwDims<W>::kMain;
+  o.merge_warp_new = MwDims<W>::kNew;
   o.attempt_kernel = (const void*)&k_attempt<W, SYS>;
   o.attempt_smem = attempt_smem_bytes<W, SYS>();
   return o;

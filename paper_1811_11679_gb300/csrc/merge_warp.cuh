@@ -1,4 +1,4 @@
-// merge_warp.cuh -- annihilation with one warp per bucket (64- and 128-bit keys).
+// merge_warp.cuh -- annihilation with one warp per bucket (every key width).
 //
 // The annihilation step (HANDE-QMC paper Sec. 2.4 and App. B: combine the
 // spawned particles on each determinant, merge them into the sorted main list,
@@ -31,24 +31,36 @@ namespace hande {
 
 constexpr int kMwThreads = 256;   // 8 warps per CTA
 constexpr int kMwWarps = kMwThreads / 32;
-constexpr int kMwMain = 192;      // main-list entries per bucket (segment length cap)
-constexpr int kMwNew = 128;       // staged spawns onto new determinants per warp
-constexpr int kMwKeepWords = (kMwMain + kMwNew + 31) / 32;
+
+// Tile shape per key width: main-list entries per bucket (segment length cap)
+// and staged spawns onto new determinants per warp.  512-bit keys take half of
+// each, so that two CTAs (16 warps) fit on an SM as for the narrower keys.
+template <int W>
+struct MwDims {
+  static constexpr int kMain = W == 8 ? 96 : 192;
+  static constexpr int kNew = W == 8 ? 64 : 128;
+  static constexpr int kKeepWords = (kMain + kNew + 31) / 32;
+  static constexpr int kMinBlocks = W == 8 ? 2 : 3;   // CTAs per SM the registers are sized for
+  static_assert(kKeepWords <= 32, "keep words are scanned by one warp");
+  static_assert(kNew <= 128, "the register sort takes at most 128 staged keys");
+};
 
 template <int W>
 struct WarpTile {
-  uint64_t mkey[W][kMwMain];   // segment keys
-  int64_t macc[kMwMain];       // population plus the spawns onto the entry, then its final value
-  double mhd[kMwMain];         // segment entries' H_ii - E_ref
-  uint64_t nkey[W][kMwNew];    // staged keys of new determinants (sorted unique after dedupe)
-  int64_t namt[kMwNew];
-  uint32_t nflg[kMwNew];       // bit 0: an initiator parent
-  int16_t mrank[kMwMain];      // merged rank of a segment entry
-  int16_t nrank[kMwNew];       // merged rank of a new key
-  uint8_t mflg[kMwMain];       // segment entry flags
-  uint32_t keep[kMwKeepWords]; // keep bits by merged rank
-  uint32_t kpre[kMwKeepWords]; // kept entries before each word
-  int16_t rq[kMwMain + kMwNew];  // entries awaiting their occupation-rounding draw
+  static constexpr int kMain = MwDims<W>::kMain;
+  static constexpr int kNew = MwDims<W>::kNew;
+  uint64_t mkey[W][kMain];     // segment keys
+  int64_t macc[kMain];         // population plus the spawns onto the entry, then its final value
+  double mhd[kMain];           // segment entries' H_ii - E_ref
+  uint64_t nkey[W][kNew];      // staged keys of new determinants (sorted unique after dedupe)
+  int64_t namt[kNew];
+  uint32_t nflg[kNew];         // bit 0: an initiator parent
+  int16_t mrank[kMain];        // merged rank of a segment entry
+  int16_t nrank[kNew];         // merged rank of a new key
+  uint8_t mflg[kMain];         // segment entry flags
+  uint32_t keep[MwDims<W>::kKeepWords];  // keep bits by merged rank
+  uint32_t kpre[MwDims<W>::kKeepWords];  // kept entries before each word
+  int16_t rq[kMain + kNew];    // entries awaiting their occupation-rounding draw
 };
 
 template <int W>
@@ -218,8 +230,9 @@ template <int W>
 __device__ __forceinline__ int wt_sort_dedupe(WarpTile<W>& t, int n, int lane) {
   if (n <= 1) return n;
   if (n <= 32) return wt_sort_dedupe_e<W, 1>(t, n, lane);
-  if (n <= 64) return wt_sort_dedupe_e<W, 2>(t, n, lane);
-  return wt_sort_dedupe_e<W, 4>(t, n, lane);
+  if (MwDims<W>::kNew <= 64 || n <= 64) return wt_sort_dedupe_e<W, 2>(t, n, lane);   // n <= kNew
+  if constexpr (MwDims<W>::kNew > 64) return wt_sort_dedupe_e<W, 4>(t, n, lane);
+  return n;
 }
 
 // Decide one merge segment: the segment entries [mi, mh) and the unique new
@@ -266,7 +279,7 @@ __device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c
       if (!ok) t.namt[j] = 0;
     }
     const unsigned m = __ballot_sync(0xffffffffu, need);
-    if (need) t.rq[qn + __popc(m & below)] = (int16_t)(kMwMain + j);
+    if (need) t.rq[qn + __popc(m & below)] = (int16_t)(WarpTile<W>::kMain + j);
     qn += __popc(m);
   }
   __syncwarp();
@@ -274,8 +287,8 @@ __device__ uint32_t wt_decide(const Params& P, WarpTile<W>& t, const MergeCtx& c
   for (int q0 = 0; q0 < qn; q0 += 32) {
     if (q0 + lane < qn) {
       const int x = t.rq[q0 + lane];
-      const bool isnew = x >= kMwMain;
-      const int idx = isnew ? x - kMwMain : x;
+      const bool isnew = x >= WarpTile<W>::kMain;
+      const int idx = isnew ? x - WarpTile<W>::kMain : x;
       const Key<W> k = isnew ? wt_nkey<W>(t, idx) : wt_mkey<W>(t, idx);
       const int64_t p = round_small<W>(P, c.t, k, isnew ? t.namt[idx] : t.macc[idx]);
       if (isnew) t.namt[idx] = p;
@@ -341,7 +354,7 @@ __device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int
 
 // One warp per bucket, buckets taken from a ticket counter (see the file comment).
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMwThreads, 3) k_merge_warp(Params P, int cur) {
+__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_warp(Params P, int cur) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char mw_smem[];
   const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
