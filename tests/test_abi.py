@@ -72,3 +72,52 @@ def test_batch_arguments_rejected_before_any_device_call():
     assert lib.hande_batch_size(None) == 0
     assert lib.hande_batch_replica(None, 0) is None
     lib.hande_batch_destroy(None)
+
+
+def test_batch_binding_marshalling_and_errors(monkeypatch):
+    """HandeBatch passes one (system, qmc) struct pair per replica, names the
+    failing replica's message on an error, and frees the batch once (its
+    replica views never free their contexts)."""
+    seen = {"destroy": 0}
+
+    class FakeLib:
+        def hande_batch_init(self, S, Q, n, alloc, stream, out, bad):
+            seen["n"], seen["stream"], seen["alloc"] = n, stream.value, alloc
+            seen["sys"] = [(S[r].kind, S[r].key_words, S[r].norb, S[r].rs) for r in range(n)]
+            seen["qmc"] = [(Q[r].seed, Q[r].replica, Q[r].target_population) for r in range(n)]
+            out._obj.value = 77
+            return 0
+
+        def hande_batch_replica(self, h, r):
+            return 1000 + r
+
+        def hande_batch_size(self, h):
+            return seen["n"]
+
+        def hande_batch_iterate(self, h, k):
+            return -3
+
+        def hande_last_error(self, h):
+            return b"spawn capacity exceeded" if h.value == 1001 else b""
+
+        def hande_batch_destroy(self, h):
+            seen["destroy"] += 1
+
+        def hande_destroy(self, h):
+            raise AssertionError("a replica view must not free its context")
+
+    monkeypatch.setattr(hande, "load", lambda build_if_needed=True: FakeLib())
+    s1, q1 = inputs.workload("hubbard8")
+    s2, q2 = inputs.workload("ueg14")
+    b = hande.HandeBatch([s1, s2], [q1, dict(q2, replica=5)], stream=99, torch_memory=False)
+    assert len(b) == 2 and seen["stream"] == 99 and seen["alloc"] is None
+    assert seen["sys"] == [(0, 1, 8, 0.0), (1, 2, 38, 1.0)]
+    assert seen["qmc"] == [(8, 0, 1e4), (7, 5, 1e6)]
+    assert [v.W for v in b.replicas] == [1, 2]
+    with pytest.raises(hande.HandeError, match=r"replica 1: spawn capacity exceeded"):
+        b.iterate(3)
+    b.replicas[0].close()
+    b.close()
+    b.close()
+    assert seen["destroy"] == 1
+    assert all(not v._h for v in b.replicas)
