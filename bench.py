@@ -124,7 +124,10 @@ def _peaks():
 
 
 def _phase_bytes(rec, W):
-    """Algorithmic bytes per launch of the HBM-bound phases."""
+    """Algorithmic bytes per launch of the HBM-bound phases: K = 8W key bytes, a
+    main-list entry is K + 17 bytes (key, int64 population, f64 diagonal, flag
+    byte), a bucketed spawn K + 9 (key, int64 amount, initiator byte), a staged
+    spawn K + 16 (key, amount, bucket/rank word)."""
     K = 8 * W
     ns, nd_pre, nd_post = float(rec["nspawn"]), float(rec["ndet_pre"]), float(rec["ndet"])
     return {

@@ -125,7 +125,14 @@ typedef struct {
 } hande_allocator;
 
 /* One iteration's estimators (App. A.1), evaluated on the list at the start
- * of the iteration, plus population and throughput counters. */
+ * of the iteration, plus population and throughput counters.  The projected
+ * energy itself is the caller's ratio: over the iterations of an averaging
+ * window, E_proj = E_ref + <num> / <n0> (numerator and denominator averaged
+ * separately, App. A.1; both carry the same 2^32 population scale, so it
+ * cancels, and num carries an extra 2^16 in num_hi/num_lo only), with E_ref
+ * from hande_reference.  The library reports no ratio because a per-iteration
+ * ratio of two noisy sums is biased and has no finite variance when n0 can
+ * approach zero. */
 typedef struct {
   int64_t iter;        /* iteration number t >= 1 */
   double shift;        /* S after the update at the end of iteration t */
@@ -205,23 +212,27 @@ typedef struct {
 hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out);
 
 /* No-allocation projected-energy sums.  The paper has no counterpart: this
- * entry point exists for callers that cannot allocate device memory when they
- * need the estimator -- code under CUDA stream capture, code in stream host
- * callbacks, and frameworks that fix their device-memory budget up front.
+ * entry point exists for callers that may not allocate device memory when they
+ * need the estimator -- applications that reserve their whole device-memory
+ * budget up front and give plug-in code none of it, code whose memory pool
+ * owns every free byte of the device, and latency-critical loops that must not
+ * call cudaMalloc/cudaFree because those calls can synchronise the device.
  * It computes, for the walker list given in caller-owned DEVICE arrays,
  *   d_out[0] = sum |N_i|, d_out[1] = N on the reference determinant,
  *   d_out[2], d_out[3] = lo, hi words of the exact 128-bit numerator
  *                         sum_{j != ref} N_j H_0j * 2^16 (as in hande_estimate),
  * with d_keys[n*key_words] (row-major, word 0 first per walker, any order) and
- * d_pops[n] (fixed point), asynchronously on the context's stream.  It calls no
- * allocation routine: its per-block partial sums use one fixed device array
- * of 4096 slots (128 KiB, held by every device that loads the library until
- * the process exits), so n may be at most 16,777,216 (4096 x 4096); larger n
- * returns HANDE_ERR_CAPACITY.  Every call shares that array and overwrites the
- * slots it uses, so calls in flight at the same time (on different streams)
- * race.  The first call on each device looks up the array's address
- * (cudaGetSymbolAddress) with that device current; make it before any stream
- * capture. */
+ * d_pops[n] (fixed point), asynchronously on the context's stream; the arrays
+ * must live on the device the context was created on (made current for the
+ * call, the caller's current device restored afterwards).  n = 0 writes zeros.
+ * It calls no allocation routine: its per-block partial sums use one fixed
+ * device array of 4096 slots (128 KiB, held by every device that loads the
+ * library until the process exits), so n may be at most 16,777,216
+ * (4096 x 4096); larger n returns HANDE_ERR_CAPACITY.  Every call shares that
+ * array and overwrites the slots it uses, so calls in flight at the same time
+ * (on different streams) race.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. */
 hande_status hande_estimate_noalloc(hande_ctx* ctx, const uint64_t* d_keys, const int64_t* d_pops, int64_t n,
                                     int64_t* d_out);
 

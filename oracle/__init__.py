@@ -109,6 +109,9 @@ def _load():
         lib.orc_ueg_basis.restype = C.c_int
         lib.orc_core.argtypes = [P, u64p, C.c_int64]
         lib.orc_core.restype = C.c_int64
+        lib.orc_heat_bath.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
+                                      C.c_int64]
+        lib.orc_heat_bath.restype = C.c_int64
         _lib = lib
         return lib
 
@@ -297,3 +300,17 @@ class Oracle:
         k = np.zeros((cap, self.W), dtype=np.uint64)
         n = self._lib.orc_core(self._h, k.ctypes.data_as(C.POINTER(C.c_uint64)), cap)
         return k[:n].copy()
+
+    def heat_bath_table(self, p: int, q: int):
+        """The heat-bath table of the occupied spin-orbital pair p < q:
+        (a[m], b[m], cum[m]) in table order (cumulative 64-bit thresholds)."""
+        cap = 1 << 16
+        a = np.zeros(cap, dtype=np.int32)
+        b = np.zeros(cap, dtype=np.int32)
+        cum = np.zeros(cap, dtype=np.uint64)
+        m = self._lib.orc_heat_bath(self._h, int(p), int(q), a.ctypes.data_as(C.POINTER(C.c_int)),
+                                    b.ctypes.data_as(C.POINTER(C.c_int)),
+                                    cum.ctypes.data_as(C.POINTER(C.c_uint64)), cap)
+        if m < 0:
+            raise ValueError("no heat-bath table for this system or pair")
+        return a[:m].copy(), b[:m].copy(), cum[:m].copy()

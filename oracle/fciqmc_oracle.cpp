@@ -17,12 +17,15 @@
  *   - App. A.1: projected energy  E = E_HF + sum_{i!=0} C_i H_0i / C_0.
  *   - App. B: sorted main list, spawned array, sort + merge annihilation.
  *
- * Where the paper is silent the oracle takes the readings listed in the design doc
- * (weights as int64 fixed point with F = 2^32, counter-based Philox4x64-10
- * keyed by (seed, replica) with counter (t, attempt, det), Slater-Condon sign
- * convention, UEG basis ordering, heat-bath-with-rejection generator, shift
- * update rule, exact 128-bit fixed-point accumulation of the estimator
- * numerator and of the deterministic-space product).
+ * Where the paper is silent the oracle takes these readings: weights as int64
+ * fixed point with F = 2^32; counter-based Philox4x64-10 keyed by (seed,
+ * replica) with counter (t, attempt, det); the Slater-Condon sign of moving an
+ * electron = (-1)^(occupied spin orbitals strictly between); UEG plane waves
+ * ordered by (|n|^2, nx, ny, nz); a heat-bath-with-rejection generator over
+ * cumulative integer thresholds; the shift held until the target population
+ * and then updated every A iterations; exact 128-bit fixed-point accumulation
+ * of the estimator numerator and of the deterministic-space product.  Each is
+ * stated again where the code takes it.
  *
  * Parity status: Philox, the logarithm, Slater-Condon, generators and the
  * full iteration are pinned by tests/test_oracle_*.py against numpy,
@@ -1253,6 +1256,23 @@ int orc_ueg_basis(void* h, int* kvec, double* box) {
     for (int i = 0; i < 3 * c->norb; ++i) kvec[i] = c->kvec[(size_t)i];
     *box = c->box;
     return c->norb;
+}
+
+/* The heat-bath table of the occupied pair (p < q): entries (a, b) in table
+ * order with their cumulative thresholds.  Returns the entry count, -1 for a
+ * system without tables or a bad pair, -count if cap is too small. */
+int64_t orc_heat_bath(void* h, int p, int q, int* a, int* b, uint64_t* cum, int64_t cap) {
+    Ctx* c = (Ctx*)h;
+    if (c->kind != SYS_MOLECULE || p < 0 || q <= p || q >= c->nspin) return -1;
+    const std::vector<HBEntry>& tab = c->hb[pair_index(p, q)];
+    int64_t n = (int64_t)tab.size();
+    if (n > cap) return -n;
+    for (int64_t k = 0; k < n; ++k) {
+        a[k] = tab[(size_t)k].a;
+        b[k] = tab[(size_t)k].b;
+        cum[k] = tab[(size_t)k].cum;
+    }
+    return n;
 }
 
 int64_t orc_core(void* h, uint64_t* keys, int64_t cap) {

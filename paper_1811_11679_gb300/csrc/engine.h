@@ -47,6 +47,7 @@ struct Engine {
   Params P{};            // device pointers and run constants (kernel argument)
   Ops ops{};
   int W = 1, kind = 0, nalpha = 0, nbeta = 0;
+  int device = 0;                     // CUDA device the context was created on
   cudaStream_t stream = nullptr;      // caller's stream
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   cudaStream_t aux_stream = nullptr;  // second branch of a captured iteration

@@ -580,12 +580,12 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (P.scap >= ((int64_t)1 << 31)) throw Fail{HANDE_ERR_INVALID, "spawn_capacity must be below 2^31"};
     P.rec_cap = q.record_capacity > 0 ? q.record_capacity : 1 << 16;
     // on-chip tile: distinct new keys (TC, a power of two for the bitonic sort) and
-    // main-list entries (SM) per bucket; sized so four 256-thread CTAs share an SM
-    // for 64- and 128-bit keys
+    // main-list entries (SM) per bucket
     if (q.annihilation < 0 || q.annihilation > 2) throw Fail{HANDE_ERR_INVALID, "annihilation must be 0, 1 or 2"};
     E.merge_warp = q.annihilation != 1;
     // block tiles: sized so that four 256-thread CTAs share an SM for 64- and
-    // 128-bit keys.  Warp path: 128 staged new keys per warp and segments of
+    // 128-bit keys (two for 512-bit keys).  Warp path (three 8-warp CTAs per SM,
+    // two for 512-bit keys): 128 staged new keys per warp and segments of
     // at most 192 entries (64 and 96 for 512-bit keys), buckets sized for 1.5 x
     // the staging in expected spawns (most land on listed entries) and for half
     // the staging in distinct new keys; the buckets it defers go to block tiles.
@@ -701,6 +701,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     // ---- launch geometry
     int dev = 0, nsm = 0;
     CK(cudaGetDevice(&dev));
+    E.device = dev;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     E.merge_smem_bytes = E.ops.merge_smem(P.tile_cap, P.seg_max);
     CK(cudaFuncSetAttribute(E.ops.merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1,14 +1,15 @@
 // noalloc.cu -- hande_estimate_noalloc: the projected-energy sums of a walker
 // list without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need this
-// reduction: code running under CUDA stream capture (where cudaMalloc would
-// either be refused or silently stay outside the graph), code called from a
-// host callback on a stream (which may not call CUDA allocation routines at
-// all), and frameworks that budget every byte of device memory up front and
-// forbid allocations (and the device-wide synchronisation cudaMalloc implies)
-// inside a step.  For them the per-block partial sums live in one file-scope
-// device array of fixed size instead of context scratch memory.
+// Some callers may not allocate device memory at the moment they need this
+// reduction: applications that reserve their whole device-memory budget at
+// start-up and give plug-in code none of it (an allocation there either fails
+// or pushes the process over its budget), code whose memory pool owns every
+// free byte of the device (a foreign cudaMalloc then runs out of memory even
+// though the pool has room), and latency-critical loops that must not call
+// cudaMalloc/cudaFree because those calls can synchronise the whole device and
+// stall the other streams.  For them the per-block partial sums live in one
+// file-scope device array of fixed size instead of context scratch memory.
 //
 // The array is shared by every call in the process on a given device and
 // keeps the previous call's contents; each call overwrites exactly the slots
@@ -122,18 +123,43 @@ extern "C" hande_status hande_estimate_noalloc(hande_ctx* ctx, const uint64_t* d
             "its fixed scratch array";
     return HANDE_ERR_CAPACITY;
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+  // The context's kernels and stream belong to the device it was created on;
+  // that device is made current for the set-up and the launches, and the
+  // caller's current device is restored afterwards.
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
     E.err = "hande_estimate_noalloc: no current CUDA device";
+    return HANDE_ERR_CUDA;
+  }
+  const int dev = E.device;
+  if (dev < 0 || dev >= 256) {
+    E.err = "hande_estimate_noalloc: device index out of range";
+    return HANDE_ERR_INVALID;
+  }
+  struct DeviceGuard {
+    int prev;
+    bool switched;
+    ~DeviceGuard() {
+      if (switched) cudaSetDevice(prev);
+    }
+  } guard{prev, prev != dev};
+  if (guard.switched && cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    guard.switched = false;
+    E.err = "hande_estimate_noalloc: cannot make the context's device current";
     return HANDE_ERR_CUDA;
   }
   Partial* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_scratch[dev]) {
+      // host code sees only a host-side stand-in for the array: its device
+      // address is looked up here, once per device, with that device current
       void* ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
       if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
         E.err = std::string("hande_estimate_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
         return HANDE_ERR_CUDA;
       }

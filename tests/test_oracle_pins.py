@@ -345,3 +345,57 @@ def test_generator_uses_128_bit_keys():
         seen += 1
         assert orc.hij(d0, r[0]) == r[2]
     assert seen > 0
+
+
+def _spin_eri(eri, p, q, r, s):
+    """(pq|rs) over spin orbitals (spin orbital = 2 * spatial + spin)."""
+    if (p & 1) != (q & 1) or (r & 1) != (s & 1):
+        return 0.0
+    return float(eri[p >> 1, q >> 1, r >> 1, s >> 1])
+
+
+@pytest.mark.parametrize("norb,seed,pairs", [(6, 4, None), (28, 11, 40)])
+def test_heat_bath_table_weights_are_antisymmetrised_integrals(norb, seed, pairs):
+    """The heat-bath reading: the table of an occupied pair (p < q) lists every
+    spin-allowed (a < b) outside {p, q} with w = |(pa|qb) - (pb|qa)| > 0 in
+    ascending (a, b) order, and entry k is drawn with probability w_k / sum w.
+    The weights are recomputed here from the integrals alone (a swapped index
+    or a dropped exchange term changes them), and the drawn probabilities are
+    the widths of the oracle's cumulative 64-bit thresholds."""
+    h1, eri = inputs.molecule_integrals(norb, seed=seed)
+    sysd = {"kind": "molecule", "key_words": 1, "norb": norb, "nalpha": 3, "nbeta": 2,
+            "h1": h1, "eri": eri, "ecore": 0.0}
+    orc = oracle.Oracle(sysd, inputs.qmc_params())
+    ns = 2 * norb
+    allp = [(p, q) for q in range(1, ns) for p in range(q)]
+    if pairs is not None:
+        rng = np.random.default_rng(seed)
+        allp = [allp[i] for i in rng.choice(len(allp), pairs, replace=False)]
+    two64 = 2.0 ** 64
+    for p, q in allp:
+        want_ab, want_w = [], []
+        for a in range(ns):
+            for b in range(a + 1, ns):
+                if a in (p, q) or b in (p, q):
+                    continue
+                ok = ((a & 1) == (p & 1) and (b & 1) == (q & 1)) or ((a & 1) == (q & 1) and (b & 1) == (p & 1))
+                if not ok:
+                    continue
+                w = abs(_spin_eri(eri, p, a, q, b) - _spin_eri(eri, p, b, q, a))
+                if w > 0.0:
+                    want_ab.append((a, b))
+                    want_w.append(w)
+        ta, tb, cum = orc.heat_bath_table(p, q)
+        assert list(zip(ta.tolist(), tb.tolist())) == want_ab, (p, q)
+        m = len(want_w)
+        if m == 0:
+            continue
+        if m == 1:
+            continue   # a single entry is drawn with probability 1
+        c = [int(x) for x in cum[:-1]]
+        widths = [c[0]] + [c[k] - c[k - 1] for k in range(1, m - 1)] + [(1 << 64) - c[-1]]
+        assert all(wd > 0 for wd in widths)
+        got = np.array(widths, dtype=np.float64) / two64
+        want = np.array(want_w) / np.sum(want_w)
+        tol = (m + 4) * 2.0 ** -52
+        assert np.max(np.abs(got - want)) <= tol, (p, q, np.max(np.abs(got - want)))

@@ -1,8 +1,10 @@
-"""hande_estimate_noalloc, the entry point for callers that cannot allocate
-device memory (stream capture, host callbacks, fixed memory budgets): its
-projected-energy sums must equal those the regular iteration records for the
-same walker list, call after call, although its partial sums live in one
-fixed device array shared by all calls.  Collected last on purpose."""
+"""hande_estimate_noalloc, the entry point for callers that may not allocate
+device memory (an application that reserved its whole device budget up front,
+a memory pool that owns every free byte, a latency-critical loop that must not
+call cudaMalloc because it can synchronise the device): its projected-energy
+sums must equal those the regular iteration records for the same walker list,
+call after call, although its partial sums live in one fixed device array
+shared by all calls.  Collected last on purpose."""
 from __future__ import annotations
 
 import numpy as np
@@ -54,6 +56,34 @@ def test_noalloc_estimator_equals_iteration_records(torch_cuda, workload, kw):
         assert got[3] == rec["num_hi"][-1]
         g.iterate(5)
         g.estimators()
+    g.close()
+
+
+def test_noalloc_allocates_nothing_and_handles_an_empty_list(torch_cuda):
+    """A call changes neither PyTorch's device-memory statistics (the library's
+    own buffers are routed through PyTorch's allocator) nor needs a list: n = 0
+    writes zeros."""
+    torch = torch_cuda
+    sysd, q = inputs.workload("ueg14", target_population=20000, init_pop=1000)
+    g = hande.Hande(sysd, q)
+    g.iterate(30)
+    keys, pops, _, _ = g.walkers()
+    dk, dp = _device_list(torch, keys, pops)
+    out = torch.full((4,), -1, dtype=torch.int64, device="cuda")
+    g.estimate_noalloc(dk.data_ptr(), dp.data_ptr(), len(pops), out.data_ptr())   # first call: set-up
+    g.synchronize()
+    first = out.cpu().numpy().copy()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_stats()
+    g.estimate_noalloc(dk.data_ptr(), dp.data_ptr(), len(pops), out.data_ptr())
+    g.synchronize()
+    after = torch.cuda.memory_stats()
+    for k in ("allocation.all.allocated", "segment.all.allocated", "reserved_bytes.all.current"):
+        assert before.get(k) == after.get(k), k
+    assert np.array_equal(out.cpu().numpy(), first)
+    g.estimate_noalloc(0, 0, 0, out.data_ptr())
+    g.synchronize()
+    assert out.cpu().numpy().tolist() == [0, 0, 0, 0]
     g.close()
 
 
