@@ -236,6 +236,40 @@ hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out);
 hande_status hande_estimate_noalloc(hande_ctx* ctx, const uint64_t* d_keys, const int64_t* d_pops, int64_t n,
                                     int64_t* d_out);
 
+/* Run state beyond the walker list, for restarting a calculation (Sec. 3.1:
+ * restart files carry everything -- the random-number state included -- that
+ * a restarted calculation needs to follow the same Markov chain as one that
+ * ran uninterrupted).  The random numbers here are counter-based (Philox keyed
+ * by seed and replica, counter = iteration, attempt, determinant), so their
+ * whole state is the iteration number. */
+typedef struct {
+  int64_t iter;       /* completed iterations t */
+  double shift;       /* S after iteration t */
+  int64_t nw_ref;     /* sum |N| at the last shift update (or when the target was
+                         first exceeded), fixed point; 0 before that */
+  int vary;           /* 1 once the population exceeded target_population */
+  int core_active;    /* 1 once the deterministic space was chosen */
+  int64_t ncore;      /* its size (0 when not active) */
+} hande_state;
+
+/* Copy the run state to *out and, if core_keys is not NULL and the
+ * deterministic space is active, its keys to core_keys[ncore*key_words]
+ * (ascending, word 0 first per key); HANDE_ERR_CAPACITY if ncore > core_cap.
+ * Synchronises.  Together with hande_get_walkers this is a restart snapshot. */
+hande_status hande_get_state(hande_ctx* ctx, hande_state* out, uint64_t* core_keys, int64_t core_cap);
+
+/* Restore a snapshot into a context made with the same system and run
+ * parameters: call hande_set_walkers(list) first, then this.  It sets the
+ * iteration counter, the shift, its latch and reference population, and (with
+ * core_active) installs the given deterministic space (every key must be in
+ * the list, the reference among them, at most semi_stoch_size keys) in place
+ * of any space set_walkers chose; without core_active the context has no
+ * deterministic space until semi_stoch_start (if still ahead).  Records start
+ * after the restored iteration.  The continued run equals the uninterrupted one
+ * bit for bit.  HANDE_ERR_INVALID (context unchanged except its deterministic
+ * space, which is then off) on inconsistent input.  Synchronises. */
+hande_status hande_set_state(hande_ctx* ctx, const hande_state* state, const uint64_t* core_keys);
+
 /* E_ref = H_00 of the reference determinant, and its key (key_words words). */
 hande_status hande_reference(hande_ctx* ctx, double* e_ref, uint64_t* key);
 

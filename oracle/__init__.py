@@ -109,6 +109,10 @@ def _load():
         lib.orc_ueg_basis.restype = C.c_int
         lib.orc_core.argtypes = [P, u64p, C.c_int64]
         lib.orc_core.restype = C.c_int64
+        lib.orc_get_state.argtypes = [P, i64p, dp, i64p, C.POINTER(C.c_int)]
+        lib.orc_get_state.restype = None
+        lib.orc_set_state.argtypes = [P, C.c_int64, C.c_double, C.c_int64, C.c_int, u64p, C.c_int64]
+        lib.orc_set_state.restype = C.c_int
         lib.orc_heat_bath.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                       C.c_int64]
         lib.orc_heat_bath.restype = C.c_int64
@@ -314,3 +318,21 @@ class Oracle:
         if m < 0:
             raise ValueError("no heat-bath table for this system or pair")
         return a[:m].copy(), b[:m].copy(), cum[:m].copy()
+
+    def state(self):
+        """Restart snapshot beyond the walker list: (dict with iter, shift,
+        nw_ref, vary, core_active, ncore; deterministic-space keys[ncore, W])."""
+        it, sh, nw, va = C.c_int64(), C.c_double(), C.c_int64(), C.c_int()
+        self._lib.orc_get_state(self._h, C.byref(it), C.byref(sh), C.byref(nw), C.byref(va))
+        core = self.core()
+        return ({"iter": it.value, "shift": sh.value, "nw_ref": nw.value, "vary": va.value,
+                 "core_active": int(len(core) > 0), "ncore": len(core)}, core)
+
+    def set_state(self, state: dict, core_keys=None) -> None:
+        """Restore a snapshot (after set_walkers of its list)."""
+        n = int(state["ncore"]) if state.get("core_active") else 0
+        k, kp = _u64(np.zeros((1, self.W)) if n == 0 else np.asarray(core_keys).reshape(-1, self.W))
+        rc = self._lib.orc_set_state(self._h, int(state["iter"]), float(state["shift"]), int(state["nw_ref"]),
+                                     int(state["vary"]), kp, n)
+        if rc != 0:
+            raise ValueError("a deterministic-space key is not in the walker list")

@@ -680,6 +680,7 @@ bool in_core(const Ctx& c, const Det& d) {
 inline int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
 
 void select_core(Ctx& c);
+void install_core(Ctx& c, std::vector<Det> keys);
 
 void iterate_once(Ctx& c) {
     const int64_t t = ++c.iter;
@@ -906,11 +907,18 @@ void select_core(Ctx& c) {
     });
     size_t ntake = (size_t)c.core_size - 1;
     if (ntake > idx.size()) ntake = idx.size();
-    c.core.clear();
-    c.core.push_back(c.d0);
-    for (size_t k = 0; k < ntake; ++k) c.core.push_back(c.main[idx[k]].key);
+    std::vector<Det> keys;
+    keys.push_back(c.d0);
+    for (size_t k = 0; k < ntake; ++k) keys.push_back(c.main[idx[k]].key);
+    install_core(c, keys);
+}
+
+/* make `keys` the deterministic space: sorted, members flagged in the list,
+ * H' in rows and columns of key order */
+void install_core(Ctx& c, std::vector<Det> keys) {
     const int W = c.W;
-    std::sort(c.core.begin(), c.core.end(), [W](const Det& x, const Det& y) { return det_cmp(x, y, W) < 0; });
+    std::sort(keys.begin(), keys.end(), [W](const Det& x, const Det& y) { return det_cmp(x, y, W) < 0; });
+    c.core = keys;
     for (size_t i = 0; i < c.main.size(); ++i) c.main[i].core = in_core(c, c.main[i].key) ? 1 : 0;
     /* H' = H - E_ref on the diagonal; rows and columns in key order */
     c.core_rows.assign(c.core.size(), std::vector<std::pair<int, double>>());
@@ -1256,6 +1264,48 @@ int orc_ueg_basis(void* h, int* kvec, double* box) {
     for (int i = 0; i < 3 * c->norb; ++i) kvec[i] = c->kvec[(size_t)i];
     *box = c->box;
     return c->norb;
+}
+
+/* Restart (Sec. 3.1: a restarted calculation follows the same Markov chain).
+ * With counter-based random numbers the generator state is the iteration
+ * number; the rest is the shift, its latch and reference population, and the
+ * deterministic space. */
+void orc_get_state(void* h, int64_t* iter, double* shift, int64_t* nw_ref, int* vary) {
+    Ctx* c = (Ctx*)h;
+    *iter = c->iter;
+    *shift = c->shift;
+    *nw_ref = c->nw_ref;
+    *vary = c->vary;
+}
+
+/* after orc_set_walkers: restore the counters and the deterministic space
+ * (ncore keys, all in the list; ncore = 0: none).  Returns 0, or -1 if a core
+ * key is not in the list. */
+int orc_set_state(void* h, int64_t iter, double shift, int64_t nw_ref, int vary, const uint64_t* core_keys,
+                  int64_t ncore) {
+    Ctx* c = (Ctx*)h;
+    std::vector<Det> keys;
+    for (int64_t i = 0; i < ncore; ++i) {
+        Det d;
+        memset(&d, 0, sizeof d);
+        for (int k = 0; k < c->W; ++k) d.w[k] = core_keys[i * c->W + k];
+        keys.push_back(d);
+    }
+    c->iter = iter;
+    c->shift = shift;
+    c->nw_ref = nw_ref;
+    c->vary = vary;
+    c->recs.clear();
+    if (ncore == 0) {
+        c->core.clear();
+        c->core_rows.clear();
+        for (size_t i = 0; i < c->main.size(); ++i) c->main[i].core = 0;
+        return 0;
+    }
+    install_core(*c, keys);
+    int64_t found = 0;
+    for (size_t i = 0; i < c->main.size(); ++i) found += c->main[i].core;
+    return found == ncore ? 0 : -1;
 }
 
 /* The heat-bath table of the occupied pair (p < q): entries (a, b) in table

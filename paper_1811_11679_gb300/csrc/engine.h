@@ -23,8 +23,12 @@ struct Ops {
   void (*sel_gather)(Engine& E, int cur, uint64_t* core_key, int64_t ncore, cudaStream_t s);
   void (*core_hash)(Engine& E, uint32_t* table, cudaStream_t s);
   void (*check_keys)(Engine& E, const uint64_t* aos, int64_t n, unsigned* out, cudaStream_t s);
-  void (*keys_to_soa)(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, cudaStream_t s);
-  void (*keys_to_aos)(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, cudaStream_t s);
+  // array of structures <-> structure of arrays with word stride `stride`
+  void (*keys_to_soa)(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, int64_t stride, cudaStream_t s);
+  void (*keys_to_aos)(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, int64_t stride, cudaStream_t s);
+  // core flags of the list from the core keys (P.core_key, P.ncore); a core key
+  // missing from the list sets bit 0 of *missing
+  void (*core_mark)(Engine& E, int cur, unsigned* missing, cudaStream_t s);
   void (*sel_hist)(Engine& E, int cur, int shift, uint64_t mask, uint64_t prefix, unsigned long long* hist,
                    cudaStream_t s);
   void (*sel_flags)(Engine& E, int cur, uint64_t vstar, int64_t need_eq, int stage, cudaStream_t s);

@@ -395,6 +395,9 @@ int64_t read_i64(Engine& E, size_t off) {
   return v;
 }
 
+void reserve_core(Engine& E, int64_t ncore);
+void build_core_tables(Engine& E);
+
 // Deterministic space "high": the reference plus the (size - 1) other
 // determinants of largest |N| (ties by ascending key), then H' in CSR.
 void select_core(Engine& E) {
@@ -435,6 +438,16 @@ void select_core(Engine& E) {
   E.ops.sel_flags(E, cur, vstar, need_eq, 1, E.stream);
   scan_natt(E, cur);
   const int64_t ncore = read_i64(E, offsetof(DevState, scan_total));
+  reserve_core(E, ncore);
+  E.ops.sel_gather(E, cur, E.core_key, ncore, E.stream);
+  P.ncore = (int)ncore;
+  P.core_key = E.core_key;
+  build_core_tables(E);
+}
+
+// device arrays of a deterministic space of ncore determinants
+void reserve_core(Engine& E, int64_t ncore) {
+  Params& P = E.P;
   if (ncore > E.ncore_cap) {
     E.core_key = dalloc<uint64_t>(E, (size_t)ncore * E.W);
     E.ncore_cap = ncore;
@@ -443,9 +456,13 @@ void select_core(Engine& E) {
     P.core_x = dalloc<int64_t>(E, ncore);
     E.core_rowptr = dalloc<int64_t>(E, ncore + 1);
   }
-  E.ops.sel_gather(E, cur, E.core_key, ncore, E.stream);
-  P.ncore = (int)ncore;
-  P.core_key = E.core_key;
+}
+
+// membership hash table and CSR of H' for the core keys in P.core_key (sorted,
+// P.ncore of them, flagged in the list); the space is active afterwards
+void build_core_tables(Engine& E) {
+  Params& P = E.P;
+  const int64_t ncore = P.ncore;
   // membership hash table: a power of two >= 4 ncore slots
   int64_t tsize = 64;
   while (tsize < 4 * ncore) tsize <<= 1;
@@ -886,7 +903,7 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
     // keys transposed on the device into the other list buffer (free between
     // iterations), then one copy
     uint64_t* stage = E.P.key[cur ^ 1];
-    E.ops.keys_to_aos(E, E.P.key[cur], stage, nd, E.stream);
+    E.ops.keys_to_aos(E, E.P.key[cur], stage, nd, E.P.cap, E.stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(keys, stage, (size_t)nd * W * 8, cudaMemcpyDeviceToHost, E.stream));
     CK(cudaMemcpyAsync(pops, E.P.pop[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
@@ -922,7 +939,7 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     if (bits & 2u) throw Fail{HANDE_ERR_INVALID, "a key has the wrong electron numbers"};
     if (bits & 4u) throw Fail{HANDE_ERR_INVALID, "keys must be strictly ascending"};
     if (!(bits & 8u)) throw Fail{HANDE_ERR_INVALID, "the reference determinant must be in the list"};
-    E.ops.keys_to_soa(E, stage, E.P.key[cur], n, E.stream);
+    E.ops.keys_to_soa(E, stage, E.P.key[cur], n, E.P.cap, E.stream);
     CK(cudaMemcpyAsync(E.P.pop[cur], pops, n * 8, cudaMemcpyHostToDevice, E.stream));
     CK(cudaMemsetAsync(E.P.flags[cur], 0, n, E.stream));
     CK(cudaMemcpyAsync((char*)E.P.st + offsetof(DevState, ndet) + 8 * cur, &n, 8, cudaMemcpyHostToDevice, E.stream));
@@ -937,6 +954,98 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     drop_graphs(E, 1);
     if (reselect) select_core(E);
     CK(cudaStreamSynchronize(E.stream));
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_get_state(hande_ctx* ctx, hande_state* out, uint64_t* core_keys, int64_t core_cap) {
+  if (!ctx || !out) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    hande_status es = map_error(E, read_error(E));
+    if (es != HANDE_OK) return es;
+    DevState hs;
+    CK(cudaMemcpyAsync(&hs, E.P.st, sizeof hs, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    std::memset(out, 0, sizeof *out);
+    out->iter = hs.iter;
+    out->shift = hs.shift;
+    out->nw_ref = hs.nw_ref;
+    out->vary = hs.vary;
+    out->core_active = E.core_active ? 1 : 0;
+    out->ncore = E.core_active ? E.P.ncore : 0;
+    if (!core_keys || out->ncore == 0) return HANDE_OK;
+    if (out->ncore > core_cap) return HANDE_ERR_CAPACITY;
+    // the core keys transposed on the device into the other list buffer (free
+    // between iterations), then one copy
+    uint64_t* stage = E.P.key[E.cur ^ 1];
+    E.ops.keys_to_aos(E, E.core_key, stage, out->ncore, out->ncore, E.stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(core_keys, stage, (size_t)out->ncore * E.W * 8, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_set_state(hande_ctx* ctx, const hande_state* in, const uint64_t* core_keys) {
+  if (!ctx || !in) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (in->iter < 0 || (in->vary != 0 && in->vary != 1) || in->nw_ref < 0 || !std::isfinite(in->shift))
+      throw Fail{HANDE_ERR_INVALID, "bad run state (iteration, shift, vary latch or reference population)"};
+    if (in->vary == 1 && in->nw_ref == 0)
+      throw Fail{HANDE_ERR_INVALID, "a varying shift needs a nonzero reference population"};
+    const int64_t ncore = in->core_active ? in->ncore : 0;
+    if (in->core_active && (E.core_size <= 0 || ncore < 1 || ncore > E.core_size || !core_keys))
+      throw Fail{HANDE_ERR_INVALID, "deterministic space: needs semi_stoch_size >= ncore >= 1 and its keys"};
+    const int cur = E.cur;
+    const int64_t nd = read_i64(E, offsetof(DevState, ndet) + 8 * cur);
+    if (ncore > nd) throw Fail{HANDE_ERR_INVALID, "deterministic space larger than the walker list"};
+    if (ncore > 0) {
+      // check the keys (ascending, electron numbers, the reference among them)
+      // in the other list buffer, then transpose them into the core's layout
+      uint64_t* stage = E.P.key[cur ^ 1];
+      CK(cudaMemcpyAsync(stage, core_keys, (size_t)ncore * E.W * 8, cudaMemcpyHostToDevice, E.stream));
+      CK(cudaMemsetAsync(E.check_word, 0, sizeof(unsigned), E.stream));
+      E.ops.check_keys(E, stage, ncore, E.check_word, E.stream);
+      CK(cudaGetLastError());
+      unsigned bits = 0;
+      CK(cudaMemcpyAsync(&bits, E.check_word, sizeof bits, cudaMemcpyDeviceToHost, E.stream));
+      CK(cudaStreamSynchronize(E.stream));
+      if (bits & 7u) throw Fail{HANDE_ERR_INVALID, "core keys must be valid determinants in ascending order"};
+      if (!(bits & 8u)) throw Fail{HANDE_ERR_INVALID, "the reference determinant must be in the core"};
+      reserve_core(E, ncore);
+      E.ops.keys_to_soa(E, stage, E.core_key, ncore, ncore, E.stream);
+    }
+    E.P.ncore = (int)ncore;
+    E.P.core_key = E.core_key;
+    CK(cudaMemsetAsync(E.check_word, 0, sizeof(unsigned), E.stream));
+    E.ops.core_mark(E, cur, E.check_word, E.stream);
+    CK(cudaGetLastError());
+    unsigned missing = 0;
+    CK(cudaMemcpyAsync(&missing, E.check_word, sizeof missing, cudaMemcpyDeviceToHost, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    if (missing) {
+      E.P.ncore = 0;
+      E.core_active = false;
+      drop_graphs(E, 1);
+      throw Fail{HANDE_ERR_INVALID, "a deterministic-space determinant is not in the walker list"};
+    }
+    E.core_active = false;
+    drop_graphs(E, 1);
+    if (ncore > 0) build_core_tables(E);
+    // counters of the run: iteration, shift, its latch and reference population
+    DevState* st = E.P.st;
+    CK(cudaMemcpyAsync((char*)st + offsetof(DevState, iter), &in->iter, 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync((char*)st + offsetof(DevState, shift), &in->shift, 8, cudaMemcpyHostToDevice, E.stream));
+    CK(cudaMemcpyAsync((char*)st + offsetof(DevState, nw_ref), &in->nw_ref, 8, cudaMemcpyHostToDevice, E.stream));
+    const int vary = in->vary;
+    CK(cudaMemcpyAsync((char*)st + offsetof(DevState, vary), &vary, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+    CK(cudaStreamSynchronize(E.stream));
+    E.host_iter = in->iter;
+    E.fetched = in->iter;
     return HANDE_OK;
   });
 }

@@ -286,12 +286,35 @@ void enqueue_check_keys(Engine& E, const uint64_t* aos, int64_t n, unsigned* out
   k_check_keys<W><<<4 * 152, 256, 0, s>>>(aos, n, E.P.sys.nspin, E.nalpha, E.nbeta, d0, out);
 }
 template <int W>
-void enqueue_keys_to_soa(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, cudaStream_t s) {
-  k_keys_to_soa<W><<<4 * 152, 256, 0, s>>>(aos, soa, n, E.P.cap);
+void enqueue_keys_to_soa(Engine& E, const uint64_t* aos, uint64_t* soa, int64_t n, int64_t stride, cudaStream_t s) {
+  k_keys_to_soa<W><<<4 * 152, 256, 0, s>>>(aos, soa, n, stride);
 }
 template <int W>
-void enqueue_keys_to_aos(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, cudaStream_t s) {
-  k_keys_to_aos<W><<<4 * 152, 256, 0, s>>>(soa, aos, n, E.P.cap);
+void enqueue_keys_to_aos(Engine& E, const uint64_t* soa, uint64_t* aos, int64_t n, int64_t stride, cudaStream_t s) {
+  k_keys_to_aos<W><<<4 * 152, 256, 0, s>>>(soa, aos, n, stride);
+}
+// core flags from given core keys (restart): every list entry's core bit is
+// cleared, then each core key is found by binary search and flagged
+template <int W>
+__global__ void k_core_clear(Params P, int cur) {
+  const int64_t n = P.st->ndet[cur];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    P.flags[cur][i] &= (uint8_t)~F_CORE;
+}
+template <int W>
+__global__ void k_core_mark(Params P, int cur, unsigned* missing) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= P.ncore) return;
+  const int64_t n = P.st->ndet[cur];
+  const Key<W> k = load_key<W>(P.core_key, P.ncore, r);
+  const int64_t pos = lower_bound_main<W>(P.key[cur], P.cap, n, k);
+  if (pos < n && key_eq<W>(load_key<W>(P.key[cur], P.cap, pos), k)) P.flags[cur][pos] |= F_CORE;
+  else atomicOr(missing, 1u);
+}
+template <int W>
+void enqueue_core_mark(Engine& E, int cur, unsigned* missing, cudaStream_t s) {
+  k_core_clear<W><<<4 * 152, 256, 0, s>>>(E.P, cur);
+  if (E.P.ncore > 0) k_core_mark<W><<<(E.P.ncore + 255) / 256, 256, 0, s>>>(E.P, cur, missing);
 }
 
 template <int W>
@@ -311,6 +334,7 @@ Ops make_ops() {
   o.check_keys = &enqueue_check_keys<W>;
   o.keys_to_soa = &enqueue_keys_to_soa<W>;
   o.keys_to_aos = &enqueue_keys_to_aos<W>;
+  o.core_mark = &enqueue_core_mark<W>;
   o.core_hash = &enqueue_core_hash<W>;
   o.sel_hist = &enqueue_sel_hist<W>;
   o.sel_flags = &enqueue_sel_flags<W>;

@@ -70,6 +70,11 @@ class _Estimate(C.Structure):
                 ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64)]
 
 
+class _State(C.Structure):
+    _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_ref", C.c_int64), ("vary", C.c_int),
+                ("core_active", C.c_int), ("ncore", C.c_int64)]
+
+
 class _Diag(C.Structure):
     _fields_ = [("error_bits", C.c_uint32), ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64),
                 ("nbuckets", C.c_int64), ("bucket_main", C.c_int64), ("max_bucket_spawns", C.c_int64),
@@ -79,7 +84,8 @@ class _Diag(C.Structure):
 
 # names declared in include/hande.h, in order
 EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
-           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
+           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
+           "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
            "hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize",
            "hande_batch_destroy"]
 
@@ -122,7 +128,9 @@ def load(build_if_needed: bool = True):
         lib.hande_last_error.restype = C.c_char_p
         lib.hande_diagnostics.argtypes = [P, C.POINTER(_Diag)]
         lib.hande_estimate_noalloc.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
-        for name in EXPORTS[:10]:
+        lib.hande_get_state.argtypes = [P, C.POINTER(_State), u64p, C.c_int64]
+        lib.hande_set_state.argtypes = [P, C.POINTER(_State), u64p]
+        for name in EXPORTS[:12]:
             getattr(lib, name).restype = C.c_int
         lib.hande_batch_init.argtypes = [C.POINTER(_System), C.POINTER(_Qmc), C.c_int, C.POINTER(_Allocator), P,
                                          C.POINTER(P), C.POINTER(C.c_int)]
@@ -328,6 +336,29 @@ class Hande:
         self._check(self._lib.hande_set_walkers(self._h, k.ctypes.data_as(C.POINTER(C.c_uint64)),
                                                 p.ctypes.data_as(C.POINTER(C.c_int64)), hp, len(p)),
                     "hande_set_walkers")
+
+    def state(self):
+        """Restart snapshot beyond the walker list: (dict of the run state,
+        deterministic-space keys[ncore, W] ascending)."""
+        st = _State()
+        self._check(self._lib.hande_get_state(self._h, C.byref(st), None, 0), "hande_get_state")
+        keys = np.zeros((max(int(st.ncore), 1), self.W), dtype=np.uint64)
+        self._check(self._lib.hande_get_state(self._h, C.byref(st), keys.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                              len(keys)), "hande_get_state")
+        d = {name: getattr(st, name) for name, _ in _State._fields_}
+        return d, keys[:int(st.ncore)].copy()
+
+    def set_state(self, state: dict, core_keys=None) -> None:
+        """Restore a snapshot taken by state() (after set_walkers of its list)."""
+        st = _State()
+        for name, _ in _State._fields_:
+            setattr(st, name, state[name])
+        kp = None
+        if core_keys is not None and len(core_keys):
+            k = np.ascontiguousarray(np.asarray(core_keys, dtype=np.uint64).reshape(-1, self.W))
+            self._core_keep = k
+            kp = k.ctypes.data_as(C.POINTER(C.c_uint64))
+        self._check(self._lib.hande_set_state(self._h, C.byref(st), kp), "hande_set_state")
 
     def close(self) -> None:
         if self._h and self._batch is None:   # a batch's replica is freed with its batch
