@@ -194,11 +194,12 @@ def test_oversized_buckets_small_tiles(annihilation, tile):
     """Small annihilation tiles force many buckets through the oversized paths
     (block tiles: spawn-sampled sub-ranges, two-pass merge; one warp per bucket:
     batches of new keys in key order); lists stay bit-identical."""
-    # 16 x tile walkers on the reference (about one attempt in six spawns from
-    # it): the first iteration's single bucket receives more spawns than the tile
-    sysd, q = inputs.workload("molecule28", target_population=30000, semi_stoch_size=200,
+    # 64 x tile walkers on the reference (about one attempt in fifteen spawns
+    # from it: most heat-bath draws land on occupied orbitals): the first
+    # iteration's single bucket receives several times more spawns than the tile
+    sysd, q = inputs.workload("molecule28", target_population=1e5, semi_stoch_size=200,
                               semi_stoch_start=30, tile_capacity=tile, annihilation=annihilation,
-                              init_pop=16 * tile)
+                              init_pop=64 * tile)
     g = hande.Hande(sysd, q)
     c = oracle.Oracle(sysd, q)
     seen = deferred = 0
