@@ -266,7 +266,8 @@ def run_ours(args, rank, world):
     t_e2e = time.perf_counter() - t0
     e2e = {"value": att_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
            "d2h_bytes_per_step": int(d2h / e2e_steps),
-           "step": "set_walkers(host list) + iterate(1) + get_walkers + estimators"}
+           "step": "set_walkers(host list; the deterministic space is kept, not rebuilt) + iterate(1) + "
+                   "get_walkers + estimators"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -293,6 +294,73 @@ def run_ours(args, rank, world):
         k_h, p_h, _, _ = eng.walkers()
         out["cpu_baseline"] = cpu_baseline(sysd, q, k_h, p_h)
     eng.close()
+    if rank == 0 and not args.no_configs:
+        out["configs"] = config_lines(dev)
+    return out
+
+
+def config_lines(dev):
+    """Throughput of the two smaller configurations on the same engine (extra
+    keys of the default line; each timed with CUDA events on the engine's
+    stream, graph launches, no host synchronisation inside the timed region):
+      hubbard8  1D Hubbard ring, 8 sites, 4+4 electrons, U/t = 4, integer
+                walkers, tau 0.01, target 1e4: the whole 2000-iteration run
+                (the population grows from 500 walkers inside it);
+      ueg14     UEG 14 electrons in 38 plane waves (128-bit keys), r_s = 1,
+                initiator n_a = 3, real weights, tau 0.002, target 1e6 walkers:
+                grown from 1e4 walkers until the shift varies (the population
+                reached 1e6), 200 more iterations, then 400 timed iterations."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande, inputs
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def timed(eng, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        eng.iterate(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sysd, q = inputs.workload("hubbard8")
+    eng = hande.Hande(sysd, q)
+    ms = timed(eng, 2000)
+    r = eng.estimators()
+    eng.close()
+    out["hubbard8"] = {"iterations": 2000, "us_per_iteration": ms * 1e3 / 2000,
+                       "attempts_per_s": float(r["natt"].sum()) / (ms / 1e3),
+                       "final_walkers": float(r["nw_post"][-1]) / 2 ** 32,
+                       "final_determinants": int(r["ndet"][-1]),
+                       "workload": "1D Hubbard ring L=8, 4+4 electrons, t=1, U=4, integer walkers, tau=0.01, "
+                                   "target 1e4, 500 walkers on the Neel determinant at the start; all 2000 "
+                                   "iterations timed"}
+
+    sysd, q = inputs.workload("ueg14", target_population=1e6, init_pop=1e4, state_capacity=2_500_000,
+                              spawn_capacity=4_000_000)
+    eng = hande.Hande(sysd, q)
+    grown = 0
+    while grown < 20000:
+        eng.iterate(250)
+        grown += 250
+        if eng.estimators()["shift"][-1] != 0.0:
+            break
+    eng.iterate(200)
+    eng.synchronize()
+    eng.estimators()
+    ms = timed(eng, 400)
+    r = eng.estimators()
+    eng.close()
+    out["ueg14"] = {"iterations": 400, "first_timed_iteration": int(r["iter"][0]),
+                    "ms_per_iteration": ms / 400, "attempts_per_s": float(r["natt"].sum()) / (ms / 1e3),
+                    "annihilated_spawns_per_s": float(r["nspawn"].sum()) / (ms / 1e3),
+                    "mean_walkers": float(r["nw_post"].mean()) / 2 ** 32,
+                    "mean_determinants": float(r["ndet"].mean()),
+                    "workload": "UEG 14 electrons in 38 spatial plane waves (76 spin orbitals, 128-bit keys), "
+                                "r_s=1, initiator n_a=3, real weights, spawn_cutoff 0.1, tau=0.002, target 1e6 "
+                                "walkers; grown from 1e4 walkers until the shift varies, +200 iterations"}
     return out
 
 
@@ -438,6 +506,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the Hubbard and UEG lines")
     ap.add_argument("--profile-case", action="store_true",
                     help="small synthetic-start case for ncu captures (no timing output)")
     ap.add_argument("--batched", type=int, default=0,

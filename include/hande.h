@@ -188,9 +188,12 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
 
 /* Replace the walker list with n entries (keys strictly ascending, each with
  * nalpha + nbeta electrons, the reference determinant present).  hdiag may be
- * NULL, in which case H_ii - E_ref is evaluated on the device.  If the
- * deterministic space is in use, or semi_stoch_start == 0, it is chosen again
- * from this list.  The iteration counter is kept.  Synchronises. */
+ * NULL, in which case H_ii - E_ref is evaluated on the device.  Before the
+ * first iteration with semi_stoch_start == 0 the deterministic space is chosen
+ * from this list; an active deterministic space is kept (its matrix is not
+ * rebuilt) and must lie in the new list (else HANDE_ERR_INVALID and the space
+ * is off; hande_set_state installs a different one).  The iteration counter is
+ * kept.  Synchronises. */
 hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
                                int64_t n);
 

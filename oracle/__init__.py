@@ -239,6 +239,8 @@ class Oracle:
         k, kp = _u64(np.asarray(keys).reshape(-1, self.W))
         p = np.ascontiguousarray(pops, dtype=np.int64)
         rc = self._lib.orc_set_walkers(self._h, kp, p.ctypes.data_as(C.POINTER(C.c_int64)), len(p))
+        if rc == -2:
+            raise ValueError("the list lacks a determinant of the deterministic space")
         if rc != 0:
             raise ValueError("walker keys must be strictly ascending")
 

@@ -1117,8 +1117,19 @@ int orc_set_walkers(void* h, const uint64_t* keys, const int64_t* pops, int64_t 
         if (!c->main.empty() && det_cmp(c->main.back().key, wk.key, c->W) >= 0) return -1;
         c->main.push_back(wk);
     }
-    /* start_iteration 0: the deterministic space is taken from the list as given */
-    if (c->core_size > 0 && c->core_start == 0 && c->iter == 0) select_core(*c);
+    /* start_iteration 0: the deterministic space is taken from the list as
+     * given before the first iteration; later a chosen space is kept and its
+     * members flagged in the new list, which must hold all of them */
+    if (c->core_size > 0 && c->core_start == 0 && c->iter == 0) {
+        select_core(*c);
+    } else if (!c->core.empty()) {
+        int64_t found = 0;
+        for (size_t i = 0; i < c->main.size(); ++i) {
+            c->main[i].core = in_core(*c, c->main[i].key) ? 1 : 0;
+            found += c->main[i].core;
+        }
+        if (found != (int64_t)c->core.size()) return -2;
+    }
     return 0;
 }
 

@@ -946,13 +946,30 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     if (hdiag) CK(cudaMemcpyAsync(E.P.hdiag[cur], hdiag, n * 8, cudaMemcpyHostToDevice, E.stream));
     else E.ops.hdiag(E, cur, n, E.stream);
     CK(cudaGetLastError());
-    // the deterministic space refers to the old list: choose it again from the
-    // new one if it is in use (or chosen at the start)
-    const bool reselect = E.core_size > 0 && (E.core_start == 0 || E.core_active);
-    E.core_active = false;
-    E.P.ncore = 0;
-    drop_graphs(E, 1);
-    if (reselect) select_core(E);
+    // before the first iteration with semi_stoch_start == 0 the deterministic
+    // space is chosen from the new list; later an active space is kept (its
+    // matrix unchanged) and its members flagged in the new list, which must
+    // hold all of them
+    if (E.core_size > 0 && E.core_start == 0 && E.host_iter == 0) {
+      E.core_active = false;
+      E.P.ncore = 0;
+      drop_graphs(E, 1);
+      select_core(E);
+    } else if (E.core_active && E.P.ncore > 0) {
+      CK(cudaMemsetAsync(E.check_word, 0, sizeof(unsigned), E.stream));
+      E.ops.core_mark(E, cur, E.check_word, E.stream);
+      CK(cudaGetLastError());
+      unsigned missing = 0;
+      CK(cudaMemcpyAsync(&missing, E.check_word, sizeof missing, cudaMemcpyDeviceToHost, E.stream));
+      CK(cudaStreamSynchronize(E.stream));
+      if (missing) {
+        E.core_active = false;
+        E.P.ncore = 0;
+        drop_graphs(E, 1);
+        throw Fail{HANDE_ERR_INVALID,
+                   "the list lacks a deterministic-space determinant (hande_set_state replaces the space)"};
+      }
+    }
     CK(cudaStreamSynchronize(E.stream));
     return HANDE_OK;
   });
