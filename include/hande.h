@@ -329,6 +329,23 @@ hande_status hande_batch_synchronize(hande_batch* b);
 /* Free all replicas, their streams and the batch (safe on NULL). */
 void hande_batch_destroy(hande_batch* b);
 
+/* ---------------------------------------------------------------- tensor cores
+ * The paper has no learned part: its excitation generators are uniform or
+ * heat-bath tables (Sec. 2.1, Sec. 4).  The learned excitation proposal of this
+ * library (a small MLP whose output becomes the generator's selection table)
+ * runs its dense layers on the tensor cores through this GEMM.
+ *
+ * D[m][n] = sum_k A[m][k] B[n][k] for DEVICE arrays: A (m x k) and B (n x k)
+ * row-major BF16 (raw 16-bit patterns) with leading dimensions lda, ldb >= k
+ * that are multiples of 8 and rows starting on 16-byte boundaries; D (m x n)
+ * row-major FP32 with leading dimension ldd >= n.  Products of BF16 values are
+ * exact and are accumulated in FP32 by tcgen05 MMAs (128 x 128 output tiles).
+ * Runs on `cuda_stream` (a cudaStream_t) and synchronises it.
+ * HANDE_ERR_INVALID on bad sizes/alignment, HANDE_ERR_TIMEOUT if a bounded
+ * device-side wait gave up, HANDE_ERR_CUDA on a failed CUDA call. */
+hande_status hande_gemm_bf16(const uint16_t* d_a, int64_t lda, const uint16_t* d_b, int64_t ldb, float* d_d,
+                             int64_t ldd, int m, int n, int k, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,133 @@
+// mlp.cu -- tensor-core GEMM entry point and (below) the learned excitation
+// proposal built on it.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/hande.h"
+#include "tc_gemm.cuh"
+
+namespace hande {
+namespace tc {
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+std::mutex g_mu;
+EncodeTiledFn g_encode = nullptr;
+bool g_attr_set[256] = {};
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda)
+EncodeTiledFn encoder() {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<EncodeTiledFn>(fn);
+    else
+      cudaGetLastError();
+  }
+  return g_encode;
+}
+
+}  // namespace
+
+// 2D BF16 tensor {inner, outer} with row stride ld (elements), box {64, box_outer},
+// 128-byte swizzle, zero fill outside
+bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld, uint32_t box_outer) {
+  EncodeTiledFn enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Validated launch of D = A B^T (see tc_gemm.cuh); false with a message on bad input
+bool launch_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* D, int64_t ldd, int M,
+                 int N, int K, unsigned* err, cudaStream_t s, const char** why) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !D || !err) {
+    *why = "bad GEMM sizes or pointers";
+    return false;
+  }
+  if (lda < K || ldb < K || ldd < N || (lda & 7) || (ldb & 7) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
+    *why = "GEMM operands need 16-byte aligned rows (leading dimensions multiples of 8, >= K)";
+    return false;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    *why = "no current CUDA device";
+    return false;
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_attr_set[dev]) {
+      if (cudaFuncSetAttribute(k_gemm_bf16_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        *why = "cannot reserve the GEMM's shared memory";
+        return false;
+      }
+      g_attr_set[dev] = true;
+    }
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kBM) ||
+      !make_map(&mb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, kBN)) {
+    *why = "cuTensorMapEncodeTiled failed";
+    return false;
+  }
+  dim3 grid((unsigned)((N + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM));
+  k_gemm_bf16_tn<<<grid, kThreads, kSmemBytes, s>>>(ma, mb, D, ldd, M, N, K, err);
+  if (cudaGetLastError() != cudaSuccess) {
+    *why = "GEMM launch failed";
+    return false;
+  }
+  return true;
+}
+
+namespace {
+__device__ unsigned g_gemm_err;   // error word of hande_gemm_bf16 calls
+}
+
+}  // namespace tc
+}  // namespace hande
+
+using namespace hande;
+
+extern "C" hande_status hande_gemm_bf16(const uint16_t* d_a, int64_t lda, const uint16_t* d_b, int64_t ldb,
+                                        float* d_d, int64_t ldd, int m, int n, int k, void* cuda_stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  unsigned* err = nullptr;
+  if (cudaGetSymbolAddress((void**)&err, tc::g_gemm_err) != cudaSuccess) {
+    cudaGetLastError();
+    return HANDE_ERR_CUDA;
+  }
+  const unsigned zero = 0;
+  if (cudaMemcpyAsync(err, &zero, sizeof zero, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return HANDE_ERR_CUDA;
+  }
+  const char* why = "";
+  if (!tc::launch_gemm(d_a, lda, d_b, ldb, d_d, ldd, m, n, k, err, s, &why))
+    return (m < 1 || n < 1 || k < 1 || lda < k || ldb < k || ldd < n || (lda & 7) || (ldb & 7)) ? HANDE_ERR_INVALID
+                                                                                              : HANDE_ERR_CUDA;
+  unsigned e = 0;
+  if (cudaMemcpyAsync(&e, err, sizeof e, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return HANDE_ERR_CUDA;
+  }
+  return e ? HANDE_ERR_TIMEOUT : HANDE_OK;
+}

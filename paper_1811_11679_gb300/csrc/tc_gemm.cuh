@@ -1,0 +1,275 @@
+// tc_gemm.cuh -- BF16 GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   D[m][n] = sum_k A[m][k] B[n][k]        (A: M x K, B: N x K, both K-major
+//                                           BF16 row-major; D: FP32)
+//
+// One CTA computes one 128 x 128 tile of D.  The K dimension is taken in
+// chunks of 64 elements (128 bytes): a TMA tile load brings the A and B chunk
+// of a stage into shared memory in the 128-byte-swizzled K-major layout the
+// tensor core reads, four stages deep; one thread issues the MMAs (four
+// 128 x 128 x 16 tcgen05.mma per chunk, FP32 accumulators in tensor memory) and
+// commits each stage to an mbarrier that frees it for the next TMA load.  When
+// the last MMA has completed, the four warps read the accumulator rows they own
+// (tcgen05.ld, 32 lanes x 32 columns at a time) and store them.  Rows, columns
+// and K beyond the matrix are zero-filled by the TMA and masked in the store,
+// so any M, N, K >= 1 work (leading dimensions: multiples of 8 elements).
+//
+// Every wait is bounded: a wait that gives up sets bit ERR_MMA_TIMEOUT of *err,
+// the kernel skips its remaining work, waits (bounded) for its own MMAs and
+// frees its tensor memory.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace hande {
+namespace tc {
+
+constexpr int kBM = 128;        // tile rows (MMA M)
+constexpr int kBN = 128;        // tile columns (MMA N)
+constexpr int kBK = 64;         // K per stage: 64 BF16 = 128 bytes = one swizzle row
+constexpr int kMmaK = 16;       // K of one tcgen05.mma kind::f16
+constexpr int kStages = 4;
+constexpr int kThreads = 128;   // four warps: the 128 TMEM lanes
+constexpr uint32_t kTileABytes = kBM * kBK * 2;
+constexpr uint32_t kTileBBytes = kBN * kBK * 2;
+constexpr uint32_t kTmemCols = kBN;   // FP32 accumulator: one column per output column
+constexpr unsigned ERR_MMA_TIMEOUT = 1u;
+// dynamic shared memory: 1024-byte aligned stages + barriers
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kTileABytes + kTileBBytes) + 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ------------------------------------------------------------------ mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait for the phase with the given parity to complete: gives up after
+// about one second of the global timer
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 15) == 15 && global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// ------------------------------------------------------------------ TMA
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// ------------------------------------------------------------------ tcgen05
+// shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// layout written by a TMA load with CU_TENSOR_MAP_SWIZZLE_128B (rows of 128
+// bytes, groups of 8 rows 1024 bytes apart); the stage base is 1024-aligned
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // bits  0-13: start address / 16
+                                             // bits 16-29: leading byte offset (unused: the
+                                             // 32-byte K step stays inside one swizzle row)
+  d |= (uint64_t)(1024 >> 4) << 32;          // bits 32-45: stride byte offset / 16 (8-row groups)
+  d |= (uint64_t)1 << 46;                    // bits 46-47: descriptor version 1
+  d |= (uint64_t)2 << 61;                    // bits 61-63: 128-byte swizzle
+  return d;
+}
+// instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
+  return (1u << 4)                         // D format: F32
+         | (1u << 7)                       // A format: BF16
+         | (1u << 10)                      // B format: BF16
+         | ((uint32_t)(n >> 3) << 17)      // N / 8
+         | ((uint32_t)(m >> 4) << 24);     // M / 16
+}
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on the mbarrier once every MMA issued so far by this thread completed
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// whole warp: allocate ncols tensor-memory columns, address written to *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// whole warp: 32 consecutive 32-bit columns of the warp's 32 lanes (lane l gets row l)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ the GEMM
+// grid (ceil(N / 128), ceil(M / 128)), kThreads threads, kSmemBytes dynamic
+// shared memory.  tmA: A as a 2D tensor {K, M} (row stride lda * 2 bytes), box
+// {64, 128}; tmB likewise for B {K, N}.  D row stride ldd (FP32).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* D,
+                   int64_t ldd, int M, int N, int K, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = base;
+  unsigned char* sB = base + (size_t)kStages * kTileABytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)kStages * kTileBBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_fail;
+
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  const int m0 = (int)blockIdx.y * kBM, n0 = (int)blockIdx.x * kBN;
+  const int nk = (K + kBK - 1) / kBK;
+
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+    auto load = [&](int kc, int s) {
+      mbar_expect_tx(&full[s], kTileABytes + kTileBBytes);
+      tma_load_2d(sA + (size_t)s * kTileABytes, &tmA, &full[s], kc * kBK, m0);
+      tma_load_2d(sB + (size_t)s * kTileBBytes, &tmB, &full[s], kc * kBK, n0);
+    };
+    const int pre = nk < kStages ? nk : kStages;
+    for (int kc = 0; kc < pre; ++kc) load(kc, kc);
+    int issued = pre, consumed = 0;
+    bool ok = true;
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int s = kc % kStages;
+      if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
+        ok = false;
+        break;
+      }
+      consumed = kc + 1;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + (size_t)s * kTileABytes);
+      const uint32_t b0 = smem_u32(sB + (size_t)s * kTileBBytes);
+#pragma unroll
+      for (int j = 0; j < kBK / kMmaK; ++j) {
+        // K step j: 16 BF16 = 32 bytes further along each 128-byte row
+        tc_mma(tmem, sw128_kmajor_desc(a0 + 32u * j), sw128_kmajor_desc(b0 + 32u * j), idesc,
+               (kc > 0 || j > 0) ? 1u : 0u);
+      }
+      tc_commit(&empty[s]);
+      // refill the stage the previous chunk used once its MMAs have read it
+      const int kp = kc - 1;
+      if (kp >= 0 && kp + kStages < nk) {
+        const int sp = kp % kStages;
+        if (!mbar_wait(&empty[sp], (uint32_t)((kp / kStages) & 1))) {
+          ok = false;
+          break;
+        }
+        load(kp + kStages, sp);
+        issued = kp + kStages + 1;
+      }
+    }
+    if (!ok) {
+      s_fail = 1;
+      atomicOr(err, ERR_MMA_TIMEOUT);
+      // let the tile loads still in flight land before the CTA exits (bounded)
+      for (int kc = consumed; kc < issued; ++kc) mbar_wait(&full[kc % kStages], (uint32_t)((kc / kStages) & 1));
+    }
+    tc_commit(done);   // completes when every MMA issued above has completed
+  }
+  __syncwarp();
+  // uniform over the CTA (the accumulator reads below are warp-collective)
+  const bool finished = __syncthreads_and(mbar_wait(done, 0) ? 1 : 0) != 0;
+  tc_fence_after();
+  if (!finished) {
+    if (threadIdx.x == 0) atomicOr(err, ERR_MMA_TIMEOUT);
+  } else if (!s_fail) {
+    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kBN; c0 += 32) {
+      if (n0 + c0 >= N) break;
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (row < M) {
+        float* out = D + (int64_t)row * ldd + n0 + c0;
+        const int nc = N - (n0 + c0) < 32 ? N - (n0 + c0) : 32;
+        if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            *reinterpret_cast<float4*>(out + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+                                                              __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i < nc) out[i] = __uint_as_float(r[i]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem, kTmemCols);
+}
+
+}  // namespace tc
+}  // namespace hande

@@ -87,7 +87,7 @@ EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_s
            "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
            "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
            "hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize",
-           "hande_batch_destroy"]
+           "hande_batch_destroy", "hande_gemm_bf16"]
 
 _lib = None
 _lock = threading.Lock()
@@ -143,6 +143,8 @@ def load(build_if_needed: bool = True):
         lib.hande_batch_destroy.restype = None
         for name in ("hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_synchronize"):
             getattr(lib, name).restype = C.c_int
+        lib.hande_gemm_bf16.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P]
+        lib.hande_gemm_bf16.restype = C.c_int
         _lib = lib
         return lib
 
@@ -376,6 +378,27 @@ class Hande:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def gemm_bf16(a, b, out=None, stream=None):
+    """D = A B^T on the tensor cores (include/hande.h, hande_gemm_bf16) for
+    CUDA tensors: a (m x k) and b (n x k) bfloat16, row-major with unit column
+    stride; returns (or fills) a float32 (m x n) tensor."""
+    import torch
+    lib = load()
+    m, k = a.shape
+    n, k2 = b.shape
+    if k2 != k or a.dtype != torch.bfloat16 or b.dtype != torch.bfloat16 or a.stride(1) != 1 or b.stride(1) != 1:
+        raise ValueError("a (m x k) and b (n x k) must be bfloat16 with unit column stride")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float32, device=a.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(a.device).cuda_stream
+    rc = lib.hande_gemm_bf16(C.c_void_p(a.data_ptr()), a.stride(0), C.c_void_p(b.data_ptr()), b.stride(0),
+                             C.c_void_p(out.data_ptr()), out.stride(0), m, n, k, C.c_void_p(int(stream)))
+    if rc != 0:
+        raise HandeError(rc, "hande_gemm_bf16")
+    return out
 
 
 class HandeBatch:
