@@ -60,7 +60,7 @@ class _Qmc(C.Structure):
                 ("shift_period", C.c_int), ("initiator", C.c_int),
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int),
                 ("semi_stoch_start", C.c_int),
-                ("seed", C.c_uint64), ("replica", C.c_uint64)]
+                ("seed", C.c_uint64), ("replica", C.c_uint64), ("excit_gen", C.c_int)]
 
 
 def _load():
@@ -109,6 +109,10 @@ def _load():
         lib.orc_ueg_basis.restype = C.c_int
         lib.orc_core.argtypes = [P, u64p, C.c_int64]
         lib.orc_core.restype = C.c_int64
+        lib.orc_set_proposal.argtypes = [P, C.POINTER(C.c_uint32)]
+        lib.orc_set_proposal.restype = C.c_int
+        lib.orc_proposal_mask.argtypes = [P, C.POINTER(C.c_uint8)]
+        lib.orc_proposal_mask.restype = C.c_int
         lib.orc_get_state.argtypes = [P, i64p, dp, i64p, C.POINTER(C.c_int)]
         lib.orc_get_state.restype = None
         lib.orc_set_state.argtypes = [P, C.c_int64, C.c_double, C.c_int64, C.c_int, u64p, C.c_int64]
@@ -193,11 +197,13 @@ class Oracle:
         q.semi_stoch_start = int(qmc.get("semi_stoch_start", 0))
         q.seed = int(qmc["seed"])
         q.replica = int(qmc.get("replica", 0))
+        q.excit_gen = int(qmc.get("excit_gen", 0))
         h = lib.orc_create(C.byref(s), C.byref(q))
         if not h:
             raise ValueError("oracle rejected the system/qmc parameters")
         self._h = h
         self.W = s.key_words
+        self._norb = s.norb
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -338,3 +344,18 @@ class Oracle:
                                      int(state["vary"]), kp, n)
         if rc != 0:
             raise ValueError("a deterministic-space key is not in the walker list")
+
+    def proposal_mask(self) -> np.ndarray:
+        """UEG: drawable particle orbitals of the proposal table, bool[2 M^2, M]
+        (row r = (I M + J) 2 + same-spin)."""
+        M = int(self._norb)
+        m = np.zeros((2 * M * M, M), dtype=np.uint8)
+        if self._lib.orc_proposal_mask(self._h, m.ctypes.data_as(C.POINTER(C.c_uint8))) != 0:
+            raise ValueError("no proposal table for this system")
+        return m.astype(bool)
+
+    def set_proposal(self, q) -> None:
+        """Install the integer weights q[2 M^2, M] of the proposal-table generator."""
+        a = np.ascontiguousarray(q, dtype=np.uint32)
+        if self._lib.orc_set_proposal(self._h, a.ctypes.data_as(C.POINTER(C.c_uint32))) != 0:
+            raise ValueError("proposal table rejected (weights >= 1 exactly where drawable, <= 2^24)")

@@ -287,6 +287,10 @@ struct Ctx {
     uint32_t psingle_thr;
     double p_single, p_double;
     std::vector<std::vector<HBEntry>> hb;   /* per pair index of (p<q) */
+    /* proposal-table generator (UEG): per row r = (I M + J) 2 + same-spin,
+     * cumulative integer weights over the particle orbital A (empty = off) */
+    int excit_gen;
+    std::vector<uint32_t> ptab_cum;
     /* qmc */
     double tau, target, zeta, cutoff, init_pop, n_a;
     int period, initiator, real_amp, core_size, core_start;
@@ -579,9 +583,61 @@ Excit gen_heat_bath(const Ctx& c, const Det& d, const uint64_t w[4]) {
     return e;
 }
 
+/* UEG doubles from a proposal table (the learned proposal's selection table).
+ * The occupied pair (i < j) is drawn uniformly as in gen_ueg; the particle
+ * orbital A (spin of i) is drawn from the integer weights q_r[A] of the row
+ * r = (I M + J) 2 + [spin i == spin j] by inverse CDF over their cumulative
+ * sums (Q_r = the row total, x = floor(w2 Q_r / 2^64), A = the first index whose
+ * cumulative sum exceeds x); b follows from momentum conservation.  The child
+ * {a, b} of a same-spin pair is also drawn through A' = B, so
+ *   p_gen = [1 / C(N,2)] (q_A + [same spin] q_B) / Q_r,
+ * exact in the integers; 1/p_gen = inv_a inv_b with inv_a = C(N,2) and
+ * inv_b = Q_r / (q_A + [same] q_B) (one rounding).  Null when a or b is
+ * occupied. */
+inline uint32_t ptab_weight(const Ctx& c, size_t row, int A) {
+    const uint32_t* cum = &c.ptab_cum[row * (size_t)c.norb];
+    return cum[A] - (A > 0 ? cum[A - 1] : 0u);
+}
+
+Excit gen_ueg_table(const Ctx& c, const Det& d, const uint64_t w[4]) {
+    Excit e;
+    e.null = true;
+    std::vector<int> o = occ_list(d, c.nspin);
+    int n = (int)o.size();
+    uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+    int ii, jj;
+    unrank_pair(draw_index(w[1], npairs), ii, jj);
+    int p = o[ii], q = o[jj];
+    int I = p >> 1, J = q >> 1, same = (p & 1) == (q & 1) ? 1 : 0;
+    size_t row = ((size_t)I * c.norb + J) * 2 + same;
+    const uint32_t* cum = &c.ptab_cum[row * (size_t)c.norb];
+    uint32_t Q = cum[c.norb - 1];
+    if (Q == 0) return e;
+    uint64_t x = draw_index(w[2], (uint64_t)Q);
+    int A = 0;
+    while (!((uint64_t)cum[A] > x)) ++A;
+    int B = ueg_orb_of(c, c.kvec[3 * I] + c.kvec[3 * J] - c.kvec[3 * A],
+                       c.kvec[3 * I + 1] + c.kvec[3 * J + 1] - c.kvec[3 * A + 1],
+                       c.kvec[3 * I + 2] + c.kvec[3 * J + 2] - c.kvec[3 * A + 2]);
+    if (B < 0) return e;   /* not drawn: such entries have weight 0 */
+    int a = 2 * A + (p & 1), b = 2 * B + (q & 1);
+    if (a == b || occ_bit(d, a) || occ_bit(d, b)) return e;
+    uint32_t qab = ptab_weight(c, row, A) + (same ? ptab_weight(c, row, B) : 0u);
+    e.pgen = ((double)qab / (double)Q) / (double)npairs;
+    e.inv_a = (double)npairs;
+    e.inv_b = (double)Q / (double)qab;
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    e.hij = h_double(c, d, p, q, lo, hi);
+    e.child = d;
+    flip_bit(e.child, p); flip_bit(e.child, q);
+    flip_bit(e.child, a); flip_bit(e.child, b);
+    e.null = false;
+    return e;
+}
+
 Excit generate(const Ctx& c, const Det& d, const uint64_t w[4]) {
     if (c.kind == SYS_HUBBARD) return gen_hubbard(c, d, w);
-    if (c.kind == SYS_UEG) return gen_ueg(c, d, w);
+    if (c.kind == SYS_UEG) return c.excit_gen == 1 ? gen_ueg_table(c, d, w) : gen_ueg(c, d, w);
     return gen_heat_bath(c, d, w);
 }
 
@@ -951,6 +1007,7 @@ typedef struct {
     double p_single;
     int shift_period, initiator, real_amplitudes, semi_stoch_size, semi_stoch_start;
     uint64_t seed, replica;
+    int excit_gen;      /* 0: the system's generator; 1: proposal table (UEG) */
 } orc_qmc;
 
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
@@ -960,6 +1017,28 @@ void orc_fixed_term(int64_t n, double h, int64_t* hi, uint64_t* lo) {
     i128 v = fixed_term(n, h);
     *hi = (int64_t)(v >> 64);
     *lo = (uint64_t)v;
+}
+
+/* a particle orbital A is drawable in row (I, J, same) when its momentum
+ * partner B = k_I + k_J - k_A is in the basis and, for a same-spin pair, B != A */
+static bool ptab_valid(const Ctx& c, int I, int J, int same, int A) {
+    int B = ueg_orb_of(c, c.kvec[3 * I] + c.kvec[3 * J] - c.kvec[3 * A],
+                       c.kvec[3 * I + 1] + c.kvec[3 * J + 1] - c.kvec[3 * A + 1],
+                       c.kvec[3 * I + 2] + c.kvec[3 * J + 2] - c.kvec[3 * A + 2]);
+    return B >= 0 && !(same && B == A);
+}
+
+/* install integer weights q[rows][M] (rows = 2 M^2) as cumulative sums */
+static void set_ptab(Ctx& c, const uint32_t* q) {
+    size_t rows = (size_t)c.norb * c.norb * 2;
+    c.ptab_cum.assign(rows * (size_t)c.norb, 0u);
+    for (size_t r = 0; r < rows; ++r) {
+        uint32_t s = 0;
+        for (int A = 0; A < c.norb; ++A) {
+            s += q[r * (size_t)c.norb + A];
+            c.ptab_cum[r * (size_t)c.norb + A] = s;
+        }
+    }
 }
 
 static bool setup_ueg(Ctx& c) {
@@ -1038,6 +1117,8 @@ void* orc_create(const orc_system* s, const orc_qmc* q) {
     c->core_start = q->semi_stoch_start;
     c->seed = q->seed;
     c->replica = q->replica;
+    c->excit_gen = q->excit_gen;
+    if (c->excit_gen != 0 && !(c->excit_gen == 1 && c->kind == SYS_UEG)) { delete c; return nullptr; }
     /* thresholds in fixed point, saturated at the int64 range */
     c->target_fixed = c->target * 4294967296.0 >= 9223372036854775807.0
                           ? INT64_MAX : llrint(c->target * 4294967296.0);
@@ -1057,7 +1138,20 @@ void* orc_create(const orc_system* s, const orc_qmc* q) {
         for (int k = 0; k < c->nalpha; ++k) flip_bit(c->d0, 2 * (2 * k) + 0);
         for (int k = 0; k < c->nbeta; ++k) flip_bit(c->d0, 2 * (2 * k + 1) + 1);
     } else {
-        if (c->kind == SYS_UEG) setup_ueg(*c);
+        if (c->kind == SYS_UEG) {
+            setup_ueg(*c);
+            if (c->excit_gen == 1) {
+                /* until a table is given: weight 1 on every valid particle orbital */
+                std::vector<uint32_t> q((size_t)c->norb * c->norb * 2 * c->norb, 0u);
+                for (int I = 0; I < c->norb; ++I)
+                    for (int J = 0; J < c->norb; ++J)
+                        for (int same = 0; same < 2; ++same)
+                            for (int A = 0; A < c->norb; ++A)
+                                if (ptab_valid(*c, I, J, same, A))
+                                    q[(((size_t)I * c->norb + J) * 2 + same) * c->norb + A] = 1;
+                set_ptab(*c, q.data());
+            }
+        }
         for (int k = 0; k < c->nalpha; ++k) flip_bit(c->d0, 2 * k);
         for (int k = 0; k < c->nbeta; ++k) flip_bit(c->d0, 2 * k + 1);
         if (c->kind == SYS_MOLECULE) build_heat_bath(*c);
@@ -1214,6 +1308,26 @@ int64_t orc_enumerate(void* h, const uint64_t* key, uint64_t* children, double* 
                 Excit e = generate(*c, d, w);
                 add(e.null ? nullptr : &e.child, 1.0 / (2.0 * n));
             }
+    } else if (c->kind == SYS_UEG && c->excit_gen == 1) {
+        uint64_t npairs = (uint64_t)n * (n - 1) / 2;
+        for (uint64_t P = 0; P < npairs; ++P) {
+            int ii, jj;
+            unrank_pair(P, ii, jj);
+            int p = o[ii], q = o[jj];
+            size_t row = (((size_t)(p >> 1)) * c->norb + (q >> 1)) * 2 + ((p & 1) == (q & 1) ? 1 : 0);
+            uint32_t Q = c->ptab_cum[row * (size_t)c->norb + c->norb - 1];
+            for (int A = 0; A < c->norb; ++A) {
+                uint32_t qa = ptab_weight(*c, row, A);
+                if (qa == 0) continue;
+                /* the smallest word drawing x = cum[A] - qa, i.e. orbital A */
+                uint64_t xlo = (uint64_t)c->ptab_cum[row * (size_t)c->norb + A] - qa;
+                uint64_t w[4] = {0, 0, 0, 0};
+                w[1] = (uint64_t)((((u128)P << 64) + npairs - 1) / npairs);
+                w[2] = (uint64_t)((((u128)xlo << 64) + (uint64_t)Q - 1) / (uint64_t)Q);
+                Excit e = generate(*c, d, w);
+                add(e.null ? nullptr : &e.child, ((double)qa / (double)Q) / (double)npairs);
+            }
+        }
     } else if (c->kind == SYS_UEG) {
         uint64_t npairs = (uint64_t)n * (n - 1) / 2;
         for (uint64_t P = 0; P < npairs; ++P)
@@ -1275,6 +1389,38 @@ int orc_ueg_basis(void* h, int* kvec, double* box) {
     for (int i = 0; i < 3 * c->norb; ++i) kvec[i] = c->kvec[(size_t)i];
     *box = c->box;
     return c->norb;
+}
+
+/* Proposal table of the UEG table generator: q[2 M^2][M] integer weights,
+ * row r = (I M + J) 2 + same-spin.  A weight must be >= 1 exactly where the
+ * particle orbital is drawable (ptab_valid) and 0 elsewhere, each <= 2^24.
+ * Returns 0, or -1 for a system without the table generator or a bad table. */
+int orc_set_proposal(void* h, const uint32_t* q) {
+    Ctx* c = (Ctx*)h;
+    if (c->kind != SYS_UEG || c->excit_gen != 1) return -1;
+    for (int I = 0; I < c->norb; ++I)
+        for (int J = 0; J < c->norb; ++J)
+            for (int same = 0; same < 2; ++same)
+                for (int A = 0; A < c->norb; ++A) {
+                    uint32_t v = q[(((size_t)I * c->norb + J) * 2 + same) * c->norb + A];
+                    bool ok = ptab_valid(*c, I, J, same, A);
+                    if (ok ? (v < 1 || v > (1u << 24)) : v != 0) return -1;
+                }
+    set_ptab(*c, q);
+    return 0;
+}
+
+/* drawable particle orbitals: mask[2 M^2][M] (1 = drawable) */
+int orc_proposal_mask(void* h, uint8_t* mask) {
+    Ctx* c = (Ctx*)h;
+    if (c->kind != SYS_UEG) return -1;
+    for (int I = 0; I < c->norb; ++I)
+        for (int J = 0; J < c->norb; ++J)
+            for (int same = 0; same < 2; ++same)
+                for (int A = 0; A < c->norb; ++A)
+                    mask[(((size_t)I * c->norb + J) * 2 + same) * c->norb + A] =
+                        ptab_valid(*c, I, J, same, A) ? 1 : 0;
+    return 0;
 }
 
 /* Restart (Sec. 3.1: a restarted calculation follows the same Markov chain).
