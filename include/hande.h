@@ -114,6 +114,11 @@ typedef struct {
                                  bucket), 1 = block tiles, 2 = one warp per bucket (large
                                  or overflowing buckets go to block tiles on that path);
                                  every choice gives the same walker list */
+  int excit_gen;              /* excitation generator (the paper's `excit_gen`): 0 = the
+                                 system's own (HUBBARD and UEG uniform, MOLECULE heat-bath);
+                                 1 = UEG proposal table (the learned proposal's table, see
+                                 hande_set_proposal / hande_learn_proposal), which starts
+                                 with weight 1 on every drawable particle orbital */
 } hande_qmc;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  `alloc`
@@ -328,6 +333,70 @@ hande_status hande_batch_synchronize(hande_batch* b);
 
 /* Free all replicas, their streams and the batch (safe on NULL). */
 void hande_batch_destroy(hande_batch* b);
+
+/* ---------------------------------------------------------------- learned proposal
+ * Not in the paper, whose generators are uniform or heat-bath (Sec. 2.1,
+ * Sec. 4).  With excit_gen = 1 (UEG only) a double excitation draws its
+ * occupied pair (i < j) uniformly and its particle orbital A (the spin of i)
+ * from a table row r = (I M + J) 2 + [spin i == spin j] (I, J spatial, M =
+ * norb) of integer weights q_r[A]; b follows from momentum conservation and
+ *   p_gen = [1 / C(N,2)] (q_r[A] + [same spin] q_r[B]) / sum_A' q_r[A'],
+ * exact in the integers, enters the spawn weight tau |H| / p_gen, so the
+ * estimators stay unbiased for any table.  A weight must be in [1, 2^24]
+ * exactly on the drawable orbitals (B in the basis and, for a same-spin pair,
+ * B != A) and 0 elsewhere; drawable orbitals with weight >= 1 keep every
+ * nonzero H_ij reachable. */
+
+/* Replace the table with q[2 M^2][M] (host; synchronises).  HANDE_ERR_INVALID
+ * for a context without the table generator or a table breaking the rule above. */
+hande_status hande_set_proposal(hande_ctx* ctx, const uint32_t* q);
+/* Copy the current table to q[2 M^2][M] (host; synchronises). */
+hande_status hande_get_proposal(hande_ctx* ctx, uint32_t* q);
+
+/* The learned proposal: an MLP (features x(r) = [one-hot I, one-hot J, same
+ * spin], two ReLU hidden layers of `width`, M logits; BF16 weights and
+ * activations on the tensor cores, FP32 accumulation) whose masked softmax p
+ * gives the table q_r[A] = max(1, floor(p(A | r) 2^24)).  It is trained online
+ * on the spawning attempts of the run: the spawning kernel records (row, A,
+ * |H| / p_draw) for `batch` attempts spread over each iteration, and every
+ * `period` iterations (after hande_iterate's iteration) one Adam step lowers
+ *   L = - sum_n c_n log p(A_n | r_n),  c_n = (|H_n| / p_n) / sum_m (|H_m| / p_m),
+ * the sampled cross-entropy to the distribution proportional to |H|, and the
+ * table is recomputed from the network. */
+typedef struct {
+  int width;             /* hidden width, a multiple of 64 up to 512 (0 = 256) */
+  int batch;             /* training samples per step, a multiple of 128 (0 = 4096) */
+  int period;            /* iterations between training steps (0 = no online training) */
+  double learning_rate;  /* Adam step size (0 = 1e-3) */
+  uint64_t seed;         /* initial weights: uniform in +-sqrt(6 / fan-in), zero biases */
+} hande_learning;
+
+/* Attach the learned proposal to a UEG context made with excit_gen = 1 (at
+ * most 256 orbitals) and recompute the table from its initial network.
+ * Synchronises. */
+hande_status hande_learn_proposal(hande_ctx* ctx, const hande_learning* learning);
+
+/* Network parameters as one FP32 vector, in this order: W1 [width][2M+1], b1
+ * [width], W2 [width][width], b2 [width], W3 [M][width], b3 [M] (row-major).
+ * Copies them to `get` and/or replaces them with `set` (host, n entries each,
+ * either may be NULL; setting resets the Adam moments).  n must be the
+ * parameter count, which *n_out receives when get and set are NULL.
+ * Synchronises. */
+hande_status hande_learn_params(hande_ctx* ctx, float* get, const float* set, int64_t n, int64_t* n_out);
+
+/* Loss L and its gradient (grads[n_params], host) for a batch of n <= batch
+ * samples: rows[n], drawn orbitals targets[n] (drawable), weights[n] >= 0 (the
+ * |H| / p of each sample).  The same BF16 forward and backward kernels the
+ * online training runs.  Synchronises. */
+hande_status hande_learn_gradients(hande_ctx* ctx, const int32_t* rows, const int32_t* targets, const float* weights,
+                                   int n, float* grads, double* loss);
+
+/* Masked softmax probabilities p(A | rows[i]) into probs[n][M] (host), n <= batch. */
+hande_status hande_learn_probabilities(hande_ctx* ctx, const int32_t* rows, int n, float* probs);
+
+/* Recompute the table from the current network now (normally done after every
+ * training step).  Synchronises. */
+hande_status hande_learn_refresh(hande_ctx* ctx);
 
 /* ---------------------------------------------------------------- tensor cores
  * The paper has no learned part: its excitation generators are uniform or

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhande.so")
-UNITS = ["host.cu", "inst_w1.cu", "inst_w2.cu", "inst_w8.cu", "noalloc.cu", "batch.cu", "mlp.cu"]
+UNITS = ["host.cu", "inst_w1.cu", "inst_w2.cu", "inst_w8.cu", "noalloc.cu", "batch.cu", "mlp.cu", "learn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,6 +12,7 @@
 namespace hande {
 
 struct Engine;
+struct Learner;   // learned excitation proposal (learn.cu)
 
 // launchers for one (key width, system kind) pair
 struct Ops {
@@ -80,10 +81,31 @@ struct Engine {
   unsigned* check_word = nullptr;   // result word of the walker-list checks
   int64_t core_table_cap = 0;
   double e_ref = 0.0;
+  // UEG proposal table (excit_gen = 1): cumulative weights on the device and
+  // the drawable mask (host and device); the learned proposal, if attached
+  uint32_t* ptab = nullptr;
+  uint8_t* pmask_dev = nullptr;
+  std::vector<uint8_t> pmask;
+  Learner* learn = nullptr;
   bool failed = false;
   unsigned err_bits = 0;
   std::string err;
 };
+
+// learned proposal (learn.cu)
+void proposal_init(Engine& E, const int4* kvec, const int16_t* klookup, int nmax, int side);
+void proposal_set(Engine& E, const uint32_t* q);
+void proposal_get(Engine& E, uint32_t* q);
+void learner_attach(Engine& E, const hande_learning& in);
+void learner_release(Engine& E);
+int64_t learner_nparam(const Engine& E);
+void learner_params(Engine& E, float* get, const float* set);
+void learner_gradients(Engine& E, const int32_t* rows, const int32_t* tgt, const float* w, int n, float* grads,
+                       double* loss);
+void learner_probabilities(Engine& E, const int32_t* rows, int n, float* probs);
+void learner_refresh(Engine& E);
+void learner_step(Engine& E);
+bool learner_due(const Engine& E);
 
 }  // namespace hande
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "engine.h"
+#include "host_util.h"
 
 using namespace hande;
 
@@ -20,44 +21,8 @@ namespace {
 
 const double kPi = 3.14159265358979323846;
 
-struct CudaError {
-  cudaError_t e;
-  const char* what;
-};
-
-#define CK(call)                                      \
-  do {                                                \
-    cudaError_t _e = (call);                          \
-    if (_e != cudaSuccess) throw CudaError{_e, #call}; \
-  } while (0)
-
-struct Fail {
-  hande_status code;
-  std::string msg;
-};
-
-void* dev_alloc(Engine& E, size_t bytes) {
-  bytes = (bytes + 255) & ~size_t(255);
-  if (bytes == 0) bytes = 256;
-  void* p = nullptr;
-  if (E.has_alloc) {
-    p = E.alloc.alloc(bytes, E.alloc.user);
-    if (!p) throw Fail{HANDE_ERR_NOMEM, "device allocation failed (" + std::to_string(bytes) + " bytes)"};
-  } else {
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      throw Fail{HANDE_ERR_NOMEM, "cudaMalloc failed (" + std::to_string(bytes) + " bytes)"};
-    }
-  }
-  E.blocks.push_back({p, bytes});
-  return p;
-}
-template <typename T>
-T* dalloc(Engine& E, size_t count) {
-  return static_cast<T*>(dev_alloc(E, count * sizeof(T)));
-}
-
 void release_all(Engine& E) {
+  learner_release(E);
   for (int a = 0; a < 2; ++a)
     for (int b = 0; b < 2; ++b)
       if (E.graph[a][b]) {
@@ -557,6 +522,8 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (q.real_amplitudes && !(q.spawn_cutoff >= 0.0)) throw Fail{HANDE_ERR_INVALID, "bad spawn_cutoff"};
     if (s.kind == HANDE_MOLECULE && !(q.p_single >= 0.0 && q.p_single < 1.0))
       throw Fail{HANDE_ERR_INVALID, "p_single must be in [0, 1)"};
+    if (q.excit_gen != 0 && !(q.excit_gen == 1 && s.kind == HANDE_UEG))
+      throw Fail{HANDE_ERR_INVALID, "excit_gen must be 0, or 1 (proposal table) for the UEG"};
 
     E.W = s.key_words;
     E.kind = s.kind;
@@ -656,6 +623,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
       sd.c_ueg[1] = tau * ((npairs * (double)s.norb) / 1.0);
       sd.c_single[0] = tau * (((double)n * (double)(s.norb - s.nalpha)) / sd.p_single);
       sd.c_single[1] = tau * (((double)n * (double)(s.norb - s.nbeta)) / sd.p_single);
+      sd.c_tab = tau * npairs;
       sd.half = q.real_amplitudes ? 1 : 0;
       // heat-bath entries: spawn amount of |<pq||ab>| ((tau inv_a) inv_b), then (a, b, sign)
       const double c_double = tau * (npairs / sd.p_double);
@@ -680,6 +648,8 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.hb_guide = upload(E, T.hb_guide);
     sd.orb_diag = upload(E, T.orb_diag);
     sd.pair_diag = upload(E, T.pair_diag);
+    sd.ptab_cum = nullptr;
+    if (q.excit_gen == 1) proposal_init(E, T.kvec.data(), T.klookup.data(), sd.nmax, sd.side);
 
     // ---- device buffers
     const int64_t cap = P.cap, scap = P.scap;
@@ -787,6 +757,7 @@ hande_status hande_iterate(hande_ctx* ctx, int n) {
       CK(cudaGraphLaunch(E.graph[E.cur][core], E.stream));
       E.cur ^= 1;
       E.host_iter += 1;
+      if (learner_due(E)) learner_step(E);
       if (E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start) {
         hande_status es = map_error(E, read_error(E));
         if (es != HANDE_OK) return es;
@@ -1063,6 +1034,90 @@ hande_status hande_set_state(hande_ctx* ctx, const hande_state* in, const uint64
     CK(cudaStreamSynchronize(E.stream));
     E.host_iter = in->iter;
     E.fetched = in->iter;
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_set_proposal(hande_ctx* ctx, const uint32_t* q) {
+  if (!ctx || !q) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.ptab) throw Fail{HANDE_ERR_INVALID, "the context has no proposal table (UEG with excit_gen = 1)"};
+    proposal_set(E, q);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_get_proposal(hande_ctx* ctx, uint32_t* q) {
+  if (!ctx || !q) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.ptab) throw Fail{HANDE_ERR_INVALID, "the context has no proposal table (UEG with excit_gen = 1)"};
+    proposal_get(E, q);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_learn_proposal(hande_ctx* ctx, const hande_learning* learning) {
+  if (!ctx || !learning) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    learner_attach(E, *learning);
+    // the captured iterations now record training samples
+    drop_graphs(E, 0);
+    drop_graphs(E, 1);
+    learner_refresh(E);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_learn_params(hande_ctx* ctx, float* get, const float* set, int64_t n, int64_t* n_out) {
+  if (!ctx) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.learn) throw Fail{HANDE_ERR_INVALID, "no learned proposal attached"};
+    if (n_out) *n_out = learner_nparam(E);
+    if (!get && !set) return HANDE_OK;
+    if (n != learner_nparam(E)) throw Fail{HANDE_ERR_INVALID, "parameter count mismatch"};
+    learner_params(E, get, set);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_learn_gradients(hande_ctx* ctx, const int32_t* rows, const int32_t* targets, const float* weights,
+                                   int n, float* grads, double* loss) {
+  if (!ctx || !rows || !targets || !weights || !grads || !loss) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.learn) throw Fail{HANDE_ERR_INVALID, "no learned proposal attached"};
+    learner_gradients(E, rows, targets, weights, n, grads, loss);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_learn_probabilities(hande_ctx* ctx, const int32_t* rows, int n, float* probs) {
+  if (!ctx || !rows || !probs) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.learn) throw Fail{HANDE_ERR_INVALID, "no learned proposal attached"};
+    learner_probabilities(E, rows, n, probs);
+    return HANDE_OK;
+  });
+}
+
+hande_status hande_learn_refresh(hande_ctx* ctx) {
+  if (!ctx) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    if (!E.learn) throw Fail{HANDE_ERR_INVALID, "no learned proposal attached"};
+    learner_refresh(E);
     return HANDE_OK;
   });
 }

@@ -117,6 +117,13 @@ struct Params {
   const double* core_val;
   int64_t* core_delta;
   int64_t* core_x;      // the core determinants' populations N(t-1), gathered by k_core_locate
+  // training samples of the learned proposal (UEG table generator): attempts
+  // g with g % stride == 0 (stride = ceil(natt / smp_cap)) write slot g / stride:
+  // row, drawn particle orbital and w = |H| / p(A | row) (0 = no sample)
+  int smp_cap;
+  int32_t* smp_row;
+  int32_t* smp_A;
+  float* smp_w;
   // state
   DevState* st;
   Record* rec;
@@ -789,6 +796,39 @@ __device__ __forceinline__ void load_window(const int64_t* a, int64_t n, int64_t
   av32 = (lane == 31 && wi + 1 < n) ? a[wi + 1] : INT64_MAX;
 }
 
+// Training sample of the learned proposal from a proposal-table draw (also a
+// rejected one: the UEG matrix element depends only on the four momenta):
+// w = |H| / p(A | row) with |H| = |v(k_I - k_A) - [same spin] v(k_I - k_B)|,
+// v(q) = 4 pi / (Omega |q|^2), q = 0 terms omitted.
+template <int W>
+__device__ __forceinline__ void record_sample(const Params& P, int64_t natt, int64_t g, const Excitation<W>& ex) {
+  const int64_t stride = (natt + P.smp_cap - 1) / P.smp_cap;
+  if (stride < 1 || g % stride != 0) return;
+  const int64_t slot = g / stride;
+  if (slot >= P.smp_cap) return;
+  float wv = 0.0f;
+  int row = 0, A = 0;
+  if (ex.prow >= 0) {
+    const SysDev& s = P.sys;
+    const int M = s.norb, same = ex.prow & 1, IJ = ex.prow >> 1, I = IJ / M, J = IJ % M;
+    A = ex.pA;
+    row = ex.prow;
+    const int4 ki = __ldg(&s.kvec[I]), kj = __ldg(&s.kvec[J]), ka = __ldg(&s.kvec[A]);
+    const int bx = ki.x + kj.x - ka.x, by = ki.y + kj.y - ka.y, bz = ki.z + kj.z - ka.z;
+    const int B = __ldg(&s.klookup[((bx + s.nmax) * s.side + (by + s.nmax)) * s.side + (bz + s.nmax)]);
+    const int dA = (ki.x - ka.x) * (ki.x - ka.x) + (ki.y - ka.y) * (ki.y - ka.y) + (ki.z - ka.z) * (ki.z - ka.z);
+    const int4 kb = __ldg(&s.kvec[B]);
+    const int dB = (ki.x - kb.x) * (ki.x - kb.x) + (ki.y - kb.y) * (ki.y - kb.y) + (ki.z - kb.z) * (ki.z - kb.z);
+    const double direct = dA > 0 ? s.vfac / (double)dA : 0.0;
+    const double exch = (same && dB > 0) ? s.vfac / (double)dB : 0.0;
+    const double h = fabs(direct - exch);
+    wv = (float)(h * ((double)ex.pQ / (double)ex.pqa));
+  }
+  P.smp_row[slot] = row;
+  P.smp_A[slot] = A;
+  P.smp_w[slot] = wv;
+}
+
 template <int W, int SYS>
 __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) {
   DevState* st = P.st;
@@ -914,6 +954,7 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       const uint8_t f = fl[par];
       const Words4 w = draw<W>(P.seed, P.replica, t, a, k);
       const Excitation<W> ex = generate<W, SYS>(P.sys, gt, k, w);
+      if (SYS == SYS_UEG && P.smp_cap > 0) record_sample(P, natt, g, ex);
       if (ex.single) {
         single = true;
         word = w.w;

@@ -66,6 +66,11 @@ struct SysDev {
   double c_ueg[2];
   double c_single[2];
   int half;   // spawn amounts rounded to nearest (real weights) or floored (integer walkers)
+  // UEG proposal table (the learned proposal's selection table; null = the
+  // uniform generator): for row r = (I M + J) 2 + [spin i == spin j], M
+  // cumulative integer weights over the particle orbital A; c_tab = tau C(N,2)
+  const uint32_t* ptab_cum;
+  double c_tab;
   // pair index P = j(j-1)/2 + i -> (i | j << 8), i < j < nel
   const uint16_t* pair_ij;
   // molecule: single-excitation terms G[(i*nspin + a)*nspin + k] = (ia|kk) - (ik|ka)
@@ -240,6 +245,8 @@ struct Excitation {
   bool single;           // a molecular single: selected only (si, sa), evaluated later
   bool hneg;             // H_child,parent < 0
   int si, sa;
+  int prow, pA;          // proposal table: the row and particle orbital drawn (prow < 0: none)
+  uint32_t pqa, pQ;      //   the drawn weight q_A and the row total Q
   uint64_t famt;         // fixed-point amount of |H| tau / p_gen (floored or rounded)
   Key<W> child;
 };
@@ -291,6 +298,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
   e.single = false;
   e.hneg = false;
   e.famt = 0;
+  e.prow = -1;
   const int n = s.nel;
   if (SYS == SYS_HUBBARD) {
     int p = select_bit<W>(d, (int)draw_index(w.x, (uint64_t)n));
@@ -313,6 +321,45 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
     int ii, jj;
     unrank_pair(gt.pair_ij, draw_index(w.y, npairs), ii, jj);
     int p = select_bit<W>(d, ii), q = select_bit<W>(d, jj);
+    if (s.ptab_cum) {
+      // proposal table: A by inverse CDF over the integer weights of row
+      // (I, J, same spin); p_gen = (q_A + [same] q_B) / (Q C(N,2)), exact
+      const int M = s.norb, I = p >> 1, J = q >> 1, same = ((p ^ q) & 1) ? 0 : 1;
+      const int row = (I * M + J) * 2 + same;
+      const uint32_t* cum = s.ptab_cum + (size_t)row * M;
+      const uint32_t Q = __ldg(&cum[M - 1]);
+      if (Q == 0) return e;
+      const uint64_t x = draw_index(w.z, (uint64_t)Q);
+      int lo = 0, hi = M - 1;   // the first A whose cumulative weight exceeds x
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(&cum[mid]) > x) hi = mid;
+        else lo = mid + 1;
+      }
+      const int A = lo;
+      int4 kp = __ldg(&s.kvec[I]), kq = __ldg(&s.kvec[J]), ka = __ldg(&s.kvec[A]);
+      int bx = kp.x + kq.x - ka.x, by = kp.y + kq.y - ka.y, bz = kp.z + kq.z - ka.z;
+      if (bx < -s.nmax || bx > s.nmax || by < -s.nmax || by > s.nmax || bz < -s.nmax || bz > s.nmax) return e;
+      const int B = __ldg(&s.klookup[((bx + s.nmax) * s.side + (by + s.nmax)) * s.side + (bz + s.nmax)]);
+      if (B < 0) return e;   // weight 0: not drawn
+      const uint32_t qa = __ldg(&cum[A]) - (A > 0 ? __ldg(&cum[A - 1]) : 0u);
+      const uint32_t qb = same ? __ldg(&cum[B]) - (B > 0 ? __ldg(&cum[B - 1]) : 0u) : 0u;
+      e.prow = row;
+      e.pA = A;
+      e.pqa = qa;
+      e.pQ = Q;
+      const int a = 2 * A + (p & 1), b = 2 * B + (q & 1);
+      if (a == b || key_bit<W>(d, a) || key_bit<W>(d, b)) return e;
+      const int lo2 = a < b ? a : b, hi2 = a < b ? b : a;
+      e.child = d;
+      key_flip<W>(e.child, p);
+      key_flip<W>(e.child, q);
+      key_flip<W>(e.child, a);
+      key_flip<W>(e.child, b);
+      const double inv_b = __ddiv_rn((double)Q, (double)(qa + qb));
+      finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo2, hi2), __dmul_rn(s.c_tab, inv_b));
+      return e;
+    }
     int A = (int)draw_index(w.z, (uint64_t)s.norb);
     int a = 2 * A + (p & 1);
     int4 kp = __ldg(&s.kvec[p >> 1]), kq = __ldg(&s.kvec[q >> 1]), ka = __ldg(&s.kvec[A]);

@@ -53,7 +53,7 @@ class _Qmc(C.Structure):
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int), ("semi_stoch_start", C.c_int),
                 ("seed", C.c_uint64), ("replica", C.c_uint64), ("state_capacity", C.c_int64),
                 ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int), ("tile_capacity", C.c_int),
-                ("annihilation", C.c_int)]
+                ("annihilation", C.c_int), ("excit_gen", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -68,6 +68,11 @@ class _Estimate(C.Structure):
     _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_pre", C.c_int64), ("n0", C.c_int64),
                 ("num_hi", C.c_int64), ("num_lo", C.c_uint64), ("num", C.c_double), ("nw_post", C.c_int64),
                 ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64)]
+
+
+class _Learning(C.Structure):
+    _fields_ = [("width", C.c_int), ("batch", C.c_int), ("period", C.c_int), ("learning_rate", C.c_double),
+                ("seed", C.c_uint64)]
 
 
 class _State(C.Structure):
@@ -87,7 +92,9 @@ EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_s
            "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
            "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
            "hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize",
-           "hande_batch_destroy", "hande_gemm_bf16"]
+           "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
+           "hande_learn_params", "hande_learn_gradients", "hande_learn_probabilities", "hande_learn_refresh",
+           "hande_gemm_bf16"]
 
 _lib = None
 _lock = threading.Lock()
@@ -145,6 +152,17 @@ def load(build_if_needed: bool = True):
             getattr(lib, name).restype = C.c_int
         lib.hande_gemm_bf16.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P]
         lib.hande_gemm_bf16.restype = C.c_int
+        u32p, i32p, fp = C.POINTER(C.c_uint32), C.POINTER(C.c_int32), C.POINTER(C.c_float)
+        lib.hande_set_proposal.argtypes = [P, u32p]
+        lib.hande_get_proposal.argtypes = [P, u32p]
+        lib.hande_learn_proposal.argtypes = [P, C.POINTER(_Learning)]
+        lib.hande_learn_params.argtypes = [P, fp, fp, C.c_int64, i64p]
+        lib.hande_learn_gradients.argtypes = [P, i32p, i32p, fp, C.c_int, fp, dp]
+        lib.hande_learn_probabilities.argtypes = [P, i32p, C.c_int, fp]
+        lib.hande_learn_refresh.argtypes = [P]
+        for name in ("hande_set_proposal", "hande_get_proposal", "hande_learn_proposal", "hande_learn_params",
+                     "hande_learn_gradients", "hande_learn_probabilities", "hande_learn_refresh"):
+            getattr(lib, name).restype = C.c_int
         _lib = lib
         return lib
 
@@ -206,6 +224,7 @@ def _structs(system: dict, qmc: dict):
     q.record_capacity = int(qmc.get("record_capacity", 0))
     q.tile_capacity = int(qmc.get("tile_capacity", 0))
     q.annihilation = int(qmc.get("annihilation", 0))
+    q.excit_gen = int(qmc.get("excit_gen", 0))
     return s, q, keep
 
 
@@ -234,6 +253,7 @@ class Hande:
         self._batch = None
         s, q, self._keep = _structs(system, qmc)
         self.W = s.key_words
+        self._system_norb = s.norb
         self.stream, self._alloc, self._alloc_fns = _stream_and_allocator(stream, torch_memory)
         alloc_p = C.byref(self._alloc) if self._alloc is not None else None
         rc = lib.hande_init_system(C.byref(s), C.byref(q), alloc_p, C.c_void_p(self.stream), C.byref(self._h))
@@ -362,6 +382,72 @@ class Hande:
             kp = k.ctypes.data_as(C.POINTER(C.c_uint64))
         self._check(self._lib.hande_set_state(self._h, C.byref(st), kp), "hande_set_state")
 
+    # ------------------------------------------------------------ learned proposal
+    def _norb(self):
+        return int(self._system_norb)
+
+    def set_proposal(self, q) -> None:
+        """Integer weights q[2 M^2, M] of the UEG proposal table (excit_gen = 1)."""
+        a = np.ascontiguousarray(q, dtype=np.uint32)
+        self._check(self._lib.hande_set_proposal(self._h, a.ctypes.data_as(C.POINTER(C.c_uint32))),
+                    "hande_set_proposal")
+
+    def proposal(self) -> np.ndarray:
+        M = self._norb()
+        q = np.zeros((2 * M * M, M), dtype=np.uint32)
+        self._check(self._lib.hande_get_proposal(self._h, q.ctypes.data_as(C.POINTER(C.c_uint32))),
+                    "hande_get_proposal")
+        return q
+
+    def learn_proposal(self, width=256, batch=4096, period=10, learning_rate=1e-3, seed=1) -> None:
+        """Attach the learned proposal (include/hande.h, hande_learn_proposal)."""
+        L = _Learning(int(width), int(batch), int(period), float(learning_rate), int(seed))
+        self._check(self._lib.hande_learn_proposal(self._h, C.byref(L)), "hande_learn_proposal")
+
+    def learn_params(self, set_params=None) -> np.ndarray:
+        """The network's parameters as one float32 vector (optionally replaced first)."""
+        n = C.c_int64()
+        self._check(self._lib.hande_learn_params(self._h, None, None, 0, C.byref(n)), "hande_learn_params")
+        out = np.zeros(n.value, dtype=np.float32)
+        sp = None
+        if set_params is not None:
+            src = np.ascontiguousarray(set_params, dtype=np.float32)
+            if src.size != n.value:
+                raise ValueError(f"expected {n.value} parameters")
+            self._params_keep = src
+            sp = src.ctypes.data_as(C.POINTER(C.c_float))
+        self._check(self._lib.hande_learn_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float)), sp, n.value,
+                                                 None), "hande_learn_params")
+        return out
+
+    def learn_gradients(self, rows, targets, weights):
+        """(loss, gradient vector) of a sample batch through the BF16 tensor-core kernels."""
+        r = np.ascontiguousarray(rows, dtype=np.int32)
+        t = np.ascontiguousarray(targets, dtype=np.int32)
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        n = C.c_int64()
+        self._check(self._lib.hande_learn_params(self._h, None, None, 0, C.byref(n)), "hande_learn_params")
+        g = np.zeros(n.value, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self._lib.hande_learn_gradients(self._h, r.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                    t.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                    w.ctypes.data_as(C.POINTER(C.c_float)), len(r),
+                                                    g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)),
+                    "hande_learn_gradients")
+        return loss.value, g
+
+    def learn_probabilities(self, rows) -> np.ndarray:
+        r = np.ascontiguousarray(rows, dtype=np.int32)
+        M = self._norb()
+        p = np.zeros((len(r), M), dtype=np.float32)
+        self._check(self._lib.hande_learn_probabilities(self._h, r.ctypes.data_as(C.POINTER(C.c_int32)), len(r),
+                                                        p.ctypes.data_as(C.POINTER(C.c_float))),
+                    "hande_learn_probabilities")
+        return p
+
+    def learn_refresh(self) -> None:
+        self._check(self._lib.hande_learn_refresh(self._h), "hande_learn_refresh")
+
     def close(self) -> None:
         if self._h and self._batch is None:   # a batch's replica is freed with its batch
             self._lib.hande_destroy(self._h)
@@ -431,6 +517,7 @@ class HandeBatch:
             v._lib, v._batch, v._keep = lib, self, []
             v._h = C.c_void_p(lib.hande_batch_replica(self._h, r))
             v.W = int(systems[r]["key_words"])
+            v._system_norb = int(systems[r]["norb"])
             v.stream, v._alloc, v._alloc_fns = None, None, None
             self.replicas.append(v)
 

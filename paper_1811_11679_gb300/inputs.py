@@ -231,3 +231,11 @@ def synthetic_walkers(system: dict, n_det: int, n_walkers: float, seed: int = 21
     pops *= rng.choice(np.array([-1, 1], dtype=np.int64), size=len(pops))
     pops[is0] = int(round(ref_fraction * n_walkers * F))
     return allk, pops
+
+
+def random_proposal(mask, seed: int = 17) -> np.ndarray:
+    """Seeded integer weights in [1, 2^24] on the drawable entries of a UEG
+    proposal-table mask (bool[2 M^2, M]), 0 elsewhere."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    q = rng.integers(1, 1 << 24, size=mask.shape, endpoint=True).astype(np.uint32)
+    return np.where(mask, q, 0).astype(np.uint32)
