@@ -61,9 +61,19 @@ typedef enum {
 typedef enum { HANDE_HUBBARD = 0, HANDE_UEG = 1, HANDE_MOLECULE = 2 } hande_system_kind;
 
 /* The Hamiltonian (the paper's `sys` table).
- *   HUBBARD   real-space 1D chain/ring of `norb` sites, hopping -t between
- *             neighbours, on-site U; periodic needs norb >= 3.  Reference
- *             determinant: alpha on even sites, beta on odd sites.
+ *   HUBBARD   real-space Hubbard model, hopping -t between neighbours, on-site
+ *             U.  ndim = 0: a 1D chain of `norb` sites (periodic needs norb >= 3).
+ *             ndim = d in 1..3: the periodic lattice whose cell is spanned by
+ *             the integer vectors lattice[3k .. 3k+d) (the paper's `lattice`
+ *             input; e.g. {3, 3}, {3, -3} is the tilted 18-site square
+ *             cluster); its sites are the integer points r with fractional
+ *             coordinates r A^-1 in [0, 1)^d, in lexicographic order of r
+ *             (when every lattice vector has an even coordinate sum the cell is
+ *             bipartite: its even- and odd-parity sites then alternate, each
+ *             half lexicographic, so that the reference below is the Neel
+ *             state), and norb must be |det A|; hops go to r +- e_k (reduced into the cell),
+ *             which must reach 2d distinct other sites.  Reference determinant:
+ *             alpha on even sites, beta on odd sites.
  *   UEG       3D uniform electron gas in the `norb` plane waves of lowest
  *             |n|^2 (ties by (nx, ny, nz)), box from the Wigner-Seitz radius
  *             rs, Coulomb kernel 4 pi / (Omega |q|^2), q = 0 and Madelung terms
@@ -83,6 +93,8 @@ typedef struct {
   const double* h1;  /* MOLECULE only */
   const double* eri; /* MOLECULE only */
   double ecore;      /* MOLECULE only */
+  int ndim;          /* HUBBARD: 0 = chain of norb sites, else lattice dimension */
+  int lattice[9];    /* HUBBARD: row k (lattice[3k .. 3k+ndim)) = lattice vector k */
 } hande_system;
 
 /* Run parameters (the paper's `qmc` and `semi_stoch` tables). */

@@ -275,6 +275,8 @@ struct Ctx {
     /* system */
     int kind, W, norb, nalpha, nbeta, nel, nspin;
     int L, periodic;
+    int z;                          /* Hubbard: hopping directions per site */
+    std::vector<int> nbr;           /* Hubbard: nbr[site * z + k], -1 = none */
     double t_hop, U;
     /* UEG */
     double rs, box, vfac, kfac;
@@ -386,8 +388,9 @@ double h_single(const Ctx& c, const Det& d, int i, int a) {
         /* hopping -t between nearest-neighbour sites with the same spin */
         if ((i & 1) != (a & 1)) return 0.0;
         int si = i >> 1, sa = a >> 1;
-        int diff = si > sa ? si - sa : sa - si;
-        bool bond = (diff == 1) || (c.periodic && c.L > 2 && diff == c.L - 1);
+        bool bond = false;
+        for (int k = 0; k < c.z; ++k)
+            if (c.nbr[(size_t)si * c.z + k] == sa) bond = true;
         if (!bond) return 0.0;
         v = -c.t_hop;
     } else if (c.kind == SYS_UEG) {
@@ -475,17 +478,14 @@ Excit gen_hubbard(const Ctx& c, const Det& d, const uint64_t w[4]) {
     int n = (int)o.size();
     int p = o[draw_index(w[0], (uint64_t)n)];
     int site = p >> 1, spin = p & 1;
-    int dir = (int)(w[1] >> 63);
-    int ns = dir == 0 ? site + 1 : site - 1;
-    if (c.periodic) {
-        ns = (ns + c.L) % c.L;
-    } else if (ns < 0 || ns >= c.L) {
-        return e;
-    }
+    /* direction k uniform among the z hops (chain: k = 0 right, 1 left) */
+    int k = (int)draw_index(w[1], (uint64_t)c.z);
+    int ns = c.nbr[(size_t)site * c.z + k];
+    if (ns < 0) return e;
     int q = 2 * ns + spin;
     if (occ_bit(d, q)) return e;
-    e.pgen = 1.0 / (2.0 * (double)n);
-    e.inv_a = 2.0 * (double)n;
+    e.pgen = 1.0 / ((double)c.z * (double)n);
+    e.inv_a = (double)c.z * (double)n;
     e.inv_b = 1.0;
     e.hij = h_single(c, d, p, q);
     e.child = d;
@@ -1000,7 +1000,122 @@ typedef struct {
     const double* h1;
     const double* eri;
     double ecore;
+    int ndim;           /* Hubbard lattice: 0 = 1D chain of norb sites, else lattice vectors */
+    int lattice[9];     /* row k = vector a_k (ndim x ndim, row-major in a 3 x 3 array) */
 } orc_system;
+
+/* Hubbard sites and hops.  ndim = 0: a chain of L sites, hops to s + 1 (k = 0)
+ * and s - 1 (k = 1), wrapped when periodic (L >= 3), else none past the ends.
+ * ndim = d >= 1: the real-space lattice spanned by the integer rows a_k of the
+ * paper's `lattice` input, periodic in each: the sites are the integer points
+ * r whose fractional coordinates f = r A^-1 lie in [0, 1)^d, in lexicographic
+ * order of r (sublattice-interleaved for a bipartite cell, see below); hop k
+ * goes to r + e_{k/2} (k even) or r - e_{k/2} (k odd),
+ * reduced into the cell by lattice vectors.  The 2d hops of a site must reach
+ * 2d distinct other sites.  Returns false for an invalid lattice. */
+static bool build_hubbard_sites(Ctx& c, int ndim, const int* lat) {
+    if (ndim == 0) {
+        c.z = 2;
+        c.nbr.assign((size_t)c.L * 2, -1);
+        for (int s = 0; s < c.L; ++s) {
+            int r = s + 1, l = s - 1;
+            if (c.periodic) { r %= c.L; l = (l + c.L) % c.L; }
+            c.nbr[(size_t)s * 2] = (r >= 0 && r < c.L) ? r : -1;
+            c.nbr[(size_t)s * 2 + 1] = (l >= 0 && l < c.L) ? l : -1;
+        }
+        return true;
+    }
+    if (ndim > 3) return false;
+    const int d = ndim;
+    long long A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) A[i][j] = lat[3 * i + j];
+    /* adjugate and determinant of the d x d block (identity elsewhere) */
+    long long adj[3][3], det;
+    adj[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    adj[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    adj[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    adj[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    adj[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    adj[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    adj[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    adj[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    adj[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    det = A[0][0] * adj[0][0] + A[0][1] * adj[1][0] + A[0][2] * adj[2][0];
+    if (det == 0) return false;
+    long long D = det < 0 ? -det : det, sg = det < 0 ? -1 : 1;
+    if (D != c.L) return false;
+    /* f = r adj / det: r is in the cell iff 0 <= (r adj sg)_k < D */
+    auto frac = [&](const long long r[3], long long g[3]) {
+        for (int k = 0; k < 3; ++k) g[k] = sg * (r[0] * adj[0][k] + r[1] * adj[1][k] + r[2] * adj[2][k]);
+    };
+    long long lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int m = 0; m < (1 << d); ++m) {
+        long long v[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i)
+            if (m >> i & 1)
+                for (int j = 0; j < d; ++j) v[j] += A[i][j];
+        for (int j = 0; j < d; ++j) { if (v[j] < lo[j]) lo[j] = v[j]; if (v[j] > hi[j]) hi[j] = v[j]; }
+    }
+    std::vector<std::vector<long long>> sites;
+    long long r[3] = {0, 0, 0};
+    for (r[0] = lo[0]; r[0] <= hi[0]; ++r[0])
+        for (r[1] = d > 1 ? lo[1] : 0; r[1] <= (d > 1 ? hi[1] : 0); ++r[1])
+            for (r[2] = d > 2 ? lo[2] : 0; r[2] <= (d > 2 ? hi[2] : 0); ++r[2]) {
+                long long g[3];
+                frac(r, g);
+                bool in = true;
+                for (int k = 0; k < d; ++k) in = in && g[k] >= 0 && g[k] < D;
+                if (in) sites.push_back({r[0], r[1], r[2]});
+            }
+    if ((long long)sites.size() != D) return false;
+    /* a cell whose lattice vectors all have even coordinate sums is bipartite
+     * (checkerboard by the parity of x + y + z) with equal halves: order it
+     * sublattice-interleaved (even-parity site, odd-parity site, ...), each half
+     * in lexicographic order, so that the reference (alpha on even indices,
+     * beta on odd) is the Neel state */
+    bool bip = D % 2 == 0;
+    for (int i = 0; i < d; ++i) {
+        long long sum = 0;
+        for (int j = 0; j < d; ++j) sum += A[i][j];
+        if (sum % 2 != 0) bip = false;
+    }
+    if (bip) {
+        std::vector<std::vector<long long>> ev, od;
+        for (size_t i = 0; i < sites.size(); ++i) {
+            long long par = sites[i][0] + sites[i][1] + sites[i][2];
+            if (((par % 2) + 2) % 2 == 0) ev.push_back(sites[i]); else od.push_back(sites[i]);
+        }
+        if (ev.size() == od.size()) {
+            sites.clear();
+            for (size_t i = 0; i < ev.size(); ++i) { sites.push_back(ev[i]); sites.push_back(od[i]); }
+        }
+    }
+    auto index_of = [&](long long x[3]) -> int {
+        for (size_t i = 0; i < sites.size(); ++i)
+            if (sites[i][0] == x[0] && sites[i][1] == x[1] && sites[i][2] == x[2]) return (int)i;
+        return -1;
+    };
+    c.z = 2 * d;
+    c.nbr.assign((size_t)c.L * c.z, -1);
+    for (int s = 0; s < c.L; ++s)
+        for (int k = 0; k < c.z; ++k) {
+            long long x[3] = {sites[s][0], sites[s][1], sites[s][2]};
+            x[k / 2] += (k & 1) ? -1 : 1;
+            long long g[3];
+            frac(x, g);
+            for (int i = 0; i < d; ++i) {      /* n_i = floor(g_i / D), x -= n A */
+                long long n = g[i] >= 0 ? g[i] / D : -((-g[i] + D - 1) / D);
+                for (int j = 0; j < d; ++j) x[j] -= n * A[i][j];
+            }
+            int t = index_of(x);
+            if (t < 0 || t == s) return false;
+            for (int k2 = 0; k2 < k; ++k2)
+                if (c.nbr[(size_t)s * c.z + k2] == t) return false;
+            c.nbr[(size_t)s * c.z + k] = t;
+        }
+    return true;
+}
 
 typedef struct {
     double tau, target_population, shift_damping, spawn_cutoff, init_pop, initiator_threshold;
@@ -1098,7 +1213,8 @@ void* orc_create(const orc_system* s, const orc_qmc* q) {
     c->rs = s->rs;
     c->ecore = s->ecore;
     if (c->W < 1 || c->W > MAXW || c->nspin > 64 * c->W) { delete c; return nullptr; }
-    if (c->kind == SYS_HUBBARD && c->periodic && c->L < 3) { delete c; return nullptr; }
+    if (c->kind == SYS_HUBBARD && s->ndim == 0 && c->periodic && c->L < 3) { delete c; return nullptr; }
+    if (c->kind == SYS_HUBBARD && !build_hubbard_sites(*c, s->ndim, s->lattice)) { delete c; return nullptr; }
     if (c->kind == SYS_MOLECULE) {
         size_t n = (size_t)c->norb;
         c->h1.assign(s->h1, s->h1 + n * n);
@@ -1300,13 +1416,13 @@ int64_t orc_enumerate(void* h, const uint64_t* key, uint64_t* children, double* 
     auto add = [&](const Det* ch, double p) { paths.push_back(std::make_pair(ch ? *ch : zero, p)); };
     if (c->kind == SYS_HUBBARD) {
         for (int k = 0; k < n; ++k)
-            for (int dir = 0; dir < 2; ++dir) {
+            for (int dir = 0; dir < c->z; ++dir) {
                 uint64_t w[4] = {0, 0, 0, 0};
-                /* smallest word mapping to electron k */
+                /* smallest words mapping to electron k and direction dir */
                 w[0] = (uint64_t)((((u128)k << 64) + (uint64_t)n - 1) / (uint64_t)n);
-                w[1] = dir ? (1ull << 63) : 0;
+                w[1] = (uint64_t)((((u128)(uint64_t)dir << 64) + (uint64_t)c->z - 1) / (uint64_t)c->z);
                 Excit e = generate(*c, d, w);
-                add(e.null ? nullptr : &e.child, 1.0 / (2.0 * n));
+                add(e.null ? nullptr : &e.child, 1.0 / ((double)c->z * n));
             }
     } else if (c->kind == SYS_UEG && c->excit_gen == 1) {
         uint64_t npairs = (uint64_t)n * (n - 1) / 2;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -66,6 +67,118 @@ struct HostTables {
 };
 
 inline size_t tri_h(size_t p, size_t q) { return p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p; }
+
+// Hubbard hops: z per site, nbr[site z + k] (-1 = none).  Chain (ndim 0): hop 0
+// to s + 1, hop 1 to s - 1, wrapped if periodic.  Lattice (ndim d): sites are
+// the integer points whose coordinates in the basis of the lattice vectors
+// (Cramer's rule, exact in integers) lie in [0, 1)^d, ordered lexicographically
+// (checkerboard-interleaved for a bipartite cell);
+// hop k moves by +e_{k/2} (k even) or -e_{k/2} (k odd) and is brought back
+// into the cell by whole lattice vectors.  False if the lattice is degenerate,
+// its cell does not hold norb sites, or a site's hops are not 2d distinct sites.
+bool hubbard_hops(const hande_system& s, int& z, std::vector<int16_t>& nbr) {
+  const int L = s.norb;
+  if (s.ndim == 0) {
+    z = 2;
+    nbr.assign((size_t)2 * L, -1);
+    for (int i = 0; i < L; ++i) {
+      int right = i + 1, left = i - 1;
+      if (s.periodic) {
+        right = right == L ? 0 : right;
+        left = left < 0 ? L - 1 : left;
+      }
+      nbr[2 * i] = (int16_t)(right < L ? right : -1);
+      nbr[2 * i + 1] = (int16_t)(left >= 0 ? left : -1);
+    }
+    return true;
+  }
+  const int d = s.ndim;
+  if (d < 1 || d > 3) return false;
+  // lattice matrix padded with the identity; coordinates c of a point r in the
+  // lattice basis: c_k = det(A with row k replaced by r) / det(A)
+  int64_t A[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) A[i][j] = s.lattice[3 * i + j];
+  auto det3 = [](const int64_t M[3][3]) {
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  };
+  const int64_t det = det3(A);
+  if (det == 0 || (det < 0 ? -det : det) != L) return false;
+  auto numer = [&](const int64_t r[3], int k) {   // det with row k replaced by r
+    int64_t M[3][3];
+    std::memcpy(M, A, sizeof M);
+    for (int j = 0; j < 3; ++j) M[k][j] = r[j];
+    return det3(M);
+  };
+  auto in_cell = [&](const int64_t r[3]) {
+    for (int k = 0; k < d; ++k) {
+      int64_t num = numer(r, k);
+      if (det < 0) num = -num;
+      const int64_t D = det < 0 ? -det : det;
+      if (num < 0 || num >= D) return false;
+    }
+    return true;
+  };
+  // bounding box of the cell's corners
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int m = 0; m < (1 << d); ++m)
+    for (int j = 0; j < d; ++j) {
+      int64_t v = 0;
+      for (int i = 0; i < d; ++i)
+        if ((m >> i) & 1) v += A[i][j];
+      lo[j] = std::min(lo[j], v);
+      hi[j] = std::max(hi[j], v);
+    }
+  std::vector<std::array<int64_t, 3>> site;
+  for (int64_t x = lo[0]; x <= hi[0]; ++x)
+    for (int64_t y = lo[1]; y <= hi[1]; ++y)
+      for (int64_t w = lo[2]; w <= hi[2]; ++w) {
+        const int64_t r[3] = {x, y, w};
+        if (in_cell(r)) site.push_back({x, y, w});
+      }
+  if ((int64_t)site.size() != L) return false;
+  // checkerboard order for a bipartite cell (every lattice vector has an even
+  // coordinate sum, equal halves): even-parity and odd-parity sites alternate,
+  // each half lexicographic, so even indices form one sublattice
+  bool bipartite = L % 2 == 0;
+  for (int i = 0; i < d; ++i) bipartite = bipartite && ((A[i][0] + A[i][1] + A[i][2]) & 1) == 0;
+  if (bipartite) {
+    std::vector<std::array<int64_t, 3>> half[2];
+    for (const auto& r : site) half[(r[0] + r[1] + r[2]) & 1].push_back(r);
+    if (half[0].size() == half[1].size()) {
+      for (size_t i = 0; i < half[0].size(); ++i) {
+        site[2 * i] = half[0][i];
+        site[2 * i + 1] = half[1][i];
+      }
+    }
+  }
+  z = 2 * d;
+  nbr.assign((size_t)z * L, -1);
+  const int64_t D = det < 0 ? -det : det;
+  for (int i = 0; i < L; ++i)
+    for (int k = 0; k < z; ++k) {
+      int64_t r[3] = {site[i][0], site[i][1], site[i][2]};
+      r[k >> 1] += (k & 1) ? -1 : 1;
+      // subtract floor(c) whole lattice vectors
+      int64_t shift[3] = {0, 0, 0};
+      for (int q = 0; q < d; ++q) {
+        int64_t num = numer(r, q);
+        if (det < 0) num = -num;
+        shift[q] = num >= 0 ? num / D : -((-num + D - 1) / D);
+      }
+      for (int q = 0; q < d; ++q)
+        for (int j = 0; j < d; ++j) r[j] -= shift[q] * A[q][j];
+      int t = -1;
+      for (int j = 0; j < L; ++j)
+        if (site[j][0] == r[0] && site[j][1] == r[1] && site[j][2] == r[2]) t = j;
+      if (t < 0 || t == i) return false;
+      for (int k2 = 0; k2 < k; ++k2)
+        if (nbr[(size_t)i * z + k2] == t) return false;
+      nbr[(size_t)i * z + k] = (int16_t)t;
+    }
+  return true;
+}
 
 // plane waves n in Z^3 ordered by (|n|^2, nx, ny, nz); the first norb are the basis
 void build_ueg(const hande_system& s, SysDev& sd, HostTables& T) {
@@ -508,7 +621,8 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     if (s.nalpha < 0 || s.nbeta < 0 || s.nalpha > s.norb || s.nbeta > s.norb || s.nalpha + s.nbeta < 2)
       throw Fail{HANDE_ERR_INVALID, "bad electron numbers"};
     if (s.kind == HANDE_HUBBARD) {
-      if (s.periodic && s.norb < 3) throw Fail{HANDE_ERR_INVALID, "periodic Hubbard needs at least 3 sites"};
+      if (s.ndim == 0 && s.periodic && s.norb < 3)
+        throw Fail{HANDE_ERR_INVALID, "periodic Hubbard chain needs at least 3 sites"};
       if (s.nalpha > (s.norb + 1) / 2 || s.nbeta > s.norb / 2)
         throw Fail{HANDE_ERR_INVALID, "Hubbard reference needs nalpha <= ceil(L/2), nbeta <= floor(L/2)"};
     }
@@ -611,6 +725,10 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.t = s.t;
     sd.U = s.U;
     HostTables T;
+    std::vector<int16_t> hops;
+    sd.z = 0;
+    if (s.kind == HANDE_HUBBARD && !hubbard_hops(s, sd.z, hops))
+      throw Fail{HANDE_ERR_INVALID, "Hubbard lattice: degenerate, |det| != norb, or hops not to distinct sites"};
     if (s.kind == HANDE_UEG) build_ueg(s, sd, T);
     if (s.kind == HANDE_MOLECULE) build_molecule(s, q, sd, T);
     {
@@ -618,7 +736,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
       const double npairs = (double)((int64_t)n * (n - 1) / 2);
       // 1/p_gen = inv_a inv_b; spawn-weight factor (tau inv_a) inv_b
       const double tau = q.tau;
-      sd.c_hub = tau * (2.0 * (double)n);
+      sd.c_hub = tau * ((double)sd.z * (double)n);
       sd.c_ueg[0] = tau * ((npairs * (double)s.norb) / 2.0);
       sd.c_ueg[1] = tau * ((npairs * (double)s.norb) / 1.0);
       sd.c_single[0] = tau * (((double)n * (double)(s.norb - s.nalpha)) / sd.p_single);
@@ -648,6 +766,7 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     sd.hb_guide = upload(E, T.hb_guide);
     sd.orb_diag = upload(E, T.orb_diag);
     sd.pair_diag = upload(E, T.pair_diag);
+    sd.nbr = upload(E, hops);
     sd.ptab_cum = nullptr;
     if (q.excit_gen == 1) proposal_init(E, T.kvec.data(), T.klookup.data(), sd.nmax, sd.side);
 

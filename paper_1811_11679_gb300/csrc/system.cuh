@@ -27,8 +27,9 @@ enum { SYS_HUBBARD = 0, SYS_UEG = 1, SYS_MOLECULE = 2 };
 
 struct SysDev {
   int norb, nspin, nel;
-  // Hubbard
-  int L, periodic;
+  // Hubbard: L sites, z hops per site, nbr[site * z + k] the site hop k reaches (-1: none)
+  int L, periodic, z;
+  const int16_t* nbr;
   double t, U;
   // UEG: per spatial orbital (nx, ny, nz, |n|^2) packed in int4; momentum cube
   double vfac, kfac;
@@ -160,8 +161,8 @@ __device__ double h_single(const SysDev& s, const Key<W>& d, int i, int a) {
   if (SYS == SYS_HUBBARD) {
     if ((i ^ a) & 1) return 0.0;
     int si = i >> 1, sa = a >> 1;
-    int diff = si > sa ? si - sa : sa - si;
-    bool bond = (diff == 1) || (s.periodic && s.L > 2 && diff == s.L - 1);
+    bool bond = false;
+    for (int k = 0; k < s.z; ++k) bond = bond || __ldg(&s.nbr[si * s.z + k]) == sa;
     if (!bond) return 0.0;
     v = -s.t;
   } else if (SYS == SYS_UEG) {
@@ -303,12 +304,9 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
   if (SYS == SYS_HUBBARD) {
     int p = select_bit<W>(d, (int)draw_index(w.x, (uint64_t)n));
     int site = p >> 1, spin = p & 1;
-    int ns = (w.y >> 63) == 0 ? site + 1 : site - 1;
-    if (s.periodic) {
-      ns = (ns + s.L) % s.L;
-    } else if (ns < 0 || ns >= s.L) {
-      return e;
-    }
+    // hop k uniform among the z of the site (chain: 0 right, 1 left)
+    int ns = __ldg(&s.nbr[site * s.z + (int)draw_index(w.y, (uint64_t)s.z)]);
+    if (ns < 0) return e;
     int q = 2 * ns + spin;
     if (key_bit<W>(d, q)) return e;
     e.child = d;

@@ -43,7 +43,7 @@ class _System(C.Structure):
     _fields_ = [("kind", C.c_int), ("key_words", C.c_int), ("norb", C.c_int), ("nalpha", C.c_int),
                 ("nbeta", C.c_int), ("periodic", C.c_int), ("t", C.c_double), ("U", C.c_double),
                 ("rs", C.c_double), ("h1", C.POINTER(C.c_double)), ("eri", C.POINTER(C.c_double)),
-                ("ecore", C.c_double)]
+                ("ecore", C.c_double), ("ndim", C.c_int), ("lattice", C.c_int * 9)]
 
 
 class _Qmc(C.Structure):
@@ -197,6 +197,13 @@ def _structs(system: dict, qmc: dict):
     s.U = float(system.get("U", 0.0))
     s.rs = float(system.get("rs", 0.0))
     s.ecore = float(system.get("ecore", 0.0))
+    lat = system.get("lattice")
+    if lat is not None:
+        lat = np.asarray(lat, dtype=np.int64)
+        s.ndim = lat.shape[0]
+        for i in range(s.ndim):
+            for j in range(s.ndim):
+                s.lattice[3 * i + j] = int(lat[i, j])
     keep = []
     if s.kind == 2:
         h1 = np.ascontiguousarray(system["h1"], dtype=np.float64)

@@ -12,6 +12,9 @@ Workloads (sizes as in the HANDE-QMC paper's tutorial and examples):
   * ueg14        -- uniform electron gas, 14 electrons, 38 plane-wave spatial
                     orbitals (76 spin orbitals, 128-bit keys), r_s = 1,
                     initiator real-weight FCIQMC, tau=0.002.
+  * hubbard18_2d -- 2D Hubbard model, tilted 18-site square cluster (lattice
+                    vectors (3, 3), (3, -3)), 9 up + 9 down, U/t = 1.3,
+                    initiator real-weight FCIQMC, deterministic space 1e4.
   * molecule28   -- synthetic molecule, 28 spatial orbitals (56 spin orbitals,
                     64-bit keys), 15 electrons (8 up, 7 down), heat-bath
                     generator, initiator, real weights, semi-stochastic core,
@@ -66,6 +69,15 @@ def hubbard_system(L=8, nalpha=4, nbeta=4, t=1.0, U=4.0, periodic=True):
             "nalpha": nalpha, "nbeta": nbeta, "t": t, "U": U, "periodic": int(periodic)}
 
 
+def hubbard_lattice_system(lattice, nalpha, nbeta, t=1.0, U=4.0):
+    """Real-space Hubbard model on the periodic lattice spanned by the integer
+    rows of `lattice` (the paper's `lattice` input); |det| sites."""
+    lat = np.asarray(lattice, dtype=np.int64)
+    L = int(round(abs(np.linalg.det(lat.astype(np.float64)))))
+    return {"kind": "hubbard", "key_words": 1 if 2 * L <= 64 else (2 if 2 * L <= 128 else 8), "norb": L,
+            "nalpha": nalpha, "nbeta": nbeta, "t": t, "U": U, "periodic": 1, "lattice": lat.tolist()}
+
+
 def ueg_system(nel=14, norb=38, rs=1.0, key_words=None):
     nspin = 2 * norb
     if key_words is None:
@@ -99,6 +111,12 @@ WORKLOADS = {
     "ueg14": (lambda: ueg_system(14, 38, 1.0),
               lambda: qmc_params(tau=0.002, target_population=1e6, initiator=1,
                                  real_amplitudes=1, spawn_cutoff=0.1, seed=7)),
+    # half-filled 2D Hubbard model on the tilted 18-site square cluster, U/t = 1.3,
+    # semi-stochastic with a 1e4 deterministic space (the paper's Fig. semistoch b)
+    "hubbard18_2d": (lambda: hubbard_lattice_system([[3, 3], [3, -3]], 9, 9, t=1.0, U=1.3),
+                     lambda: qmc_params(tau=0.01, target_population=1e6, initiator=1, real_amplitudes=1,
+                                        spawn_cutoff=0.01, init_pop=100, semi_stoch_size=10000,
+                                        semi_stoch_start=500, seed=8)),
     # synthetic 28-orbital molecule, heat-bath, initiator, real weights, core 1e4
     "molecule28": (lambda: molecule_system(),
                    lambda: qmc_params(tau=0.01, target_population=1e7, initiator=1,

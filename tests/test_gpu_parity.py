@@ -257,3 +257,21 @@ def test_oversized_buckets_from_synthetic_start(annihilation):
         seen = max(seen, g.diagnostics()["max_bucket_spawns"])
     _same_records(g, c)
     assert seen > 64              # buckets beyond a 64-key tile occurred
+
+
+def test_hubbard_2d_tilted_8_site_integer_walkers():
+    """2D Hubbard model on the tilted 8-site cluster (lattice vectors (2, 2),
+    (2, -2)), integer walkers: bit-exact for 300 iterations."""
+    sysd = inputs.hubbard_lattice_system([[2, 2], [2, -2]], 4, 4, t=1.0, U=4.0)
+    q = inputs.qmc_params(tau=0.01, target_population=3000, seed=4)
+    sizes = _run_parity(sysd, q, 300)
+    assert max(sizes) > 500
+
+
+def test_hubbard18_2d_semistochastic():
+    """The half-filled 18-site cluster at U/t = 1.3 (the paper's semi-stochastic
+    example), initiator, real weights, a 500-determinant deterministic space
+    chosen at iteration 60."""
+    sysd, q = inputs.workload("hubbard18_2d", target_population=20000, semi_stoch_size=500, semi_stoch_start=60)
+    sizes = _run_parity(sysd, q, 120)
+    assert max(sizes) > 2000
