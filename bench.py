@@ -296,6 +296,8 @@ def run_ours(args, rank, world):
     eng.close()
     if rank == 0 and not args.no_configs:
         out["configs"] = config_lines(dev)
+        out["learned_proposal"] = learned_leg(dev)
+        out["tensor_core_gemm"] = tensor_core_leg(dev)
     return out
 
 
@@ -353,6 +355,28 @@ def config_lines(dev):
     ms = timed(eng, 400)
     r = eng.estimators()
     eng.close()
+    sysd, q = inputs.workload("hubbard18_2d", state_capacity=4_000_000, spawn_capacity=6_000_000)
+    eng = hande.Hande(sysd, q)
+    grown = 0
+    while grown < 5000:
+        eng.iterate(100)
+        grown += 100
+        if eng.estimators()["shift"][-1] != 0.0 and eng.iterations > q["semi_stoch_start"]:
+            break
+    eng.iterate(200)
+    eng.synchronize()
+    eng.estimators()
+    ms2 = timed(eng, 400)
+    r2 = eng.estimators()
+    ncore = int(eng.diagnostics()["ncore"])
+    eng.close()
+    out["hubbard18_2d"] = {"iterations": 400, "first_timed_iteration": int(r2["iter"][0]),
+                           "ms_per_iteration": ms2 / 400, "attempts_per_s": float(r2["natt"].sum()) / (ms2 / 1e3),
+                           "mean_walkers": float(r2["nw_post"].mean()) / 2 ** 32,
+                           "mean_determinants": float(r2["ndet"].mean()), "deterministic_space": ncore,
+                           "workload": "2D Hubbard model, tilted 18-site square cluster (lattice vectors (3,3), "
+                                       "(3,-3)), 9+9 electrons, U/t=1.3, initiator, real weights, tau=0.01, target "
+                                       "1e6 walkers, deterministic space 1e4 chosen at iteration 500"}
     out["ueg14"] = {"iterations": 400, "first_timed_iteration": int(r["iter"][0]),
                     "ms_per_iteration": ms / 400, "attempts_per_s": float(r["natt"].sum()) / (ms / 1e3),
                     "annihilated_spawns_per_s": float(r["nspawn"].sum()) / (ms / 1e3),
@@ -362,6 +386,103 @@ def config_lines(dev):
                                 "r_s=1, initiator n_a=3, real weights, spawn_cutoff 0.1, tau=0.002, target 1e6 "
                                 "walkers; grown from 1e4 walkers until the shift varies, +200 iterations"}
     return out
+
+
+def learned_leg(dev, iterations=4000):
+    """The learned excitation proposal against the uniform generator on the
+    same UEG run (14 electrons in 38 plane waves, r_s=1, initiator, real
+    weights, tau=0.002, target 2e5 walkers): each grown until the shift varies,
+    equilibrated 500 iterations, then `iterations` timed iterations (CUDA
+    events; the learned run keeps training every 10 iterations inside the timed
+    region).  Error-bar-normalised cost = (reblocked error of E_proj)^2 x time."""
+    import torch
+
+    from paper_1811_11679_gb300 import analysis, hande, inputs
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name in ("uniform", "learned"):
+        sysd, q = inputs.workload("ueg14", target_population=2e5, init_pop=2e4, state_capacity=1_500_000,
+                                  spawn_capacity=3_000_000, excit_gen=1 if name == "learned" else 0)
+        eng = hande.Hande(sysd, q)
+        if name == "learned":
+            eng.learn_proposal(width=256, batch=4096, period=10, learning_rate=2e-3, seed=1)
+        for _ in range(80):
+            eng.iterate(250)
+            if eng.estimators()["shift"][-1] != 0.0:
+                break
+        eng.iterate(500)
+        eng.synchronize()
+        eng.estimators()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        eng.iterate(iterations)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = eng.estimators()
+        e_ref, _ = eng.reference()
+        E, err = analysis.projected_energy(r, e_ref)
+        eng.close()
+        out[name] = {"E_proj": E, "error": err, "ms_per_iteration": ms / iterations,
+                     "attempts_per_s": float(r["natt"].sum()) / (ms / 1e3),
+                     "spawns_per_attempt": float(r["nspawn"].sum()) / max(float(r["natt"].sum()), 1.0),
+                     "mean_walkers": float(r["nw_post"].mean()) / 2 ** 32,
+                     "cost_error2_x_seconds": err * err * ms / 1e3}
+    u, l = out["uniform"], out["learned"]
+    out["efficiency_gain"] = u["cost_error2_x_seconds"] / l["cost_error2_x_seconds"]
+    out["agreement_sigma"] = abs(u["E_proj"] - l["E_proj"]) / float(np.hypot(u["error"], l["error"]))
+    out["workload"] = ("UEG 14e in 38 plane waves, r_s=1, initiator n_a=3, real weights, tau=0.002, target 2e5; "
+                       f"{iterations} timed iterations each; learned = MLP 3 layers width 256 (BF16 tensor cores), "
+                       "Adam every 10 iterations on 4096 recorded attempts")
+    return out
+
+
+def tensor_core_leg(dev, calls=20):
+    """The tensor-core GEMM alone (tcgen05 MMAs, TMA tiles, TMEM accumulators)
+    at the learned proposal's shapes: the table refresh of a 246-orbital basis
+    (2 x 246^2 rows, first layer K = 512 and hidden layer K = 256) and a
+    4096-sample training batch; FLOP/s against the measured BF16 burst peak."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande
+    peak = _bf16_peak()
+    stream = torch.cuda.current_stream(dev)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rows = []
+    g = torch.Generator(device="cuda").manual_seed(3)
+    for what, m, n, k in (("table refresh, 246 orbitals, layer 1", 121088, 256, 512),
+                          ("table refresh, 246 orbitals, layer 2", 121088, 256, 256),
+                          ("training batch 4096, layer 2", 4096, 256, 256)):
+        a = torch.randn((m, k), generator=g, device="cuda").to(torch.bfloat16)
+        b = torch.randn((n, k), generator=g, device="cuda").to(torch.bfloat16)
+        d = torch.empty((m, n), dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            hande.gemm_bf16(a, b, d, status=status)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(calls):
+            hande.gemm_bf16(a, b, d, status=status)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / calls
+        tf = 2.0 * m * n * k / (ms / 1e3) / 1e12
+        rows.append({"shape": what, "m": m, "n": n, "k": k, "us_per_launch": ms * 1e3, "tflops": tf,
+                     "frac": tf / peak[0]})
+    assert int(status.item()) == 0, "tensor-core GEMM wait timed out"
+    best = max(rows, key=lambda x: x["tflops"])
+    return {"bound": "tensor", "achieved": round(best["tflops"], 1), "peak": peak[0], "unit": "TFLOP/s",
+            "frac": round(best["frac"], 4), "traffic": None, "peak_source": peak[1], "kernel": "k_gemm_bf16_tn",
+            "shapes": rows}
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured (burst)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
 
 
 def cpu_baseline(sysd, q, keys, pops):

@@ -421,11 +421,13 @@ hande_status hande_learn_refresh(hande_ctx* ctx);
  * that are multiples of 8 and rows starting on 16-byte boundaries; D (m x n)
  * row-major FP32 with leading dimension ldd >= n.  Products of BF16 values are
  * exact and are accumulated in FP32 by tcgen05 MMAs (128 x 128 output tiles).
- * Runs on `cuda_stream` (a cudaStream_t) and synchronises it.
- * HANDE_ERR_INVALID on bad sizes/alignment, HANDE_ERR_TIMEOUT if a bounded
- * device-side wait gave up, HANDE_ERR_CUDA on a failed CUDA call. */
+ * Runs on `cuda_stream` (a cudaStream_t).  With d_status NULL the call
+ * synchronises the stream and returns HANDE_ERR_TIMEOUT if a bounded device
+ * wait gave up; with a caller-owned DEVICE word d_status it returns at once and
+ * the kernel ORs 1 into *d_status on such a failure.  HANDE_ERR_INVALID on bad
+ * sizes or alignment, HANDE_ERR_CUDA on a failed CUDA call. */
 hande_status hande_gemm_bf16(const uint16_t* d_a, int64_t lda, const uint16_t* d_b, int64_t ldb, float* d_d,
-                             int64_t ldd, int m, int n, int k, void* cuda_stream);
+                             int64_t ldd, int m, int n, int k, unsigned* d_status, void* cuda_stream);
 
 #ifdef __cplusplus
 }

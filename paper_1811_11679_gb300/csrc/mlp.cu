@@ -107,8 +107,16 @@ __device__ unsigned g_gemm_err;   // error word of hande_gemm_bf16 calls
 using namespace hande;
 
 extern "C" hande_status hande_gemm_bf16(const uint16_t* d_a, int64_t lda, const uint16_t* d_b, int64_t ldb,
-                                        float* d_d, int64_t ldd, int m, int n, int k, void* cuda_stream) {
+                                        float* d_d, int64_t ldd, int m, int n, int k, unsigned* d_status,
+                                        void* cuda_stream) {
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  if (m < 1 || n < 1 || k < 1 || lda < k || ldb < k || ldd < n || (lda & 7) || (ldb & 7) || !d_a || !d_b || !d_d ||
+      ((uintptr_t)d_a & 15) || ((uintptr_t)d_b & 15))
+    return HANDE_ERR_INVALID;
+  const char* why = "";
+  if (d_status) {   // asynchronous: a wait that gives up is ORed into the caller's word
+    return tc::launch_gemm(d_a, lda, d_b, ldb, d_d, ldd, m, n, k, d_status, s, &why) ? HANDE_OK : HANDE_ERR_CUDA;
+  }
   unsigned* err = nullptr;
   if (cudaGetSymbolAddress((void**)&err, tc::g_gemm_err) != cudaSuccess) {
     cudaGetLastError();
@@ -119,10 +127,7 @@ extern "C" hande_status hande_gemm_bf16(const uint16_t* d_a, int64_t lda, const 
     cudaGetLastError();
     return HANDE_ERR_CUDA;
   }
-  const char* why = "";
-  if (!tc::launch_gemm(d_a, lda, d_b, ldb, d_d, ldd, m, n, k, err, s, &why))
-    return (m < 1 || n < 1 || k < 1 || lda < k || ldb < k || ldd < n || (lda & 7) || (ldb & 7)) ? HANDE_ERR_INVALID
-                                                                                              : HANDE_ERR_CUDA;
+  if (!tc::launch_gemm(d_a, lda, d_b, ldb, d_d, ldd, m, n, k, err, s, &why)) return HANDE_ERR_CUDA;
   unsigned e = 0;
   if (cudaMemcpyAsync(&e, err, sizeof e, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {

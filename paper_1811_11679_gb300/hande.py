@@ -150,7 +150,7 @@ def load(build_if_needed: bool = True):
         lib.hande_batch_destroy.restype = None
         for name in ("hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_synchronize"):
             getattr(lib, name).restype = C.c_int
-        lib.hande_gemm_bf16.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P]
+        lib.hande_gemm_bf16.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P, P]
         lib.hande_gemm_bf16.restype = C.c_int
         u32p, i32p, fp = C.POINTER(C.c_uint32), C.POINTER(C.c_int32), C.POINTER(C.c_float)
         lib.hande_set_proposal.argtypes = [P, u32p]
@@ -473,10 +473,12 @@ class Hande:
         self.close()
 
 
-def gemm_bf16(a, b, out=None, stream=None):
+def gemm_bf16(a, b, out=None, stream=None, status=None):
     """D = A B^T on the tensor cores (include/hande.h, hande_gemm_bf16) for
     CUDA tensors: a (m x k) and b (n x k) bfloat16, row-major with unit column
-    stride; returns (or fills) a float32 (m x n) tensor."""
+    stride; returns (or fills) a float32 (m x n) tensor.  With `status` (an
+    int32 CUDA tensor) the call is asynchronous and a device-side timeout is
+    ORed into status[0]; without it the call synchronises."""
     import torch
     lib = load()
     m, k = a.shape
@@ -487,8 +489,9 @@ def gemm_bf16(a, b, out=None, stream=None):
         out = torch.empty((m, n), dtype=torch.float32, device=a.device)
     if stream is None:
         stream = torch.cuda.current_stream(a.device).cuda_stream
+    sp = C.c_void_p(status.data_ptr()) if status is not None else None
     rc = lib.hande_gemm_bf16(C.c_void_p(a.data_ptr()), a.stride(0), C.c_void_p(b.data_ptr()), b.stride(0),
-                             C.c_void_p(out.data_ptr()), out.stride(0), m, n, k, C.c_void_p(int(stream)))
+                             C.c_void_p(out.data_ptr()), out.stride(0), m, n, k, sp, C.c_void_p(int(stream)))
     if rc != 0:
         raise HandeError(rc, "hande_gemm_bf16")
     return out
