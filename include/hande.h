@@ -131,6 +131,13 @@ typedef struct {
                                  1 = UEG proposal table (the learned proposal's table, see
                                  hande_set_proposal / hande_learn_proposal), which starts
                                  with weight 1 on every drawable particle orbital */
+  int tau_search;             /* the paper's `tau_search`: 1 = until the population first
+                                 exceeds target_population, after each iteration
+                                 tau <- min(tau, 1 / R), R the largest |H_ij| / p_gen =
+                                 (|H_ij| inv_a) inv_b of any spawning attempt so far, so
+                                 that no attempt spawns more than one walker; tau is
+                                 fixed afterwards.  Synchronises once per iteration while
+                                 searching */
 } hande_qmc;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  `alloc`
@@ -162,6 +169,7 @@ typedef struct {
   int64_t ndet;        /* occupied determinants after annihilation */
   int64_t natt;        /* spawning attempts */
   int64_t nspawn;      /* nonzero spawns */
+  double tau;          /* the time step iteration t used */
 } hande_estimate;
 
 typedef struct hande_ctx hande_ctx;
@@ -270,6 +278,8 @@ typedef struct {
   int vary;           /* 1 once the population exceeded target_population */
   int core_active;    /* 1 once the deterministic space was chosen */
   int64_t ncore;      /* its size (0 when not active) */
+  double tau;         /* the time step of the next iteration */
+  double rmax;        /* time-step search: largest |H_ij| / p_gen seen (0 = none) */
 } hande_state;
 
 /* Copy the run state to *out and, if core_keys is not NULL and the

@@ -24,24 +24,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fciqmc_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 SYS_HUBBARD, SYS_UEG, SYS_MOLECULE = 0, 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile liboracle.so (g++, -O2, FMA contraction off) if it is stale."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile liboracle.so (g++, -O2, FMA contraction off) if it is stale; with
+    openmp=True the same source as liboracle_omp.so (-fopenmp), whose
+    orc_iterate_parallel runs the hash-partitioned form of the iteration."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    lib = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", "-o", tmp, _SRC]
+    if openmp:
+        cmd.insert(1, "-fopenmp")
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 class _System(C.Structure):
@@ -60,15 +66,14 @@ class _Qmc(C.Structure):
                 ("shift_period", C.c_int), ("initiator", C.c_int),
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int),
                 ("semi_stoch_start", C.c_int),
-                ("seed", C.c_uint64), ("replica", C.c_uint64), ("excit_gen", C.c_int)]
+                ("seed", C.c_uint64), ("replica", C.c_uint64), ("excit_gen", C.c_int), ("tau_search", C.c_int)]
 
 
-def _load():
-    global _lib
+def _load(openmp: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build())
+        if openmp in _libs:
+            return _libs[openmp]
+        lib = C.CDLL(build(openmp=openmp))
         P = C.c_void_p
         u64p, i64p, dp = C.POINTER(C.c_uint64), C.POINTER(C.c_int64), C.POINTER(C.c_double)
         lib.orc_philox.argtypes = [u64p, u64p, u64p]
@@ -94,7 +99,7 @@ def _load():
         lib.orc_set_walkers.argtypes = [P, u64p, i64p, C.c_int64]
         lib.orc_set_walkers.restype = C.c_int
         lib.orc_records.argtypes = [P, i64p, dp, i64p, i64p, dp, i64p, u64p, i64p, i64p, i64p,
-                                    i64p, C.c_int64]
+                                    i64p, dp, C.c_int64]
         lib.orc_records.restype = C.c_int64
         lib.orc_reference.argtypes = [P, u64p]
         lib.orc_hdiag.argtypes = [P, u64p]
@@ -113,14 +118,17 @@ def _load():
         lib.orc_set_proposal.restype = C.c_int
         lib.orc_proposal_mask.argtypes = [P, C.POINTER(C.c_uint8)]
         lib.orc_proposal_mask.restype = C.c_int
-        lib.orc_get_state.argtypes = [P, i64p, dp, i64p, C.POINTER(C.c_int)]
+        lib.orc_get_state.argtypes = [P, i64p, dp, i64p, C.POINTER(C.c_int), dp, dp]
         lib.orc_get_state.restype = None
-        lib.orc_set_state.argtypes = [P, C.c_int64, C.c_double, C.c_int64, C.c_int, u64p, C.c_int64]
+        lib.orc_set_state.argtypes = [P, C.c_int64, C.c_double, C.c_int64, C.c_int, C.c_double, C.c_double, u64p,
+                                      C.c_int64]
         lib.orc_set_state.restype = C.c_int
         lib.orc_heat_bath.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), u64p,
                                       C.c_int64]
         lib.orc_heat_bath.restype = C.c_int64
-        _lib = lib
+        lib.orc_iterate_parallel.argtypes = [P, C.c_int, C.c_int]
+        lib.orc_iterate_parallel.restype = C.c_int
+        _libs[openmp] = lib
         return lib
 
 
@@ -158,10 +166,13 @@ def fixed_product(a: float, b: float, round_half: bool) -> int:
 
 class Oracle:
     """One FCIQMC run on the CPU.  ``system``/``qmc`` are plain dicts (see
-    paper_1811_11679_gb300.inputs for the keys)."""
+    paper_1811_11679_gb300.inputs for the keys).  With ``threads`` the run uses
+    the OpenMP build and iterates in the hash-partitioned form on that many
+    threads (0 = all cores); the results are the serial ones bit for bit."""
 
-    def __init__(self, system: dict, qmc: dict):
-        lib = _load()
+    def __init__(self, system: dict, qmc: dict, threads: int | None = None):
+        self.threads = threads
+        lib = _load(openmp=threads is not None)
         self._lib = lib
         s = _System()
         kind = {"hubbard": SYS_HUBBARD, "ueg": SYS_UEG, "molecule": SYS_MOLECULE}[system["kind"]]
@@ -205,6 +216,7 @@ class Oracle:
         q.seed = int(qmc["seed"])
         q.replica = int(qmc.get("replica", 0))
         q.excit_gen = int(qmc.get("excit_gen", 0))
+        q.tau_search = int(qmc.get("tau_search", 0))
         h = lib.orc_create(C.byref(s), C.byref(q))
         if not h:
             raise ValueError("oracle rejected the system/qmc parameters")
@@ -219,7 +231,10 @@ class Oracle:
             self._h = None
 
     def iterate(self, n: int = 1) -> None:
-        self._lib.orc_iterate(self._h, int(n))
+        if self.threads is None:
+            self._lib.orc_iterate(self._h, int(n))
+        elif self._lib.orc_iterate_parallel(self._h, int(n), int(self.threads)) != 0:
+            raise RuntimeError("the oracle was built without OpenMP")
 
     @property
     def e_ref(self) -> float:
@@ -260,9 +275,9 @@ class Oracle:
     def records(self) -> dict:
         cols = {}
         names = ["iter", "shift", "nw_pre", "n0", "num", "num_hi", "num_lo", "nw_post", "ndet",
-                 "natt", "nspawn"]
+                 "natt", "nspawn", "tau"]
         types = [np.int64, np.float64, np.int64, np.int64, np.float64, np.int64, np.uint64,
-                 np.int64, np.int64, np.int64, np.int64]
+                 np.int64, np.int64, np.int64, np.int64, np.float64]
         n = max(1, self._lib.orc_nrec(self._h))
         arrs = [np.zeros(n, dtype=t) for t in types]
         ptrs = []
@@ -338,17 +353,20 @@ class Oracle:
         """Restart snapshot beyond the walker list: (dict with iter, shift,
         nw_ref, vary, core_active, ncore; deterministic-space keys[ncore, W])."""
         it, sh, nw, va = C.c_int64(), C.c_double(), C.c_int64(), C.c_int()
-        self._lib.orc_get_state(self._h, C.byref(it), C.byref(sh), C.byref(nw), C.byref(va))
+        tau, rmax = C.c_double(), C.c_double()
+        self._lib.orc_get_state(self._h, C.byref(it), C.byref(sh), C.byref(nw), C.byref(va), C.byref(tau),
+                                C.byref(rmax))
         core = self.core()
         return ({"iter": it.value, "shift": sh.value, "nw_ref": nw.value, "vary": va.value,
-                 "core_active": int(len(core) > 0), "ncore": len(core)}, core)
+                 "core_active": int(len(core) > 0), "ncore": len(core), "tau": tau.value,
+                 "rmax": rmax.value}, core)
 
     def set_state(self, state: dict, core_keys=None) -> None:
         """Restore a snapshot (after set_walkers of its list)."""
         n = int(state["ncore"]) if state.get("core_active") else 0
         k, kp = _u64(np.zeros((1, self.W)) if n == 0 else np.asarray(core_keys).reshape(-1, self.W))
         rc = self._lib.orc_set_state(self._h, int(state["iter"]), float(state["shift"]), int(state["nw_ref"]),
-                                     int(state["vary"]), kp, n)
+                                     int(state["vary"]), float(state["tau"]), float(state["rmax"]), kp, n)
         if rc != 0:
             raise ValueError("a deterministic-space key is not in the walker list")
 

@@ -42,6 +42,9 @@
 #include <vector>
 #include <algorithm>
 #include <string>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -269,6 +272,7 @@ struct Record {
     int64_t num_hi;
     uint64_t num_lo;
     double num;
+    double tau;        /* the time step iteration t used */
 };
 
 struct Ctx {
@@ -293,6 +297,9 @@ struct Ctx {
      * cumulative integer weights over the particle orbital A (empty = off) */
     int excit_gen;
     std::vector<uint32_t> ptab_cum;
+    /* time-step search: the largest |H_ij| / p_gen of any attempt so far */
+    int tau_search;
+    double rmax;
     /* qmc */
     double tau, target, zeta, cutoff, init_pop, n_a;
     int period, initiator, real_amp, core_size, core_start;
@@ -738,140 +745,132 @@ inline int64_t iabs64(int64_t x) { return x < 0 ? -x : x; }
 void select_core(Ctx& c);
 void install_core(Ctx& c, std::vector<Det> keys);
 
-void iterate_once(Ctx& c) {
-    const int64_t t = ++c.iter;
-    Record rec;
-    memset(&rec, 0, sizeof rec);
-    rec.iter = t;
-
-    /* (1) estimators on M(t-1): N_w, N_0, numerator sum_{j != 0} N_j H_0j (App. A.1) */
-    i128 num = 0;
-    for (size_t i = 0; i < c.main.size(); ++i) {
-        const Walker& wk = c.main[i];
-        rec.nw_pre += iabs64(wk.pop);
-        if (is_d0(c, wk.key)) {
-            rec.n0 = wk.pop;
-            continue;
-        }
-        if (wk.pop == 0 || exc_level(c, c.d0, wk.key) > 2) continue;
-        double h0j = h_elem(c, wk.key, c.d0);
-        num += fixed_term(wk.pop, h0j);
+/* (1) estimator terms of one entry of M(t-1): N_w, N_0 and the numerator
+ * sum_{j != 0} N_j H_0j (App. A.1) */
+void estimator_terms(const Ctx& c, const Walker& wk, int64_t& nw, int64_t& n0, i128& num) {
+    nw += iabs64(wk.pop);
+    if (is_d0(c, wk.key)) {
+        n0 = wk.pop;
+        return;
     }
-    rec.num_hi = (int64_t)(num >> 64);
-    rec.num_lo = (uint64_t)num;
-    rec.num = from_fixed(num);
+    if (wk.pop == 0 || exc_level(c, c.d0, wk.key) > 2) return;
+    double h0j = h_elem(c, wk.key, c.d0);
+    num += fixed_term(wk.pop, h0j);
+}
 
-    /* (2) initiator flags (Sec. 2.1) */
-    std::vector<int> init(c.main.size(), 1);
-    if (c.initiator)
-        for (size_t i = 0; i < c.main.size(); ++i) {
-            const Walker& wk = c.main[i];
-            init[i] = (iabs64(wk.pop) > c.init_thr) || is_d0(c, wk.key) || wk.core;
-        }
+/* (2) initiator flag (Sec. 2.1) */
+int initiator_flag(const Ctx& c, const Walker& wk) {
+    if (!c.initiator) return 1;
+    return (iabs64(wk.pop) > c.init_thr) || is_d0(c, wk.key) || wk.core;
+}
 
-    /* (3) spawning from every occupied determinant (Sec. 2.4) */
-    std::vector<Spawn> spawned;
-    for (size_t i = 0; i < c.main.size(); ++i) {
-        const Walker& wk = c.main[i];
-        if (wk.pop == 0) continue;
-        uint64_t mag = (uint64_t)iabs64(wk.pop);
-        uint64_t wdet[4];
-        draw(c, t, SENTINEL_DET, wk.key, wdet);
-        uint64_t natt = mag >> 32;
-        if (c.real_amp) {
-            uint64_t frac = mag & 0xffffffffull;
-            if ((wdet[0] >> 32) < frac) natt += 1;
-        }
-        rec.natt += (int64_t)natt;
-        int psign = wk.pop < 0 ? -1 : 1;
-        for (uint64_t a = 0; a < natt; ++a) {
-            uint64_t w[4];
-            draw(c, t, a, wk.key, w);
-            Excit ex = generate(c, wk.key, w);
-            if (ex.null) continue;
-            if (ex.hij == 0.0) continue;
-            if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
-            /* spawn weight tau |H_ij| / p_gen = |H_ij| * ct, ct = (tau inv_a) inv_b,
-             * taken exactly in walker fixed point (one rounding of the product) */
-            double ct = (c.tau * ex.inv_a) * ex.inv_b;
-            int64_t q;
-            if (!c.real_amp) {
-                /* floor(m) walkers, one more with probability frac(m) (frac to 2^-32) */
-                uint64_t f = fixed_product(fabs(ex.hij), ct, 0);
-                uint64_t k = f >> 32;
-                if ((w[3] >> 32) < (f & 0xffffffffull)) k += 1;
-                if (k == 0) continue;
-                q = k >= (1ull << 30) ? (int64_t)AMOUNT_MAX : (int64_t)(k << 32);
-            } else {
-                uint64_t r = fixed_product(fabs(ex.hij), ct, 1);
-                if (r < c.cutoff_fixed) {   /* kept, as the cutoff, with probability r / cutoff */
-                    if (draw_index(w[3], c.cutoff_fixed) < r) r = c.cutoff_fixed;
-                    else continue;
-                }
-                if (r == 0) continue;
-                q = (int64_t)r;
-            }
-            int hs = ex.hij < 0.0 ? -1 : 1;
-            Spawn s;
-            s.key = ex.child;
-            s.amount = (-hs * psign) < 0 ? -q : q;
-            s.init = init[i];
-            spawned.push_back(s);
-        }
+/* (3) the spawning attempts of one determinant (Sec. 2.4); appends its spawns */
+void spawn_from(const Ctx& c, int64_t t, const Walker& wk, int init, std::vector<Spawn>& spawned, int64_t& natt_tot,
+                double& rmax) {
+    if (wk.pop == 0) return;
+    uint64_t mag = (uint64_t)iabs64(wk.pop);
+    uint64_t wdet[4];
+    draw(c, t, SENTINEL_DET, wk.key, wdet);
+    uint64_t natt = mag >> 32;
+    if (c.real_amp) {
+        uint64_t frac = mag & 0xffffffffull;
+        if ((wdet[0] >> 32) < frac) natt += 1;
     }
-    rec.nspawn = (int64_t)spawned.size();
-
-    /* (4) death / cloning for determinants outside the core, from N(t-1) */
-    std::vector<int64_t> newpop(c.main.size());
-    for (size_t i = 0; i < c.main.size(); ++i) {
-        const Walker& wk = c.main[i];
-        newpop[i] = wk.pop;
-        if (wk.core || wk.pop == 0) continue;
-        double d = c.tau * (wk.hdiag - c.shift);
-        if (c.real_amp) {
-            double x = d * (double)wk.pop;
-            newpop[i] = wk.pop - llrint(x);
+    natt_tot += (int64_t)natt;
+    int psign = wk.pop < 0 ? -1 : 1;
+    for (uint64_t a = 0; a < natt; ++a) {
+        uint64_t w[4];
+        draw(c, t, a, wk.key, w);
+        Excit ex = generate(c, wk.key, w);
+        if (ex.null) continue;
+        if (ex.hij == 0.0) continue;
+        if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
+        /* |H_ij| / p_gen of the attempt, (|H| inv_a) inv_b, for the time-step search */
+        double ratio = (fabs(ex.hij) * ex.inv_a) * ex.inv_b;
+        if (ratio > rmax) rmax = ratio;
+        /* spawn weight tau |H_ij| / p_gen = |H_ij| * ct, ct = (tau inv_a) inv_b,
+         * taken exactly in walker fixed point (one rounding of the product) */
+        double ct = (c.tau * ex.inv_a) * ex.inv_b;
+        int64_t q;
+        if (!c.real_amp) {
+            /* floor(m) walkers, one more with probability frac(m) (frac to 2^-32) */
+            uint64_t f = fixed_product(fabs(ex.hij), ct, 0);
+            uint64_t k = f >> 32;
+            if ((w[3] >> 32) < (f & 0xffffffffull)) k += 1;
+            if (k == 0) continue;
+            q = k >= (1ull << 30) ? (int64_t)AMOUNT_MAX : (int64_t)(k << 32);
         } else {
-            uint64_t wdet[4];
-            draw(c, t, SENTINEL_DET, wk.key, wdet);
-            int64_t n = iabs64(wk.pop) >> 32;
-            double x = fabs(d) * (double)n;
-            double fl = floor(x);
-            int64_t k = (int64_t)fl;
-            if (draw_unit(wdet[1]) < x - fl) k += 1;
-            int64_t nn = d > 0.0 ? n - k : n + k;
-            newpop[i] = (wk.pop < 0 ? -nn : nn) * (int64_t)FIXED_ONE;
-        }
-    }
-
-    /* (5) semi-stochastic: exact projection inside the core (App. A.2) */
-    if (!c.core.empty()) {
-        std::vector<size_t> pos(c.core.size());
-        for (size_t r = 0; r < c.core.size(); ++r) {
-            size_t lo = 0, hi = c.main.size();
-            while (lo < hi) {
-                size_t mid = (lo + hi) / 2;
-                if (det_cmp(c.main[mid].key, c.core[r], c.W) < 0) lo = mid + 1; else hi = mid;
+            uint64_t r = fixed_product(fabs(ex.hij), ct, 1);
+            if (r < c.cutoff_fixed) {   /* kept, as the cutoff, with probability r / cutoff */
+                if (draw_index(w[3], c.cutoff_fixed) < r) r = c.cutoff_fixed;
+                else continue;
             }
-            pos[r] = lo;
+            if (r == 0) continue;
+            q = (int64_t)r;
         }
-        for (size_t r = 0; r < c.core.size(); ++r) {
-            i128 acc = 0;
-            for (size_t k = 0; k < c.core_rows[r].size(); ++k) {
-                int col = c.core_rows[r][k].first;
-                double h = c.core_rows[r][k].second;
-                acc += fixed_term(c.main[pos[col]].pop, h);
-            }
-            double y = from_fixed(acc);
-            int64_t pr = c.main[pos[r]].pop;
-            double v = y - c.shift * (double)pr;
-            double x = c.tau * v;
-            newpop[pos[r]] = pr - llrint(x);
-        }
+        int hs = ex.hij < 0.0 ? -1 : 1;
+        Spawn sp;
+        sp.key = ex.child;
+        sp.amount = (-hs * psign) < 0 ? -q : q;
+        sp.init = init;
+        spawned.push_back(sp);
     }
+}
 
-    /* (6) annihilation: sort the spawned array, combine equal keys, merge
-     *     into the sorted main list; initiator rule for new determinants. */
+/* (4) death / cloning of a non-core determinant from N(t-1): its new population */
+int64_t after_death(const Ctx& c, int64_t t, const Walker& wk) {
+    if (wk.core || wk.pop == 0) return wk.pop;
+    double d = c.tau * (wk.hdiag - c.shift);
+    if (c.real_amp) {
+        double x = d * (double)wk.pop;
+        return wk.pop - llrint(x);
+    }
+    uint64_t wdet[4];
+    draw(c, t, SENTINEL_DET, wk.key, wdet);
+    int64_t n = iabs64(wk.pop) >> 32;
+    double x = fabs(d) * (double)n;
+    double fl = floor(x);
+    int64_t k = (int64_t)fl;
+    if (draw_unit(wdet[1]) < x - fl) k += 1;
+    int64_t nn = d > 0.0 ? n - k : n + k;
+    return (wk.pop < 0 ? -nn : nn) * (int64_t)FIXED_ONE;
+}
+
+/* positions of the core determinants in the sorted main list */
+std::vector<size_t> core_positions(const Ctx& c) {
+    std::vector<size_t> pos(c.core.size());
+    for (size_t r = 0; r < c.core.size(); ++r) {
+        size_t lo = 0, hi = c.main.size();
+        while (lo < hi) {
+            size_t mid = (lo + hi) / 2;
+            if (det_cmp(c.main[mid].key, c.core[r], c.W) < 0) lo = mid + 1; else hi = mid;
+        }
+        pos[r] = lo;
+    }
+    return pos;
+}
+
+/* (5) semi-stochastic: exact projection of core row r (App. A.2), its new population */
+int64_t after_projection(const Ctx& c, size_t r, const std::vector<size_t>& pos) {
+    i128 acc = 0;
+    for (size_t k = 0; k < c.core_rows[r].size(); ++k) {
+        int col = c.core_rows[r][k].first;
+        double h = c.core_rows[r][k].second;
+        acc += fixed_term(c.main[pos[col]].pop, h);
+    }
+    double y = from_fixed(acc);
+    int64_t pr = c.main[pos[r]].pop;
+    double v = y - c.shift * (double)pr;
+    double x = c.tau * v;
+    return pr - llrint(x);
+}
+
+/* (6) annihilation: sort the spawns, combine equal keys, merge them into the
+ * sorted main entries main[mine[0]], main[mine[1]], ... (new populations in
+ * newpop), initiator rule for new determinants; appends the surviving
+ * entries in key order */
+void annihilate(const Ctx& c, int64_t t, std::vector<Spawn>& spawned, const std::vector<size_t>& mine,
+                const std::vector<int64_t>& newpop, std::vector<Walker>& out) {
     const int W = c.W;
     std::sort(spawned.begin(), spawned.end(), [W](const Spawn& x, const Spawn& y) {
         return det_cmp(x.key, y.key, W) < 0;
@@ -885,31 +884,29 @@ void iterate_once(Ctx& c) {
             merged.push_back(spawned[k]);
         }
     }
-    std::vector<Walker> out;
-    out.reserve(c.main.size() + merged.size());
     size_t im = 0, is = 0;
-    while (im < c.main.size() || is < merged.size()) {
+    while (im < mine.size() || is < merged.size()) {
         int r;
-        if (im == c.main.size()) r = 1;
+        if (im == mine.size()) r = 1;
         else if (is == merged.size()) r = -1;
-        else r = det_cmp(c.main[im].key, merged[is].key, W);
+        else r = det_cmp(c.main[mine[im]].key, merged[is].key, W);
         Walker nw;
         if (r < 0) {
-            nw = c.main[im];
-            nw.pop = newpop[im];
+            nw = c.main[mine[im]];
+            nw.pop = newpop[mine[im]];
             ++im;
         } else if (r == 0) {
-            nw = c.main[im];
-            nw.pop = newpop[im] + merged[is].amount;
+            nw = c.main[mine[im]];
+            nw.pop = newpop[mine[im]] + merged[is].amount;
             ++im; ++is;
         } else {
-            const Spawn& s = merged[is];
+            const Spawn& sp = merged[is];
             ++is;
-            if (c.initiator && !s.init) continue;
-            if (s.amount == 0) continue;
-            nw.key = s.key;
-            nw.pop = s.amount;
-            nw.hdiag = h_diag(c, s.key) - c.e_ref;
+            if (c.initiator && !sp.init) continue;
+            if (sp.amount == 0) continue;
+            nw.key = sp.key;
+            nw.pop = sp.amount;
+            nw.hdiag = h_diag(c, sp.key) - c.e_ref;
             nw.core = 0;
         }
         bool keep_always = nw.core || is_d0(c, nw.key);
@@ -925,9 +922,11 @@ void iterate_once(Ctx& c) {
         if (nw.pop == 0 && !keep_always) continue;
         out.push_back(nw);
     }
-    c.main.swap(out);
+}
 
-    /* (7) shift update (Sec. 2.1): S <- S - zeta/(A tau) ln(N_w(t)/N_w(t-A)) */
+/* (7) shift update (Sec. 2.1): S <- S - zeta/(A tau) ln(N_w(t)/N_w(t-A)), the
+ * record, and (8) the deterministic space "high", chosen once at start_iteration */
+void finish_iteration(Ctx& c, Record& rec, int64_t t) {
     int64_t nw_post = 0;
     for (size_t i = 0; i < c.main.size(); ++i) nw_post += iabs64(c.main[i].pop);
     if (c.vary) {
@@ -944,11 +943,132 @@ void iterate_once(Ctx& c) {
     rec.shift = c.shift;
     rec.nw_post = nw_post;
     rec.ndet = (int64_t)c.main.size();
+    rec.tau = c.tau;
     c.recs.push_back(rec);
-
-    /* (8) deterministic space "high": chosen once, at start_iteration */
+    /* time-step search (the tutorial's tau_search): until the population first
+     * exceeds the target, the next iteration's time step is the largest that
+     * keeps every spawn seen so far at or below one walker, never larger than now */
+    if (c.tau_search && !c.vary && c.rmax > 0.0) {
+        double cand = 1.0 / c.rmax;
+        if (cand < c.tau) c.tau = cand;
+    }
     if (c.core_size > 0 && t == c.core_start) select_core(c);
 }
+
+/* One FCIQMC iteration (Sec. 2.1 / 2.4, App. B), steps (1)-(8) in order. */
+void iterate_once(Ctx& c) {
+    const int64_t t = ++c.iter;
+    Record rec;
+    memset(&rec, 0, sizeof rec);
+    rec.iter = t;
+    i128 num = 0;
+    for (size_t i = 0; i < c.main.size(); ++i) estimator_terms(c, c.main[i], rec.nw_pre, rec.n0, num);
+    rec.num_hi = (int64_t)(num >> 64);
+    rec.num_lo = (uint64_t)num;
+    rec.num = from_fixed(num);
+    std::vector<int> init(c.main.size());
+    for (size_t i = 0; i < c.main.size(); ++i) init[i] = initiator_flag(c, c.main[i]);
+    std::vector<Spawn> spawned;
+    for (size_t i = 0; i < c.main.size(); ++i) spawn_from(c, t, c.main[i], init[i], spawned, rec.natt, c.rmax);
+    rec.nspawn = (int64_t)spawned.size();
+    std::vector<int64_t> newpop(c.main.size());
+    for (size_t i = 0; i < c.main.size(); ++i) newpop[i] = after_death(c, t, c.main[i]);
+    if (!c.core.empty()) {
+        std::vector<size_t> pos = core_positions(c);
+        for (size_t r = 0; r < c.core.size(); ++r) newpop[pos[r]] = after_projection(c, r, pos);
+    }
+    std::vector<size_t> all(c.main.size());
+    for (size_t i = 0; i < all.size(); ++i) all[i] = i;
+    std::vector<Walker> out;
+    out.reserve(c.main.size() + spawned.size());
+    annihilate(c, t, spawned, all, newpop, out);
+    c.main.swap(out);
+    finish_iteration(c, rec, t);
+}
+
+#ifdef _OPENMP
+/* The same iteration on P threads, partitioned like the paper's parallel code
+ * (App. B, Parallelization): determinant D belongs to owner(D) = h(D) mod P
+ * (a SplitMix64 fold of its key words; the paper uses MurmurHash2).  Each
+ * thread takes one contiguous block of the list for the estimator terms,
+ * spawning, death and projection, and sends every spawn to its child's owner
+ * (the all-to-all exchange); each owner then sorts the spawns it received and
+ * merges them into its own determinants; the owners' sorted lists are merged.
+ * Random numbers are counter-based and all sums exact integers, so the result
+ * is the serial iteration's bit for bit. */
+int owner_of(const Ctx& c, const Det& d, int P) {
+    uint64_t x = 0x243F6A8885A308D3ull;
+    for (int i = 0; i < c.W; ++i) x = mix64(x ^ d.w[i]);
+    return (int)(x % (uint64_t)P);
+}
+
+void iterate_once_parallel(Ctx& c, int P) {
+    const int64_t t = ++c.iter;
+    Record rec;
+    memset(&rec, 0, sizeof rec);
+    rec.iter = t;
+    const size_t n = c.main.size();
+    std::vector<int64_t> nw(P, 0), n0(P, 0), natt(P, 0);
+    std::vector<double> rmx(P, 0.0);
+    std::vector<i128> num(P, 0);
+    std::vector<int> has0(P, 0);
+    std::vector<int64_t> newpop(n);
+    std::vector<std::vector<std::vector<Spawn>>> outbox(P, std::vector<std::vector<Spawn>>(P));
+    std::vector<std::vector<size_t>> mine(P);
+    std::vector<size_t> pos;
+    if (!c.core.empty()) pos = core_positions(c);
+#pragma omp parallel num_threads(P)
+    {
+        const int p = omp_get_thread_num();
+        const size_t beg = n * (size_t)p / (size_t)P, end = n * (size_t)(p + 1) / (size_t)P;
+        for (size_t i = beg; i < end; ++i) {
+            int64_t z = 0;
+            estimator_terms(c, c.main[i], nw[p], z, num[p]);
+            if (is_d0(c, c.main[i].key)) { n0[p] = z; has0[p] = 1; }
+        }
+        std::vector<Spawn> local;
+        for (size_t i = beg; i < end; ++i) {
+            local.clear();
+            spawn_from(c, t, c.main[i], initiator_flag(c, c.main[i]), local, natt[p], rmx[p]);
+            for (size_t k = 0; k < local.size(); ++k) outbox[p][owner_of(c, local[k].key, P)].push_back(local[k]);
+            newpop[i] = after_death(c, t, c.main[i]);
+        }
+#pragma omp barrier
+#pragma omp for schedule(static)
+        for (long r = 0; r < (long)c.core.size(); ++r) newpop[pos[r]] = after_projection(c, (size_t)r, pos);
+        /* annihilation by owner */
+        for (size_t i = 0; i < n; ++i)
+            if (owner_of(c, c.main[i].key, P) == p) mine[p].push_back(i);
+    }
+    for (int p = 0; p < P; ++p) {
+        if (rmx[p] > c.rmax) c.rmax = rmx[p];
+        rec.nw_pre += nw[p];
+        if (has0[p]) rec.n0 = n0[p];
+        rec.natt += natt[p];
+        for (int q = 0; q < P; ++q) rec.nspawn += (int64_t)outbox[p][q].size();
+    }
+    i128 tot = 0;
+    for (int p = 0; p < P; ++p) tot += num[p];
+    rec.num_hi = (int64_t)(tot >> 64);
+    rec.num_lo = (uint64_t)tot;
+    rec.num = from_fixed(tot);
+    std::vector<std::vector<Walker>> part(P);
+#pragma omp parallel num_threads(P)
+    {
+        const int p = omp_get_thread_num();
+        std::vector<Spawn> recv;
+        for (int q = 0; q < P; ++q) recv.insert(recv.end(), outbox[q][p].begin(), outbox[q][p].end());
+        annihilate(c, t, recv, mine[p], newpop, part[p]);
+    }
+    /* merge the owners' sorted lists */
+    const int W = c.W;
+    std::vector<Walker> out;
+    for (int p = 0; p < P; ++p) out.insert(out.end(), part[p].begin(), part[p].end());
+    std::sort(out.begin(), out.end(), [W](const Walker& x, const Walker& y) { return det_cmp(x.key, y.key, W) < 0; });
+    c.main.swap(out);
+    finish_iteration(c, rec, t);
+}
+#endif
 
 /* core = D0 plus the (size-1) other determinants of largest |N|, ties by key */
 void select_core(Ctx& c) {
@@ -1123,6 +1243,7 @@ typedef struct {
     int shift_period, initiator, real_amplitudes, semi_stoch_size, semi_stoch_start;
     uint64_t seed, replica;
     int excit_gen;      /* 0: the system's generator; 1: proposal table (UEG) */
+    int tau_search;     /* 1: time-step search until the population exceeds the target */
 } orc_qmc;
 
 void orc_philox(const uint64_t* ctr, const uint64_t* key, uint64_t* out) { philox4x64_10(ctr, key, out); }
@@ -1234,6 +1355,8 @@ void* orc_create(const orc_system* s, const orc_qmc* q) {
     c->seed = q->seed;
     c->replica = q->replica;
     c->excit_gen = q->excit_gen;
+    c->tau_search = q->tau_search;
+    c->rmax = 0.0;
     if (c->excit_gen != 0 && !(c->excit_gen == 1 && c->kind == SYS_UEG)) { delete c; return nullptr; }
     /* thresholds in fixed point, saturated at the int64 range */
     c->target_fixed = c->target * 4294967296.0 >= 9223372036854775807.0
@@ -1293,6 +1416,20 @@ void orc_iterate(void* h, int n) {
     for (int i = 0; i < n; ++i) iterate_once(*c);
 }
 
+/* n iterations on `threads` threads (the hash-partitioned form; bit-identical
+ * to orc_iterate).  Returns 0, or -1 in a build without OpenMP. */
+int orc_iterate_parallel(void* h, int n, int threads) {
+#ifdef _OPENMP
+    Ctx* c = (Ctx*)h;
+    if (threads < 1) threads = omp_get_max_threads();
+    for (int i = 0; i < n; ++i) iterate_once_parallel(*c, threads);
+    return 0;
+#else
+    (void)h; (void)n; (void)threads;
+    return -1;
+#endif
+}
+
 int64_t orc_nrec(void* h) { return (int64_t)((Ctx*)h)->recs.size(); }
 int64_t orc_ndet(void* h) { return (int64_t)((Ctx*)h)->main.size(); }
 double orc_eref(void* h) { return ((Ctx*)h)->e_ref; }
@@ -1346,7 +1483,7 @@ int orc_set_walkers(void* h, const uint64_t* keys, const int64_t* pops, int64_t 
 /* records: 11 int64/double slots per iteration, see Record */
 int64_t orc_records(void* h, int64_t* iter, double* shift, int64_t* nw_pre, int64_t* n0, double* num,
                     int64_t* num_hi, uint64_t* num_lo, int64_t* nw_post, int64_t* ndet, int64_t* natt,
-                    int64_t* nspawn, int64_t cap) {
+                    int64_t* nspawn, double* tau, int64_t cap) {
     Ctx* c = (Ctx*)h;
     int64_t n = (int64_t)c->recs.size();
     if (n > cap) n = cap;
@@ -1354,7 +1491,7 @@ int64_t orc_records(void* h, int64_t* iter, double* shift, int64_t* nw_pre, int6
         const Record& r = c->recs[(size_t)i];
         iter[i] = r.iter; shift[i] = r.shift; nw_pre[i] = r.nw_pre; n0[i] = r.n0;
         num[i] = r.num; num_hi[i] = r.num_hi; num_lo[i] = r.num_lo; nw_post[i] = r.nw_post;
-        ndet[i] = r.ndet; natt[i] = r.natt; nspawn[i] = r.nspawn;
+        ndet[i] = r.ndet; natt[i] = r.natt; nspawn[i] = r.nspawn; tau[i] = r.tau;
     }
     return n;
 }
@@ -1543,20 +1680,24 @@ int orc_proposal_mask(void* h, uint8_t* mask) {
  * With counter-based random numbers the generator state is the iteration
  * number; the rest is the shift, its latch and reference population, and the
  * deterministic space. */
-void orc_get_state(void* h, int64_t* iter, double* shift, int64_t* nw_ref, int* vary) {
+void orc_get_state(void* h, int64_t* iter, double* shift, int64_t* nw_ref, int* vary, double* tau, double* rmax) {
     Ctx* c = (Ctx*)h;
     *iter = c->iter;
     *shift = c->shift;
     *nw_ref = c->nw_ref;
     *vary = c->vary;
+    *tau = c->tau;
+    *rmax = c->rmax;
 }
 
 /* after orc_set_walkers: restore the counters and the deterministic space
  * (ncore keys, all in the list; ncore = 0: none).  Returns 0, or -1 if a core
  * key is not in the list. */
-int orc_set_state(void* h, int64_t iter, double shift, int64_t nw_ref, int vary, const uint64_t* core_keys,
-                  int64_t ncore) {
+int orc_set_state(void* h, int64_t iter, double shift, int64_t nw_ref, int vary, double tau, double rmax,
+                  const uint64_t* core_keys, int64_t ncore) {
     Ctx* c = (Ctx*)h;
+    c->tau = tau;
+    c->rmax = rmax;
     std::vector<Det> keys;
     for (int64_t i = 0; i < ncore; ++i) {
         Det d;

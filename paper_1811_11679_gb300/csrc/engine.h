@@ -87,6 +87,12 @@ struct Engine {
   uint8_t* pmask_dev = nullptr;
   std::vector<uint8_t> pmask;
   Learner* learn = nullptr;
+  // time-step search: requested, still running (until the population first
+  // exceeds the target); host copies of the tau-dependent heat-bath amounts
+  bool tau_search_on = false, tau_searching = false;
+  double inv_double = 0.0;
+  std::vector<double> hb_v, hb_inv;
+  std::vector<ulonglong2> hb_ent;
   bool failed = false;
   unsigned err_bits = 0;
   std::string err;

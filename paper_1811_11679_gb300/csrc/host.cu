@@ -403,6 +403,26 @@ T* upload(Engine& E, const std::vector<T>& v) {
   return d;
 }
 
+// The time step and every factor of the spawn weight that contains it:
+// (tau inv_a) for each generator and the heat-bath entries' fixed-point amounts
+// of |<pq||ab>| ((tau inv_a) inv_b), uploaded when `to_device`.
+void set_tau(Engine& E, double tau, bool to_device) {
+  SysDev& sd = E.P.sys;
+  E.P.tau = tau;
+  sd.c_hub = tau * sd.inv_hub;
+  sd.c_ueg[0] = tau * sd.inv_ueg[0];
+  sd.c_ueg[1] = tau * sd.inv_ueg[1];
+  sd.c_single[0] = tau * sd.inv_single[0];
+  sd.c_single[1] = tau * sd.inv_single[1];
+  sd.c_tab = tau * sd.inv_tab;
+  const double c_double = tau * E.inv_double;
+  for (size_t k = 0; k < E.hb_ent.size(); ++k)
+    E.hb_ent[k].x = host_fixed_amount(std::fabs(E.hb_v[k]), c_double * E.hb_inv[k], sd.half != 0);
+  if (to_device && !E.hb_ent.empty())
+    CK(cudaMemcpyAsync(const_cast<ulonglong2*>(sd.hb_ent), E.hb_ent.data(), E.hb_ent.size() * sizeof(ulonglong2),
+                       cudaMemcpyHostToDevice, E.stream));
+}
+
 unsigned read_error(Engine& E) {
   unsigned e = 0;
   CK(cudaMemcpyAsync(&e, (char*)E.P.st + offsetof(DevState, error), sizeof(e), cudaMemcpyDeviceToHost, E.stream));
@@ -427,6 +447,36 @@ hande_status map_error(Engine& E, unsigned e) {
   else if (e & ERR_STATE_CAPACITY) E.err = "walker-list capacity exceeded (raise state_capacity)";
   else E.err = "bucket capacity exceeded";
   return HANDE_ERR_CAPACITY;
+}
+
+void drop_graphs(Engine& E, int core);
+
+// After an iteration while the time-step search runs: if the population has
+// exceeded the target the search ends (tau stays); otherwise
+// tau <- min(tau, 1 / R) with R the largest |H| / p_gen of any attempt so far.
+void tau_search_step(Engine& E) {
+  DevState hs;
+  CK(cudaMemcpyAsync(&hs, E.P.st, sizeof hs, cudaMemcpyDeviceToHost, E.stream));
+  CK(cudaStreamSynchronize(E.stream));
+  if (hs.error) return;   // reported by the next synchronising call
+  if (hs.vary) {
+    E.tau_searching = false;
+    E.P.tau_search = 0;
+    E.P.sys.want_r = 0;
+    drop_graphs(E, 0);
+    drop_graphs(E, 1);
+    return;
+  }
+  double r = 0.0;
+  std::memcpy(&r, &hs.rmax_bits, 8);
+  if (r > 0.0) {
+    const double cand = 1.0 / r;
+    if (cand < E.P.tau) {
+      set_tau(E, cand, true);
+      drop_graphs(E, 0);
+      drop_graphs(E, 1);
+    }
+  }
 }
 
 void ensure_graph(Engine& E, int cur, int core) {
@@ -734,22 +784,31 @@ hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, co
     {
       const int n = sd.nel;
       const double npairs = (double)((int64_t)n * (n - 1) / 2);
-      // 1/p_gen = inv_a inv_b; spawn-weight factor (tau inv_a) inv_b
-      const double tau = q.tau;
-      sd.c_hub = tau * ((double)sd.z * (double)n);
-      sd.c_ueg[0] = tau * ((npairs * (double)s.norb) / 2.0);
-      sd.c_ueg[1] = tau * ((npairs * (double)s.norb) / 1.0);
-      sd.c_single[0] = tau * (((double)n * (double)(s.norb - s.nalpha)) / sd.p_single);
-      sd.c_single[1] = tau * (((double)n * (double)(s.norb - s.nbeta)) / sd.p_single);
-      sd.c_tab = tau * npairs;
+      // 1/p_gen = inv_a inv_b; the spawn-weight factors (tau inv_a) inv_b follow in set_tau
+      sd.inv_hub = (double)sd.z * (double)n;
+      sd.inv_ueg[0] = (npairs * (double)s.norb) / 2.0;
+      sd.inv_ueg[1] = (npairs * (double)s.norb) / 1.0;
+      sd.inv_single[0] = ((double)n * (double)(s.norb - s.nalpha)) / sd.p_single;
+      sd.inv_single[1] = ((double)n * (double)(s.norb - s.nbeta)) / sd.p_single;
+      sd.inv_tab = npairs;
       sd.half = q.real_amplitudes ? 1 : 0;
-      // heat-bath entries: spawn amount of |<pq||ab>| ((tau inv_a) inv_b), then (a, b, sign)
-      const double c_double = tau * (npairs / sd.p_double);
-      T.hb_ent.resize(T.hb_ab.size());
-      for (size_t k = 0; k < T.hb_ab.size(); ++k) {
-        const double v = T.hb_v[k];
-        T.hb_ent[k].x = host_fixed_amount(std::fabs(v), c_double * T.hb_inv[k], sd.half != 0);
-        T.hb_ent[k].y = (unsigned long long)T.hb_ab[k] | ((v < 0.0 ? 1ull : 0ull) << 16);
+      E.inv_double = npairs / sd.p_double;
+      // heat-bath entries: (a, b, sign) now, the amounts in set_tau
+      E.hb_v = T.hb_v;
+      E.hb_inv = T.hb_inv;
+      E.hb_ent.resize(T.hb_ab.size());
+      for (size_t k = 0; k < T.hb_ab.size(); ++k)
+        E.hb_ent[k].y = (unsigned long long)T.hb_ab[k] | ((T.hb_v[k] < 0.0 ? 1ull : 0ull) << 16);
+      set_tau(E, q.tau, false);
+      T.hb_ent = E.hb_ent;
+      // time-step search: |<pq||ab>| / p_gen = (|<pq||ab>| inv_a) inv_b per entry
+      E.tau_search_on = E.tau_searching = q.tau_search != 0;
+      E.P.tau_search = q.tau_search != 0 ? 1 : 0;
+      sd.want_r = E.P.tau_search;
+      if (q.tau_search && !T.hb_v.empty()) {
+        std::vector<double> R(T.hb_v.size());
+        for (size_t k = 0; k < R.size(); ++k) R[k] = (std::fabs(T.hb_v[k]) * E.inv_double) * T.hb_inv[k];
+        sd.hb_R = upload(E, R);
       }
     }
     sd.kvec = upload(E, T.kvec);
@@ -877,6 +936,7 @@ hande_status hande_iterate(hande_ctx* ctx, int n) {
       E.cur ^= 1;
       E.host_iter += 1;
       if (learner_due(E)) learner_step(E);
+      if (E.tau_searching) tau_search_step(E);
       if (E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start) {
         hande_status es = map_error(E, read_error(E));
         if (es != HANDE_OK) return es;
@@ -964,6 +1024,7 @@ hande_status hande_estimators(hande_ctx* ctx, hande_estimate* out, int max, int*
       o.ndet = r.ndet;
       o.natt = r.natt;
       o.nspawn = r.nspawn;
+      o.tau = r.tau;
     }
     E.fetched += m;
     if (n_out) *n_out = (int)m;
@@ -1082,6 +1143,8 @@ hande_status hande_get_state(hande_ctx* ctx, hande_state* out, uint64_t* core_ke
     out->vary = hs.vary;
     out->core_active = E.core_active ? 1 : 0;
     out->ncore = E.core_active ? E.P.ncore : 0;
+    out->tau = E.P.tau;
+    std::memcpy(&out->rmax, &hs.rmax_bits, 8);
     if (!core_keys || out->ncore == 0) return HANDE_OK;
     if (out->ncore > core_cap) return HANDE_ERR_CAPACITY;
     // the core keys transposed on the device into the other list buffer (free
@@ -1104,6 +1167,8 @@ hande_status hande_set_state(hande_ctx* ctx, const hande_state* in, const uint64
       throw Fail{HANDE_ERR_INVALID, "bad run state (iteration, shift, vary latch or reference population)"};
     if (in->vary == 1 && in->nw_ref == 0)
       throw Fail{HANDE_ERR_INVALID, "a varying shift needs a nonzero reference population"};
+    if (!(in->tau > 0.0) || !std::isfinite(in->tau) || !(in->rmax >= 0.0) || !std::isfinite(in->rmax))
+      throw Fail{HANDE_ERR_INVALID, "bad time step or time-step-search maximum"};
     const int64_t ncore = in->core_active ? in->ncore : 0;
     if (in->core_active && (E.core_size <= 0 || ncore < 1 || ncore > E.core_size || !core_keys))
       throw Fail{HANDE_ERR_INVALID, "deterministic space: needs semi_stoch_size >= ncore >= 1 and its keys"};
@@ -1150,6 +1215,16 @@ hande_status hande_set_state(hande_ctx* ctx, const hande_state* in, const uint64
     CK(cudaMemcpyAsync((char*)st + offsetof(DevState, nw_ref), &in->nw_ref, 8, cudaMemcpyHostToDevice, E.stream));
     const int vary = in->vary;
     CK(cudaMemcpyAsync((char*)st + offsetof(DevState, vary), &vary, sizeof(int), cudaMemcpyHostToDevice, E.stream));
+    unsigned long long rbits = 0;
+    std::memcpy(&rbits, &in->rmax, 8);
+    CK(cudaMemcpyAsync((char*)st + offsetof(DevState, rmax_bits), &rbits, 8, cudaMemcpyHostToDevice, E.stream));
+    // the time step (and its spawn-weight factors) and the search state
+    set_tau(E, in->tau, true);
+    E.tau_searching = E.tau_search_on && !in->vary;
+    E.P.tau_search = E.tau_searching ? 1 : 0;
+    E.P.sys.want_r = E.P.tau_search;
+    drop_graphs(E, 0);
+    drop_graphs(E, 1);
     CK(cudaStreamSynchronize(E.stream));
     E.host_iter = in->iter;
     E.fetched = in->iter;

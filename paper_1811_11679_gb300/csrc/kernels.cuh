@@ -33,6 +33,7 @@ struct Record {
   int64_t num_hi;
   uint64_t num_lo;
   double num;
+  double tau;
 };
 
 struct DevState {
@@ -61,6 +62,7 @@ struct DevState {
   unsigned big_ticket;     // block-kernel tickets over all buckets (large-bucket pass)
   int64_t nbig;            // large buckets taken by block tiles
   int64_t ndefer;          // buckets the warp annihilation left to the block kernel
+  unsigned long long rmax_bits;   // time-step search: largest |H| / p_gen so far (bits of a double >= 0)
 };
 
 struct Params {
@@ -68,6 +70,7 @@ struct Params {
   double tau, cutoff, zeta;
   uint64_t cutoff_fixed;   // spawn cutoff in walker fixed point
   int real_amp, initiator, period, W;
+  int tau_search;          // record the largest |H| / p_gen of the attempts
   int64_t init_thr, target_fixed;
   uint64_t seed, replica;
   uint64_t d0[kMaxW];
@@ -634,6 +637,18 @@ struct AttemptQueues {
   uint8_t* pq_flg;
 };
 
+// time-step search: the warp's largest |H| / p_gen into the running maximum
+// (bits of non-negative doubles order like the doubles); whole warp
+__device__ __forceinline__ void ratio_max(const Params& P, double r) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(r);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xffffffffu, b, o);
+    b = x > b ? x : b;
+  }
+  if (warp_lane() == 0 && b) atomicMax(&P.st->rmax_bits, b);
+}
+
 // signed spawn amount (0 = nothing) from the fixed-point amount famt of the
 // weight tau |H| / p_gen (floored for integer walkers, rounded for real
 // weights), Philox word u and parent flags pf; sign -sign(H) sign(N_parent)
@@ -743,6 +758,7 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
   Key<W> child;
   int64_t amt = 0;
   uint8_t initf = 0;
+  double rmax = 0.0;
   if (lane < take) {
     const int e = sq_n - take + lane;
     const int64_t par = Q.sq_par[e];
@@ -755,6 +771,7 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
     key_flip<W>(child, a);
     const double hij = h_single<W, SYS>(P.sys, k, i, a);
     if (nonzero(hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
+      if (P.tau_search) rmax = __dmul_rn(fabs(hij), P.sys.inv_single[i & 1]);
       const uint64_t famt = fixed_amount(abs_bits(hij), dbl_bits(P.sys.c_single[i & 1]), P.sys.half);
       amt = spawn_amount(P, famt, sign_bit(hij), u, f);
       initf = (f & F_INIT) ? 1 : 0;
@@ -763,6 +780,7 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
   }
   sq_n -= take;
   __syncwarp();
+  if (P.tau_search) ratio_max(P, rmax);
   push_spawn<W>(P, Q, pq_n, have, child, amt, initf, sx);
 }
 
@@ -948,6 +966,7 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
     uint8_t initf = 0;
     uint64_t word = 0;
     uint16_t ia = 0;
+    double rmax = 0.0;
     if (g < gend) {
       const uint64_t a = (uint64_t)(g - abeg);
       const Key<W> k = load_key<W>(key, P.cap, par);
@@ -960,6 +979,7 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
         word = w.w;
         ia = (uint16_t)(ex.si | (ex.sa << 8));
       } else if (ex.ok && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
+        rmax = fmax(rmax, ex.rval);
         amt = spawn_amount(P, ex.famt, ex.hneg, w.w, f);
         child = ex.child;
         initf = (f & F_INIT) ? 1 : 0;
@@ -977,6 +997,7 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
       sq_n += __popc(sm);
       __syncwarp();
     }
+    if (P.tau_search) ratio_max(P, rmax);
     push_spawn<W>(P, Q, pq_n, have, child, amt, initf, sx);
     if (SYS == SYS_MOLECULE && sq_n >= 32)
       flush_singles<W, SYS>(P, Q, sq_n, pq_n, 32, key, fl, sx);
@@ -1869,6 +1890,7 @@ static __global__ void k_finalize(Params P, int cur) {
   r.ndet = st->ndet[cur ^ 1];
   r.natt = st->natt;
   r.nspawn = st->nspawn;
+  r.tau = P.tau;
   st->nspawn_prev = st->nspawn;
   st->nuniq_prev = st->nuniq;
   I128 num{(uint64_t)st->num[0], (int64_t)st->num[1]};

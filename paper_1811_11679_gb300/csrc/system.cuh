@@ -72,6 +72,11 @@ struct SysDev {
   // cumulative integer weights over the particle orbital A; c_tab = tau C(N,2)
   const uint32_t* ptab_cum;
   double c_tab;
+  // time-step search: the inv_a factors without tau (inv_b = 1 unless stated)
+  // and |<pq||ab>| inv_a inv_b per heat-bath entry; want_r = 1 while searching
+  int want_r;
+  double inv_hub, inv_ueg[2], inv_single[2], inv_tab;
+  const double* hb_R;
   // pair index P = j(j-1)/2 + i -> (i | j << 8), i < j < nel
   const uint16_t* pair_ij;
   // molecule: single-excitation terms G[(i*nspin + a)*nspin + k] = (ia|kk) - (ik|ka)
@@ -248,6 +253,7 @@ struct Excitation {
   int si, sa;
   int prow, pA;          // proposal table: the row and particle orbital drawn (prow < 0: none)
   uint32_t pqa, pQ;      //   the drawn weight q_A and the row total Q
+  double rval;           // |H| / p_gen = (|H| inv_a) inv_b when the system's want_r is set
   uint64_t famt;         // fixed-point amount of |H| tau / p_gen (floored or rounded)
   Key<W> child;
 };
@@ -281,8 +287,10 @@ __device__ __forceinline__ Key<W> spin_mask(int spin, int nspin) {
 }
 
 template <int W>
-__device__ __forceinline__ void finish(Excitation<W>& e, const SysDev& s, double hij, double ct) {
+__device__ __forceinline__ void finish(Excitation<W>& e, const SysDev& s, double hij, double ct, double inv_a,
+                                       double inv_b) {
   if (!nonzero(hij)) return;
+  if (s.want_r) e.rval = __dmul_rn(__dmul_rn(fabs(hij), inv_a), inv_b);
   e.famt = fixed_amount(abs_bits(hij), dbl_bits(ct), s.half);
   e.hneg = sign_bit(hij);
   e.ok = true;
@@ -300,6 +308,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
   e.hneg = false;
   e.famt = 0;
   e.prow = -1;
+  e.rval = 0.0;
   const int n = s.nel;
   if (SYS == SYS_HUBBARD) {
     int p = select_bit<W>(d, (int)draw_index(w.x, (uint64_t)n));
@@ -312,7 +321,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
     e.child = d;
     key_flip<W>(e.child, p);
     key_flip<W>(e.child, q);
-    finish<W>(e, s, h_single<W, SYS>(s, d, p, q), s.c_hub);
+    finish<W>(e, s, h_single<W, SYS>(s, d, p, q), s.c_hub, s.inv_hub, 1.0);
     return e;
   } else if (SYS == SYS_UEG) {
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;
@@ -355,7 +364,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
       key_flip<W>(e.child, a);
       key_flip<W>(e.child, b);
       const double inv_b = __ddiv_rn((double)Q, (double)(qa + qb));
-      finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo2, hi2), __dmul_rn(s.c_tab, inv_b));
+      finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo2, hi2), __dmul_rn(s.c_tab, inv_b), s.inv_tab, inv_b);
       return e;
     }
     int A = (int)draw_index(w.z, (uint64_t)s.norb);
@@ -373,7 +382,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
     key_flip<W>(e.child, q);
     key_flip<W>(e.child, a);
     key_flip<W>(e.child, b);
-    finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo, hi), s.c_ueg[(p ^ q) & 1]);
+    finish<W>(e, s, h_double<W, SYS>(s, d, p, q, lo, hi), s.c_ueg[(p ^ q) & 1], s.inv_ueg[(p ^ q) & 1], 1.0);
     return e;
   } else {
     if ((uint32_t)(w.x >> 32) < s.psingle_thr) {
@@ -420,6 +429,7 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
     e.famt = ent.x;
     e.hneg = (((meta >> 16) ^ n1 ^ n2) & 1) != 0;
     e.ok = true;
+    if (s.want_r) e.rval = __ldg(&s.hb_R[pr.x + lo]);
     return e;
   }
 }

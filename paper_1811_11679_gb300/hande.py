@@ -53,7 +53,7 @@ class _Qmc(C.Structure):
                 ("real_amplitudes", C.c_int), ("semi_stoch_size", C.c_int), ("semi_stoch_start", C.c_int),
                 ("seed", C.c_uint64), ("replica", C.c_uint64), ("state_capacity", C.c_int64),
                 ("spawn_capacity", C.c_int64), ("record_capacity", C.c_int), ("tile_capacity", C.c_int),
-                ("annihilation", C.c_int), ("excit_gen", C.c_int)]
+                ("annihilation", C.c_int), ("excit_gen", C.c_int), ("tau_search", C.c_int)]
 
 
 _ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -67,7 +67,7 @@ class _Allocator(C.Structure):
 class _Estimate(C.Structure):
     _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_pre", C.c_int64), ("n0", C.c_int64),
                 ("num_hi", C.c_int64), ("num_lo", C.c_uint64), ("num", C.c_double), ("nw_post", C.c_int64),
-                ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64)]
+                ("ndet", C.c_int64), ("natt", C.c_int64), ("nspawn", C.c_int64), ("tau", C.c_double)]
 
 
 class _Learning(C.Structure):
@@ -77,7 +77,7 @@ class _Learning(C.Structure):
 
 class _State(C.Structure):
     _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_ref", C.c_int64), ("vary", C.c_int),
-                ("core_active", C.c_int), ("ncore", C.c_int64)]
+                ("core_active", C.c_int), ("ncore", C.c_int64), ("tau", C.c_double), ("rmax", C.c_double)]
 
 
 class _Diag(C.Structure):
@@ -232,6 +232,7 @@ def _structs(system: dict, qmc: dict):
     q.tile_capacity = int(qmc.get("tile_capacity", 0))
     q.annihilation = int(qmc.get("annihilation", 0))
     q.excit_gen = int(qmc.get("excit_gen", 0))
+    q.tau_search = int(qmc.get("tau_search", 0))
     return s, q, keep
 
 

@@ -116,7 +116,8 @@ WORKLOADS = {
     "hubbard18_2d": (lambda: hubbard_lattice_system([[3, 3], [3, -3]], 9, 9, t=1.0, U=1.3),
                      lambda: qmc_params(tau=0.01, target_population=1e6, initiator=1, real_amplitudes=1,
                                         spawn_cutoff=0.01, init_pop=100, semi_stoch_size=10000,
-                                        semi_stoch_start=500, seed=8)),
+                                        semi_stoch_start=500, seed=8, state_capacity=12_000_000,
+                                        spawn_capacity=24_000_000)),
     # synthetic 28-orbital molecule, heat-bath, initiator, real weights, core 1e4
     "molecule28": (lambda: molecule_system(),
                    lambda: qmc_params(tau=0.01, target_population=1e7, initiator=1,

@@ -35,6 +35,9 @@ def _equal_records(ra, rb):
 CASES = {
     # integer walkers, the shift varying before the snapshot
     "hubbard8": (lambda: inputs.workload("hubbard8", target_population=2000), 300, 60),
+    # time-step search still running at the snapshot
+    "ueg_tau_search": (lambda: inputs.workload("ueg14", target_population=5000, init_pop=200, tau=0.05,
+                                               tau_search=1), 8, 40),
     # heat-bath, initiator, real weights, deterministic space chosen at 30
     "molecule": (lambda: (inputs.molecule_system(norb=10, nalpha=3, nbeta=3),
                           inputs.qmc_params(tau=0.01, target_population=3000, initiator=1, real_amplitudes=1,
@@ -53,8 +56,10 @@ def test_oracle_restart_follows_the_same_chain(case):
     state, core = a.state()
     if case == "hubbard8":
         assert state["vary"] == 1
-    else:
+    elif case == "molecule":
         assert state["core_active"] == 1 and state["ncore"] > 1
+    else:
+        assert state["vary"] == 0 and state["rmax"] > 0.0
     b = oracle.Oracle(sysd, q)
     b.set_walkers(keys, pops)
     b.set_state(state, core)
@@ -104,7 +109,7 @@ def test_gpu_restart_equals_uninterrupted_run(_cuda, case):
     keys, pops, hd, _ = a.walkers()
     state, core = a.state()
     ostate, ocore = ref.state()
-    for k in ("iter", "nw_ref", "vary", "core_active", "ncore"):
+    for k in ("iter", "nw_ref", "vary", "core_active", "ncore", "tau", "rmax"):
         assert state[k] == ostate[k], k
     assert np.float64(state["shift"]).view(np.int64) == np.float64(ostate["shift"]).view(np.int64)
     assert np.array_equal(core, ocore)
