@@ -380,7 +380,7 @@ def config_lines(dev):
                                "mean_walkers": float(r2["nw_post"].mean()) / 2 ** 32,
                                "mean_determinants": float(r2["ndet"].mean()), "deterministic_space": ncore,
                                "workload": "2D Hubbard model, tilted 18-site square cluster (lattice vectors (3,3), "
-                                           "(3,-3)), 9+9 electrons, U/t=1.3, initiator, real weights, tau=0.01, target "
+                                           "(3,-3)), 9+9 electrons, U/t=1.3, initiator, real weights, tau=0.002, target "
                                            "1e6 walkers, deterministic space 1e4 chosen at iteration 500"}
     except Exception as exc:   # an extra line must not lose the others
         out["hubbard18_2d"] = {"error": f"{type(exc).__name__}: {exc}"}

@@ -321,12 +321,17 @@ const char* hande_last_error(const hande_ctx* ctx);
  * walker lists and estimator records are bit-identical, so distinct seeds (or
  * distinct qmc.replica words) give independent Markov chains.
  *
- * Each replica owns a non-blocking CUDA stream created by the batch.  A batch
- * iteration is stream-ordered with respect to `cuda_stream` (a cudaStream_t,
- * NULL = legacy default stream): every replica stream waits for the work
- * already queued on it, one CUDA-graph launch per replica follows, and
- * `cuda_stream` then waits for all replicas.  Small replicas thereby run
- * concurrently on the GPU. */
+ * Replicas sharing a key width, system kind and annihilation tile form a group.
+ * A batch iteration is one CUDA graph on `cuda_stream` (a cudaStream_t, NULL =
+ * legacy default stream): each phase of a group's iteration is one kernel
+ * launch over (CTAs per replica, replicas), every replica reading its own
+ * parameter block; groups run on parallel graph branches.  Each replica also
+ * owns a non-blocking stream used by single-replica calls on it (walkers,
+ * estimators, hande_iterate of that replica alone), which is ordered with
+ * `cuda_stream` at the start and end of every batch call.  While a replica
+ * needs per-iteration host work (learned proposal, running time-step search)
+ * or has been advanced alone, the batch instead launches one captured graph
+ * per replica on the replica streams. */
 typedef struct hande_batch hande_batch;
 
 /* Build n >= 1 replicas from the caller-owned arrays sys[n] and qmc[n]
@@ -339,8 +344,23 @@ hande_status hande_batch_init(const hande_system* sys, const hande_qmc* qmc, int
 /* Advance every replica by n_iterations >= 0 iterations (asynchronous, iteration
  * by iteration across the replicas).  On a replica error the remaining launches
  * are skipped, `cuda_stream` still waits for what was launched, and the error of
- * the first failing replica is returned (its context holds the message). */
+ * the first failing replica is returned (its context holds the message;
+ * hande_batch_failed_replica names it).  Replicas may then differ by one
+ * iteration in their iteration counts. */
 hande_status hande_batch_iterate(hande_batch* b, int n_iterations);
+
+/* Index of the replica whose error the last hande_batch_iterate or
+ * hande_batch_synchronize returned (-1 if none). */
+int hande_batch_failed_replica(const hande_batch* b);
+
+/* Autotune the batched launch shape: for each candidate number of CTAs per
+ * replica (the single run's grid of each phase times a scale), time
+ * `iterations` batched iterations and keep the fastest.  The iterations are
+ * real (the replicas advance by (candidates + 1) x iterations); the walker
+ * lists do not depend on the shape.  *best_scale and *best_ms (ms per batched
+ * iteration) receive the choice (either may be NULL).  HANDE_ERR_STATE if a
+ * replica needs per-iteration host work.  Synchronises. */
+hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_scale, double* best_ms);
 
 /* Number of replicas (0 for NULL). */
 int hande_batch_size(const hande_batch* b);

@@ -785,9 +785,12 @@ void spawn_from(const Ctx& c, int64_t t, const Walker& wk, int init, std::vector
         if (ex.null) continue;
         if (ex.hij == 0.0) continue;
         if (wk.core && in_core(c, ex.child)) continue;   /* exact inside the core */
-        /* |H_ij| / p_gen of the attempt, (|H| inv_a) inv_b, for the time-step search */
-        double ratio = (fabs(ex.hij) * ex.inv_a) * ex.inv_b;
-        if (ratio > rmax) rmax = ratio;
+        /* |H_ij| / p_gen of the attempt, (|H| inv_a) inv_b, while the time-step
+         * search runs (until the population first exceeded the target) */
+        if (c.tau_search && !c.vary) {
+            double ratio = (fabs(ex.hij) * ex.inv_a) * ex.inv_b;
+            if (ratio > rmax) rmax = ratio;
+        }
         /* spawn weight tau |H_ij| / p_gen = |H_ij| * ct, ct = (tau inv_a) inv_b,
          * taken exactly in walker fixed point (one rounding of the product) */
         double ct = (c.tau * ex.inv_a) * ex.inv_b;

@@ -14,9 +14,28 @@ namespace hande {
 struct Engine;
 struct Learner;   // learned excitation proposal (learn.cu)
 
+// Replicas of one batch that share a key width, system kind and annihilation
+// tile: each phase of their iteration is one launch over a grid (CTAs per
+// replica, replicas) with the replicas' parameter blocks in device memory.
+struct BatchGroup {
+  std::vector<Engine*> eng;
+  Params* d_params = nullptr;   // [R] parameter blocks (device)
+  int R = 0;
+  int max_ncore = 0;
+  // CTAs per replica of each phase: scan-partitioned passes (det pass, attempt
+  // scan, split), spawning, scatter, warp merge, block merge, copy, diagonals
+  int g_scan = 1, g_attempt = 1, g_scatter = 1, g_mwarp = 1, g_merge = 1, g_copy = 1, g_hdiag = 1;
+};
+
 // launchers for one (key width, system kind) pair
 struct Ops {
   void (*iteration)(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_t* ev);
+  void (*iteration_batch)(BatchGroup& G, int cur, cudaStream_t s, cudaStream_t aux, cudaEvent_t fork,
+                          cudaEvent_t join);
+  // batched kernels (for shared-memory attributes and occupancy)
+  const void* batch_attempt_kernel;
+  const void* batch_merge_kernel;
+  const void* batch_merge_warp_kernel;
   void (*hdiag)(Engine& E, int cur, int64_t n, cudaStream_t s);
   void (*eref)(Engine& E, cudaStream_t s);
   void (*csr_count)(Engine& E, int32_t* rowcnt, cudaStream_t s);
@@ -68,6 +87,7 @@ struct Engine {
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int cur = 0;
   int64_t host_iter = 0;
+  int64_t epoch = 0;   // incremented whenever the parameter block changes (graphs dropped)
   int64_t fetched = 0;
   bool core_active = false;
   int core_size = 0, core_start = 0;
@@ -112,6 +132,10 @@ void learner_probabilities(Engine& E, const int32_t* rows, int n, float* probs);
 void learner_refresh(Engine& E);
 void learner_step(Engine& E);
 bool learner_due(const Engine& E);
+// batches (host.cu)
+bool engine_batchable(const Engine& E);
+bool engine_after_iteration(Engine& E);
+hande_status engine_select_core(Engine& E);
 
 }  // namespace hande
 

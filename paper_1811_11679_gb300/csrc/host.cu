@@ -498,6 +498,7 @@ void ensure_graph(Engine& E, int cur, int core) {
 }
 
 void drop_graphs(Engine& E, int core) {
+  E.epoch += 1;   // the parameter block may have changed: batch graphs are rebuilt too
   for (int c = 0; c < 2; ++c)
     if (E.graph[c][core]) {
       cudaGraphExecDestroy(E.graph[c][core]);
@@ -628,6 +629,26 @@ void build_core_tables(Engine& E) {
 
 }  // namespace
 
+// ================================================================= batch hooks
+namespace hande {
+
+// whether the replica can advance inside a batched graph (no per-iteration host
+// work: no learned proposal, no running time-step search, no latched failure)
+bool engine_batchable(const Engine& E) { return !E.failed && !E.learn && !E.tau_searching; }
+
+// bookkeeping after a batched iteration; true if the deterministic space is
+// due now (the caller orders E.stream after the iteration and calls
+// engine_select_core)
+bool engine_after_iteration(Engine& E) {
+  E.cur ^= 1;
+  E.host_iter += 1;
+  return E.core_size > 0 && !E.core_active && E.core_start > 0 && E.host_iter == E.core_start;
+}
+
+hande_status engine_select_core(Engine& E);
+
+}  // namespace hande
+
 // ================================================================= C ABI
 namespace {
 hande_status run_guarded(Engine* E, const std::function<hande_status()>& body) {
@@ -651,6 +672,17 @@ hande_status run_guarded(Engine* E, const std::function<hande_status()>& body) {
   }
 }
 }  // namespace
+
+namespace hande {
+hande_status engine_select_core(Engine& E) {
+  return run_guarded(&E, [&]() -> hande_status {
+    hande_status es = map_error(E, read_error(E));
+    if (es != HANDE_OK) return es;
+    select_core(E);
+    return HANDE_OK;
+  });
+}
+}  // namespace hande
 
 extern "C" {
 

@@ -133,6 +133,16 @@ struct Params {
   SysDev sys;
 };
 
+// a batched launch's parameter block: replica blockIdx.y's copied to shared
+// memory by the whole block (before any thread may leave the kernel)
+__device__ __forceinline__ void load_params(Params& sP, const Params* PP) {
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(PP + blockIdx.y);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(&sP);
+  static_assert(sizeof(Params) % 8 == 0, "parameter block copied in 8-byte words");
+  for (int i = threadIdx.x; i < (int)(sizeof(Params) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
 template <int W>
 __device__ __forceinline__ Key<W> ref_key(const Params& P) {
   Key<W> k;
@@ -239,7 +249,7 @@ __device__ __forceinline__ void block_chunk(int64_t n, int64_t& beg, int64_t& en
 
 // ------------------------------------------------------------------ det pass
 template <int W, int SYS>
-__global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) {
+__device__ __forceinline__ void d_det_pass(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   __shared__ int64_t sh64[32];
@@ -305,10 +315,19 @@ __global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) {
   I128 c = block_sum_i128(num, sh128);
   if (threadIdx.x == 0 && (c.lo | (uint64_t)c.hi)) atomic_add_i128(st->num, c);
 }
+template <int W, int SYS>
+__global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) { d_det_pass<W, SYS>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W, int SYS>
+__global__ void __launch_bounds__(kScanThreads) kb_det_pass(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_det_pass<W, SYS>(sP, cur);
+}
 
 // ------------------------------------------------------------------ generic scans
 // partials scanned by one block; total written to *total
-static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* total, DevState* st) {
+__device__ __forceinline__ void d_scan_partials_i64(int64_t* part, int nparts, int64_t* total, DevState* st) {
   if (st->error) return;
   __shared__ int64_t buf[kScanBlocks];
   __shared__ int64_t wsum[33];
@@ -318,6 +337,9 @@ static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* t
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) part[i] = buf[i];
   if (threadIdx.x == 0) *total = tot;
 }
+static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* total, DevState* st) {
+  d_scan_partials_i64(part, nparts, total, st);
+}
 // Exclusive scan of in[0, *n_ptr) into out by one block of 1024 threads, for
 // short arrays (bucket counts): chunks of 4096 loaded coalesced into shared
 // memory, 4 contiguous values per thread, block scan of the thread sums.  The
@@ -325,8 +347,8 @@ static __global__ void k_scan_partials_i64(int64_t* part, int nparts, int64_t* t
 // error.  With total_hi the values are two packed 32-bit counts, the totals of
 // the low and high halves go to *total and *total_hi.
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, const int64_t* n_ptr, int64_t* total,
-                                                    int64_t cap_check, DevState* st, int64_t* total_hi = nullptr) {
+__device__ __forceinline__ void d_scan_one(const Tin* in, Tout* out, const int64_t* n_ptr, int64_t* total,
+                                           int64_t cap_check, DevState* st, int64_t* total_hi) {
   if (st->error) return;
   constexpr int kPer = 4, kChunk = 1024 * kPer;
   __shared__ unsigned long long buf[kChunk];
@@ -391,12 +413,17 @@ __global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, con
     if (cap_check >= 0 && lo > cap_check) set_error(st, ERR_STATE_CAPACITY);
   }
 }
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, const int64_t* n_ptr, int64_t* total,
+                                                    int64_t cap_check, DevState* st, int64_t* total_hi = nullptr) {
+  d_scan_one<Tin, Tout>(in, out, n_ptr, total, cap_check, st, total_hi);
+}
 
 // out[i] = exclusive prefix of in over the block's chunk + part[block]; each
 // round takes 4 consecutive values per thread (4 x blockDim per round)
 template <typename T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,
-                                                             const int64_t* part, DevState* st) {
+__device__ __forceinline__ void d_scan_apply(const T* in, T* out, const int64_t* n_ptr, const int64_t* part,
+                                             DevState* st) {
   if (st->error) return;
   constexpr int kItems = 4;
   __shared__ T wsum[33];
@@ -443,6 +470,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out
   }
 }
 template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,
+                                                             const int64_t* part, DevState* st) {
+  d_scan_apply<T>(in, out, n_ptr, part, st);
+}
+template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const int64_t* n_ptr, int64_t* part,
                                                               DevState* st) {
   if (st->error) return;
@@ -455,12 +487,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// batched forms of the scans, pointers taken from replica blockIdx.y's block
+static __global__ void kb_scan_natt(const Params* PP, int nparts) {
+  const Params& P = PP[blockIdx.y];
+  d_scan_partials_i64(P.part, nparts, &P.st->natt, P.st);
+}
+static __global__ void __launch_bounds__(kScanThreads) kb_scan_att(const Params* PP, int cur) {
+  const Params& P = PP[blockIdx.y];
+  d_scan_apply<int64_t>(P.natt, P.att_begin, &P.st->ndet[cur], P.part, P.st);
+}
+static __global__ void __launch_bounds__(1024) kb_scan_buckets(const Params* PP) {
+  const Params& P = PP[blockIdx.y];
+  d_scan_one<uint32_t, uint32_t>(P.bcount, P.boff, &P.st->nbuckets, &P.st->scan_total, -1, P.st, nullptr);
+}
+static __global__ void __launch_bounds__(1024) kb_scan_kept(const Params* PP, int cur) {
+  const Params& P = PP[blockIdx.y];
+  d_scan_one<unsigned long long, unsigned long long>(P.tile_state, P.tile_inc, &P.st->nbuckets,
+                                                     &P.st->ndet[cur ^ 1], P.cap, P.st, &P.st->nnew);
+}
+
 // ------------------------------------------------------------------ buckets
 // Bucket b holds the main-list segment [b*sb, (b+1)*sb) and every spawn whose key
 // lies in [key[b*sb], key[(b+1)*sb]); sb is chosen so a bucket expects at most
 // half a tile of spawns (even if every one went to a new determinant).
 template <int W>
-__global__ void k_split(Params P, int cur) {
+__device__ __forceinline__ void d_split(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t n = st->ndet[cur];
@@ -507,6 +558,15 @@ __global__ void k_split(Params P, int cur) {
     for (int j = 0; j < W; ++j) P.split_key[j * P.cap + b] = src < n ? P.key[cur][j * P.cap + src] : 0ull;
   }
 }
+template <int W>
+__global__ void k_split(Params P, int cur) { d_split<W>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W>
+__global__ void kb_split(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_split<W>(sP, cur);
+}
 
 // ------------------------------------------------------------------ deterministic space
 template <int W>
@@ -552,7 +612,7 @@ __global__ void k_core_hash(Params P, uint32_t* table) {
   }
 }
 template <int W>
-__global__ void k_core_locate(Params P, int cur) {
+__device__ __forceinline__ void d_core_locate(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,8 +627,17 @@ __global__ void k_core_locate(Params P, int cur) {
   P.core_pos[r] = pos;
   P.core_x[r] = P.pop[cur][pos];
 }
+template <int W>
+__global__ void k_core_locate(Params P, int cur) { d_core_locate<W>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W>
+__global__ void kb_core_locate(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_core_locate<W>(sP, cur);
+}
 // one warp per core row: y_r = sum_c H'_rc N_c exactly, dN_r = -rint(tau (y_r - S N_r))
-static __global__ void k_core_spmv(Params P, int cur) {
+__device__ __forceinline__ void d_core_spmv(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -592,12 +661,26 @@ static __global__ void k_core_spmv(Params P, int cur) {
     P.core_delta[r] = -__double2ll_rn(x);
   }
 }
-static __global__ void k_core_apply(Params P, int cur) {
+static __global__ void k_core_spmv(Params P, int cur) { d_core_spmv(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+static __global__ void kb_core_spmv(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_core_spmv(sP, cur);
+}
+__device__ __forceinline__ void d_core_apply(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= P.ncore) return;
   P.pop[cur][P.core_pos[r]] += P.core_delta[r];
+}
+static __global__ void k_core_apply(Params P, int cur) { d_core_apply(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+static __global__ void kb_core_apply(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_core_apply(sP, cur);
 }
 
 // ------------------------------------------------------------------ attempts
@@ -848,7 +931,7 @@ __device__ __forceinline__ void record_sample(const Params& P, int64_t natt, int
 }
 
 template <int W, int SYS>
-__global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) {
+__device__ __forceinline__ void d_attempt(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   constexpr int KS = attempt_split_smem<W>();
@@ -1006,9 +1089,18 @@ __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) 
     flush_singles<W, SYS>(P, Q, sq_n, pq_n, sq_n, key, fl, sx);
   if (pq_n > 0) flush_spawns<W>(P, Q, pq_n, pq_n, sx);
 }
+template <int W, int SYS>
+__global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) { d_attempt<W, SYS>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W, int SYS>
+__global__ void __launch_bounds__(kAttemptThreads) kb_attempt(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_attempt<W, SYS>(sP, cur);
+}
 
 template <int W>
-__global__ void __launch_bounds__(256) k_scatter(Params P) {
+__device__ __forceinline__ void d_scatter(const Params& P) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t ns = st->nspawn < P.scap ? st->nspawn : P.scap;
@@ -1022,6 +1114,15 @@ __global__ void __launch_bounds__(256) k_scatter(Params P) {
     P.b_amt[dst] = P.s_amt[s];
     P.b_flag[dst] = (uint8_t)(m & 1u);
   }
+}
+template <int W>
+__global__ void __launch_bounds__(256) k_scatter(Params P) { d_scatter<W>(P); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W>
+__global__ void __launch_bounds__(256) kb_scatter(const Params* PP) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_scatter<W>(sP);
 }
 
 // ------------------------------------------------------------------ merge (annihilation)
@@ -1541,7 +1642,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int
 constexpr int kMergeThreads = 256;
 
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur, int staged) {
+__device__ __forceinline__ void d_merge(const Params& P, int cur, int staged) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t wsum[33];
@@ -1862,9 +1963,18 @@ __global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Param
   int64_t tot = block_sum<int64_t>(nwsum, sh64);
   if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)tot);
 }
+template <int W, int SYS>
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur, int staged) { d_merge<W, SYS>(P, cur, staged); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W, int SYS>
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) kb_merge(const Params* PP, int cur, int staged) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_merge<W, SYS>(sP, cur, staged);
+}
 
 // ------------------------------------------------------------------ finalize
-static __global__ void k_finalize(Params P, int cur) {
+__device__ __forceinline__ void d_finalize(const Params& P, int cur) {
   DevState* st = P.st;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (st->error) return;
@@ -1905,10 +2015,17 @@ static __global__ void k_finalize(Params P, int cur) {
   st->num[1] = 0;
   st->nw_post = 0;
 }
+static __global__ void k_finalize(Params P, int cur) { d_finalize(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+static __global__ void kb_finalize(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_finalize(sP, cur);
+}
 
 // diagonal elements of the determinants the merge created (list in natt[])
 template <int W, int SYS>
-__global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) {
+__device__ __forceinline__ void d_new_hdiag(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   const int nxt = cur ^ 1;
@@ -1918,6 +2035,15 @@ __global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) {
     Key<W> k = load_key<W>(P.key[nxt], P.cap, o);
     P.hdiag[nxt][o] = __dsub_rn(h_diag<W, SYS>(P.sys, k), st->e_ref);
   }
+}
+template <int W, int SYS>
+__global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) { d_new_hdiag<W, SYS>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W, int SYS>
+__global__ void __launch_bounds__(256) kb_new_hdiag(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_new_hdiag<W, SYS>(sP, cur);
 }
 
 // ------------------------------------------------------------------ utilities

@@ -194,6 +194,50 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
   mark(10);
 }
 
+// One iteration of every replica of a batch group: the same phases and graph
+// branches as enqueue_iteration (captured form), each phase one launch whose
+// grid's y dimension is the replica and x dimension the group's CTAs per
+// replica for that phase; replica r reads its parameter block G.d_params[r].
+template <int W, int SYS>
+void enqueue_iteration_batch(BatchGroup& G, int cur, cudaStream_t s, cudaStream_t aux, cudaEvent_t fork,
+                             cudaEvent_t join) {
+  const Params* PP = G.d_params;
+  const unsigned R = (unsigned)G.R;
+  const Engine& E0 = *G.eng[0];
+  const int ncb = (G.max_ncore + 255) / 256;
+  (void)cudaEventRecord(fork, s);
+  (void)cudaStreamWaitEvent(aux, fork, 0);
+  kb_split<W><<<dim3(G.g_scan, R), 256, 0, aux>>>(PP, cur);
+  if (G.max_ncore > 0) {
+    kb_core_locate<W><<<dim3(ncb, R), 256, 0, aux>>>(PP, cur);
+    kb_core_spmv<<<dim3((unsigned)(((int64_t)G.max_ncore * 32 + 255) / 256), R), 256, 0, aux>>>(PP, cur);
+  }
+  (void)cudaEventRecord(join, aux);
+  kb_det_pass<W, SYS><<<dim3(G.g_scan, R), kScanThreads, 0, s>>>(PP, cur);
+  kb_scan_natt<<<dim3(1, R), 1024, 0, s>>>(PP, G.g_scan);
+  kb_scan_att<<<dim3(G.g_scan, R), kScanThreads, 0, s>>>(PP, cur);
+  (void)cudaStreamWaitEvent(s, join, 0);
+  if (G.max_ncore > 0) kb_core_apply<<<dim3(ncb, R), 256, 0, s>>>(PP, cur);
+  kb_attempt<W, SYS><<<dim3(G.g_attempt, R), kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(PP, cur);
+  kb_scan_buckets<<<dim3(1, R), 1024, 0, s>>>(PP);
+  kb_scatter<W><<<dim3(G.g_scatter, R), 256, 0, s>>>(PP);
+  if (E0.merge_warp) {
+    (void)cudaEventRecord(fork, s);
+    (void)cudaStreamWaitEvent(aux, fork, 0);
+    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, aux>>>(PP, cur, 2);
+    (void)cudaEventRecord(join, aux);
+    kb_merge_warp<W, SYS><<<dim3(G.g_mwarp, R), kMwThreads, E0.ops.merge_warp_smem, s>>>(PP, cur);
+    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, cur, 1);
+    (void)cudaStreamWaitEvent(s, join, 0);
+    kb_scan_kept<<<dim3(1, R), 1024, 0, s>>>(PP, cur);
+    kb_merge_copy<W><<<dim3(G.g_copy, R), 256, 0, s>>>(PP, cur);
+  } else {
+    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, cur, 0);
+  }
+  kb_new_hdiag<W, SYS><<<dim3(G.g_hdiag, R), 256, 0, s>>>(PP, cur);
+  kb_finalize<<<dim3(1, R), 32, 0, s>>>(PP, cur);
+}
+
 template <int W, int SYS>
 void enqueue_hdiag(Engine& E, int cur, int64_t n, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);
@@ -326,6 +370,10 @@ template <int W, int SYS>
 Ops make_ops() {
   Ops o;
   o.iteration = &enqueue_iteration<W, SYS>;
+  o.iteration_batch = &enqueue_iteration_batch<W, SYS>;
+  o.batch_attempt_kernel = (const void*)&kb_attempt<W, SYS>;
+  o.batch_merge_kernel = (const void*)&kb_merge<W, SYS>;
+  o.batch_merge_warp_kernel = (const void*)&kb_merge_warp<W, SYS>;
   o.hdiag = &enqueue_hdiag<W, SYS>;
   o.eref = &enqueue_eref<W, SYS>;
   o.csr_count = &enqueue_csr_count<W, SYS>;

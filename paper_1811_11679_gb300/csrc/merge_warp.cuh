@@ -354,7 +354,7 @@ __device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int
 
 // One warp per bucket, buckets taken from a ticket counter (see the file comment).
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_warp(Params P, int cur) {
+__device__ __forceinline__ void d_merge_warp(const Params& P, int cur) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char mw_smem[];
   const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
@@ -447,13 +447,22 @@ __global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_war
   for (int o = 16; o; o >>= 1) nwsum += __shfl_xor_sync(0xffffffffu, nwsum, o);
   if (lane == 0 && nwsum) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)nwsum);
 }
+template <int W, int SYS>
+__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_warp(Params P, int cur) { d_merge_warp<W, SYS>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W, int SYS>
+__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) kb_merge_warp(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_merge_warp<W, SYS>(sP, cur);
+}
 
 // Compact the staged bucket lists into the new main list (one warp per bucket,
 // coalesced) and list the new determinants (natt[]) for their diagonals.  The
 // bucket's packed scan result gives both its output offset (low 32 bits) and
 // its offset in the new-determinant list (high 32 bits).
 template <int W>
-__global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
+__device__ __forceinline__ void d_merge_copy(const Params& P, int cur) {
   DevState* st = P.st;
   if (st->error) return;
   const int nxt = cur ^ 1;
@@ -500,6 +509,15 @@ __global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) {
       }
     }
   }
+}
+template <int W>
+__global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) { d_merge_copy<W>(P, cur); }
+// the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+template <int W>
+__global__ void __launch_bounds__(256) kb_merge_copy(const Params* PP, int cur) {
+  __shared__ Params sP;
+  load_params(sP, PP);
+  d_merge_copy<W>(sP, cur);
 }
 
 }  // namespace hande

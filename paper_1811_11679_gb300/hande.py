@@ -91,8 +91,8 @@ class _Diag(C.Structure):
 EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
            "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
            "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
-           "hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize",
-           "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
+           "hande_batch_init", "hande_batch_iterate", "hande_batch_failed_replica", "hande_batch_autotune",
+           "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize", "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
            "hande_learn_params", "hande_learn_gradients", "hande_learn_probabilities", "hande_learn_refresh",
            "hande_gemm_bf16"]
 
@@ -148,6 +148,10 @@ def load(build_if_needed: bool = True):
         lib.hande_batch_synchronize.argtypes = [P]
         lib.hande_batch_destroy.argtypes = [P]
         lib.hande_batch_destroy.restype = None
+        lib.hande_batch_failed_replica.argtypes = [P]
+        lib.hande_batch_failed_replica.restype = C.c_int
+        lib.hande_batch_autotune.argtypes = [P, C.c_int, dp, dp]
+        lib.hande_batch_autotune.restype = C.c_int
         for name in ("hande_batch_init", "hande_batch_iterate", "hande_batch_size", "hande_batch_synchronize"):
             getattr(lib, name).restype = C.c_int
         lib.hande_gemm_bf16.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int, C.c_int, C.c_int, P, P]
@@ -535,17 +539,31 @@ class HandeBatch:
     def __len__(self) -> int:
         return int(self._lib.hande_batch_size(self._h))
 
+    def _raise(self, rc, what):
+        r = int(self._lib.hande_batch_failed_replica(self._h))
+        msg = self._lib.hande_last_error(self.replicas[r]._h).decode() if r >= 0 else ""
+        err = HandeError(rc, f"{what}: replica {r}: {msg}")
+        err.replica = r
+        raise err
+
     def iterate(self, n: int = 1) -> None:
         rc = self._lib.hande_batch_iterate(self._h, int(n))
         if rc != 0:
-            msgs = [f"replica {r}: {v._lib.hande_last_error(v._h).decode()}"
-                    for r, v in enumerate(self.replicas) if v._lib.hande_last_error(v._h)]
-            raise HandeError(rc, "hande_batch_iterate: " + "; ".join(msgs))
+            self._raise(rc, "hande_batch_iterate")
 
     def synchronize(self) -> None:
         rc = self._lib.hande_batch_synchronize(self._h)
         if rc != 0:
-            raise HandeError(rc, "hande_batch_synchronize")
+            self._raise(rc, "hande_batch_synchronize")
+
+    def autotune(self, iterations: int = 5):
+        """Choose the batched launch shape by timing (include/hande.h,
+        hande_batch_autotune); returns (scale, ms per batched iteration)."""
+        f, ms = C.c_double(), C.c_double()
+        rc = self._lib.hande_batch_autotune(self._h, int(iterations), C.byref(f), C.byref(ms))
+        if rc != 0:
+            self._raise(rc, "hande_batch_autotune")
+        return f.value, ms.value
 
     def close(self) -> None:
         if self._h:

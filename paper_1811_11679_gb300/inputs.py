@@ -114,7 +114,7 @@ WORKLOADS = {
     # half-filled 2D Hubbard model on the tilted 18-site square cluster, U/t = 1.3,
     # semi-stochastic with a 1e4 deterministic space (the paper's Fig. semistoch b)
     "hubbard18_2d": (lambda: hubbard_lattice_system([[3, 3], [3, -3]], 9, 9, t=1.0, U=1.3),
-                     lambda: qmc_params(tau=0.01, target_population=1e6, initiator=1, real_amplitudes=1,
+                     lambda: qmc_params(tau=0.002, target_population=1e6, initiator=1, real_amplitudes=1,
                                         spawn_cutoff=0.01, init_pop=100, semi_stoch_size=10000,
                                         semi_stoch_start=500, seed=8, state_capacity=12_000_000,
                                         spawn_capacity=24_000_000)),

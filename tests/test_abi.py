@@ -76,8 +76,8 @@ def test_batch_arguments_rejected_before_any_device_call():
 
 def test_batch_binding_marshalling_and_errors(monkeypatch):
     """HandeBatch passes one (system, qmc) struct pair per replica, names the
-    failing replica's message on an error, and frees the batch once (its
-    replica views never free their contexts)."""
+    failing replica (hande_batch_failed_replica) and its message on an error,
+    and frees the batch once (its replica views never free their contexts)."""
     seen = {"destroy": 0}
 
     class FakeLib:
@@ -96,6 +96,9 @@ def test_batch_binding_marshalling_and_errors(monkeypatch):
 
         def hande_batch_iterate(self, h, k):
             return -3
+
+        def hande_batch_failed_replica(self, h):
+            return 1
 
         def hande_last_error(self, h):
             return b"spawn capacity exceeded" if h.value == 1001 else b""

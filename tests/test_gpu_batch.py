@@ -94,3 +94,64 @@ def test_batch_stream_ordering_with_torch():
         rec = g.estimators()
         assert len(rec["iter"]) == 50 and rec["iter"][-1] == 50
     b.close()
+
+
+def test_wide_key_batch_past_the_splitter_table():
+    """Batched graphs with 512-bit replicas whose bucket counts pass the
+    256-splitter on-chip table (UEG 14e in 66 orbitals from synthetic lists),
+    beside 128-bit replicas: every replica equals the oracle bit for bit."""
+    runs, lists = [], []
+    for r, (norb, ndet) in enumerate([(66, 60000), (66, 20000), (38, 30000)]):
+        s = inputs.ueg_system(14, norb, 1.0)
+        q = inputs.qmc_params(tau=0.002, target_population=1e7, initiator=1, real_amplitudes=1, spawn_cutoff=0.1,
+                              seed=5 + r, state_capacity=400_000, spawn_capacity=800_000)
+        runs.append((s, q))
+        lists.append(inputs.synthetic_walkers(s, ndet, 3.0 * ndet, seed=30 + r))
+    b = hande.HandeBatch([s for s, _ in runs], [q for _, q in runs])
+    cs = [oracle.Oracle(s, q) for s, q in runs]
+    for g, c, (k, p) in zip(b.replicas, cs, lists):
+        g.set_walkers(k, p)
+        c.set_walkers(k, p)
+    for it in range(3):
+        b.iterate(1)
+        for c in cs:
+            c.iterate(1)
+        for r, (g, c) in enumerate(zip(b.replicas, cs)):
+            _same_lists(g, c, f"{it + 1} (replica {r})")
+    assert b.replicas[0].diagnostics()["nbuckets"] > 256
+    for g, c in zip(b.replicas, cs):
+        _same_records(g, c)
+    b.close()
+
+
+def test_autotune_keeps_the_walker_lists():
+    """The autotuner changes only the launch shape: a tuned batch and an
+    untuned one give the same lists after the same number of iterations."""
+    runs = [inputs.workload("ueg14", target_population=20000, init_pop=2000, seed=s) for s in (1, 2, 3, 4)]
+    a = hande.HandeBatch([s for s, _ in runs], [q for _, q in runs])
+    b = hande.HandeBatch([s for s, _ in runs], [q for _, q in runs])
+    a.iterate(20)
+    b.iterate(20)
+    scale, ms = a.autotune(iterations=3)
+    assert 0.0 < scale <= 1.0 and ms > 0.0
+    done = a.replicas[0].iterations
+    b.iterate(done - 20)
+    a.iterate(10)
+    b.iterate(10)
+    for ga, gb in zip(a.replicas, b.replicas):
+        assert ga.iterations == gb.iterations
+        ka, pa, _, _ = ga.walkers()
+        kb, pb, _, _ = gb.walkers()
+        assert np.array_equal(ka, kb) and np.array_equal(pa, pb)
+    a.close()
+    b.close()
+
+
+def test_failing_replica_is_named():
+    s, q = inputs.workload("hubbard8")
+    b = hande.HandeBatch([s, s, s], [q, dict(q, spawn_capacity=64, replica=1), dict(q, replica=2)])
+    b.iterate(5)
+    with pytest.raises(hande.HandeError) as e:
+        b.synchronize()
+    assert e.value.status == -3 and e.value.replica == 1
+    b.close()
