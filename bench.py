@@ -297,7 +297,7 @@ def run_ours(args, rank, world):
     eng.close()
     if rank == 0 and not args.no_configs:
         for key, leg in (("configs", config_lines), ("learned_proposal", learned_leg),
-                         ("tensor_core_gemm", tensor_core_leg)):
+                         ("batched_replicas", batched_leg), ("tensor_core_gemm", tensor_core_leg)):
             try:
                 out[key] = leg(dev)
             except Exception as exc:   # one failing extra leg must not lose the headline line
@@ -443,6 +443,59 @@ def learned_leg(dev, iterations=4000):
                        f"{iterations} timed iterations each; learned = MLP 3 layers width 256 (BF16 tensor cores), "
                        "Adam every 10 iterations on 4096 recorded attempts")
     return out
+
+
+def batched_leg(dev, replicas=64, grow=300, steps=50):
+    """Batched replicas (inputs.batched_replicas: UEG 14 electrons in 38 or 66
+    orbitals, four r_s, uneven targets 1e4-1e6) advanced by the batched graphs
+    (one launch per phase per key-width group, launch shape autotuned) against
+    the same replicas advanced back to back on the plain path (each replica's
+    own captured iteration graph on its own stream, no host synchronisation),
+    both timed with CUDA events on the caller's stream.  Both forms produce the
+    same Markov chains bit for bit, so their error bars are equal and the time
+    ratio is the error-bar-normalised cost ratio."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande, inputs
+    stream = torch.cuda.current_stream(dev)
+    systems, qmcs = inputs.batched_replicas(replicas)
+    b = hande.HandeBatch(systems, qmcs)
+    b.iterate(grow)
+    scale, tuned_ms = b.autotune(iterations=3)
+    for v in b.replicas:
+        v.estimators()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms_b = timed(lambda: b.iterate(steps))
+    att_b = float(sum(v.estimators()["natt"].sum() for v in b.replicas))
+
+    def plain():
+        for _ in range(steps):
+            for v in b.replicas:
+                v.iterate(1)
+        for v in b.replicas:
+            v.synchronize()
+    ms_p = timed(plain)
+    att_p = float(sum(v.estimators()["natt"].sum() for v in b.replicas))
+    launches = sum(v.launches_per_iteration() for v in b.replicas)
+    b.close()
+    return {"replicas": replicas, "steps": steps, "grow_iterations": grow,
+            "batched": {"attempts_per_s": att_b / (ms_b / 1e3), "ms_per_step": ms_b / steps,
+                        "autotuned_scale": scale},
+            "plain_back_to_back": {"attempts_per_s": att_p / (ms_p / 1e3), "ms_per_step": ms_p / steps,
+                                   "kernel_launches_per_step": launches},
+            "speedup": (att_b / ms_b) / (att_p / ms_p),
+            "workload": f"{replicas} UEG replicas: 14 electrons in 38 or 66 spatial orbitals (128- or 512-bit "
+                        "keys), r_s 0.5/1/2/5, targets log-uniform in [1e4, 1e6], initiator, real weights, "
+                        "tau=0.002"}
 
 
 def tensor_core_leg(dev, calls=20):
