@@ -324,8 +324,10 @@ const char* hande_last_error(const hande_ctx* ctx);
  * Replicas sharing a key width, system kind and annihilation tile form a group.
  * A batch iteration is one CUDA graph on `cuda_stream` (a cudaStream_t, NULL =
  * legacy default stream): each phase of a group's iteration is one kernel
- * launch over (CTAs per replica, replicas), every replica reading its own
- * parameter block; groups run on parallel graph branches.  Each replica also
+ * launch over all its replicas, whose blocks a planner kernel divides among
+ * the replicas in proportion to their work (list length, last attempt count),
+ * every replica reading its own parameter block; groups run on parallel graph
+ * branches.  Each replica also
  * owns a non-blocking stream used by single-replica calls on it (walkers,
  * estimators, hande_iterate of that replica alone), which is ordered with
  * `cuda_stream` at the start and end of every batch call.  While a replica
@@ -353,8 +355,8 @@ hande_status hande_batch_iterate(hande_batch* b, int n_iterations);
  * hande_batch_synchronize returned (-1 if none). */
 int hande_batch_failed_replica(const hande_batch* b);
 
-/* Autotune the batched launch shape: for each candidate number of CTAs per
- * replica (the single run's grid of each phase times a scale), time
+/* Autotune the batched launch shape: for each candidate block budget (the
+ * single run's grid of each phase times a scale in {0.5, 1, 2, 4}), time
  * `iterations` batched iterations and keep the fastest.  The iterations are
  * real (the replicas advance by (candidates + 1) x iterations); the walker
  * lists do not depend on the shape.  *best_scale and *best_ms (ms per batched

@@ -4,11 +4,14 @@
 // Replicas that share a key width, system kind and annihilation tile form a
 // group.  One batched iteration is one CUDA graph: for every group, each phase
 // of the iteration (det pass, scans, spawning, scatter, annihilation, new
-// diagonals, shift) is ONE launch whose grid covers (CTAs per replica,
-// replicas); replica r's kernels read its parameter block from a device array,
-// so every replica computes exactly what its single run would (results are
-// independent of the grid size).  Groups run on their own graph branches.  The
-// CTAs per replica of each phase are chosen by an autotuner that times whole
+// diagonals, shift) is ONE launch over all its replicas; replica r's blocks
+// read its parameter block from a device array, so every replica computes
+// exactly what its single run would (results are independent of how many
+// blocks a replica gets).  Groups run on their own graph branches.  A planner
+// kernel at the start of each batched iteration divides every
+// phase's block budget among the replicas in proportion to their work (list
+// length, last attempt count), so replicas of very uneven sizes finish each
+// phase together; the budgets are chosen by an autotuner that times whole
 // batched iterations.  A replica that needs per-iteration host work (a learned
 // proposal or a running time-step search) or that is out of step with the rest
 // makes the batch fall back to one captured graph per replica on its own
@@ -38,7 +41,7 @@ struct hande_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::vector<int64_t> sig;            // per replica: epoch and deterministic-space state
-  double scale = 0.0;                  // CTAs per replica = base grid x scale (0 = default)
+  double scale = 0.0;                  // block budget = single-run grid x scale (0 = 1)
   int last_failed = -1;
 };
 
@@ -56,8 +59,10 @@ void release(hande_batch* b) {
   free_graphs(b);
   if (b->caller) cudaStreamSynchronize(b->caller);
   for (hande_ctx* c : b->ctx) hande_destroy(c);  // synchronises each replica stream
-  for (auto& g : b->groups)
+  for (auto& g : b->groups) {
     if (g.d_params) cudaFree(g.d_params);
+    if (g.d_off) cudaFree(g.d_off);
+  }
   for (cudaEvent_t e : b->done)
     if (e) cudaEventDestroy(e);
   for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin})
@@ -104,20 +109,23 @@ bool same_group(const Engine& a, const Engine& c) {
          a.attempt_grid == c.attempt_grid && a.merge_grid == c.merge_grid && a.merge_warp_grid == c.merge_warp_grid;
 }
 
-// CTAs per replica of each phase: the single run's grid times `scale`, at least 1
+// Block budgets of each group's phases: `scale` times the single run's grid
+// for that phase (the planner divides them among the replicas by their work);
+// a replica never gets more than 4 single-run grids, nor more list-pass blocks
+// than its scan partials hold.
 void set_grids(hande_batch* b) {
-  const int n = (int)b->ctx.size();
-  const double f = b->scale > 0.0 ? b->scale : std::min(1.0, 8.0 / (double)n);
-  auto g = [&](int base) { return std::max(1, (int)(base * f + 0.5)); };
+  const double f = b->scale > 0.0 ? b->scale : 1.0;
   for (auto& G : b->groups) {
     const Engine& E = *G.eng[0];
-    G.g_scan = std::min(g(hande::kScanBlocks), hande::kScanBlocks);
-    G.g_attempt = g(E.attempt_grid);
-    G.g_scatter = g(E.attempt_grid * 4);
-    G.g_mwarp = g(E.merge_warp_grid > 0 ? E.merge_warp_grid : 1);
-    G.g_merge = g(E.merge_grid);
-    G.g_copy = g(E.attempt_grid * 2);
-    G.g_hdiag = g(E.attempt_grid);
+    const int base[hande::kPlanPhases] = {hande::kScanBlocks, E.attempt_grid, E.attempt_grid * 4,
+                                          std::max(E.merge_warp_grid, 1), E.merge_grid, E.attempt_grid * 2,
+                                          E.attempt_grid};
+    const int by_att[hande::kPlanPhases] = {0, 1, 1, 0, 0, 0, 0};
+    for (int p = 0; p < hande::kPlanPhases; ++p) {
+      G.plan.budget[p] = std::max(1, (int)(base[p] * f + 0.5));
+      G.plan.cap[p] = p == 0 ? hande::kScanBlocks : 4 * base[p];
+      G.plan.by_attempts[p] = by_att[p];
+    }
   }
   free_graphs(b);
   b->sig.clear();
@@ -295,6 +303,7 @@ hande_status hande_batch_init(const hande_system* sys, const hande_qmc* qmc, int
     G.R = (int)G.eng.size();
     const Engine& E = *G.eng[0];
     bool good = ok(cudaMalloc(&G.d_params, sizeof(hande::Params) * (size_t)G.R)) &&
+                ok(cudaMalloc(&G.d_off, sizeof(int) * (size_t)hande::kPlanPhases * (G.R + 1))) &&
                 ok(cudaStreamCreateWithFlags(&b->gs[k], cudaStreamNonBlocking)) &&
                 ok(cudaStreamCreateWithFlags(&b->gaux[k], cudaStreamNonBlocking));
     for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin})
@@ -343,10 +352,8 @@ int hande_batch_failed_replica(const hande_batch* b) { return b ? b->last_failed
 hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_scale, double* best_ms) {
   if (!b || iterations < 1) return HANDE_ERR_INVALID;
   const int n = (int)b->ctx.size();
-  std::vector<double> cand;
-  for (double f : {1.0, 2.0, 4.0, 8.0, 16.0, 32.0}) cand.push_back(std::min(1.0, f / (double)n));
-  std::sort(cand.begin(), cand.end());
-  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  (void)n;
+  const std::vector<double> cand = {0.5, 1.0, 2.0, 4.0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) return HANDE_ERR_CUDA;
   double best = -1.0, bestf = cand[0];

@@ -20,11 +20,12 @@ struct Learner;   // learned excitation proposal (learn.cu)
 struct BatchGroup {
   std::vector<Engine*> eng;
   Params* d_params = nullptr;   // [R] parameter blocks (device)
+  int* d_off = nullptr;         // [kPlanPhases][R + 1] first block of each replica (device, planner)
   int R = 0;
   int max_ncore = 0;
-  // CTAs per replica of each phase: scan-partitioned passes (det pass, attempt
-  // scan, split), spawning, scatter, warp merge, block merge, copy, diagonals
-  int g_scan = 1, g_attempt = 1, g_scatter = 1, g_mwarp = 1, g_merge = 1, g_copy = 1, g_hdiag = 1;
+  // block budgets of the phases (list pass, spawning, scatter, warp merge,
+  // block merge, copy, diagonals), divided among the replicas by the planner
+  Plan plan{};
 };
 
 // launchers for one (key width, system kind) pair

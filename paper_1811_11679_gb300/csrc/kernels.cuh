@@ -133,6 +133,13 @@ struct Params {
   SysDev sys;
 };
 
+// The block index and grid size a kernel body partitions its work by: the
+// launch's own for a single run and for per-replica grids, a replica's share
+// of a load-balanced batched launch otherwise.
+struct VGrid {
+  int b, n;
+};
+
 // a batched launch's parameter block: replica blockIdx.y's copied to shared
 // memory by the whole block (before any thread may leave the kernel)
 __device__ __forceinline__ void load_params(Params& sP, const Params* PP) {
@@ -141,6 +148,76 @@ __device__ __forceinline__ void load_params(Params& sP, const Params* PP) {
   static_assert(sizeof(Params) % 8 == 0, "parameter block copied in 8-byte words");
   for (int i = threadIdx.x; i < (int)(sizeof(Params) / 8); i += blockDim.x) dst[i] = src[i];
   __syncthreads();
+}
+
+// A block of a load-balanced batched launch: replica r owns the blocks
+// [off[r], off[r + 1]) (offsets written by the planner), this block is block
+// blockIdx.x - off[r] of them.  Loads r's parameter block; false (for the whole
+// block) when the block belongs to no replica.
+__device__ __forceinline__ bool batch_block(const Params* PP, const int* off, int R, Params& sP, VGrid& vg) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0) {
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = R;   // the last r with off[r] <= b
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const bool in = lo < R && b < off[lo + 1];
+    s_r = in ? lo : -1;
+    if (in) vg = VGrid{b - off[lo], off[lo + 1] - off[lo]};
+  }
+  __syncthreads();
+  const int r = s_r;
+  if (r < 0) return false;
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(PP + r);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(&sP);
+  for (int i = threadIdx.x; i < (int)(sizeof(Params) / 8); i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+  return true;
+}
+
+// Load-balanced batched launch shape: for each phase p, the grid's blocks
+// (budget[p]) are divided among the R replicas in proportion to their work
+// (determinants for the list passes, the last iteration's attempts for the
+// spawning phases), at least one block each and at most cap[p]; off[p][r] =
+// first block of replica r.  One block; runs first in a batched iteration.
+constexpr int kPlanPhases = 7;   // list pass, spawning, scatter, warp merge, block merge, copy, diagonals
+struct Plan {
+  int budget[kPlanPhases];
+  int cap[kPlanPhases];
+  int by_attempts[kPlanPhases];
+};
+static __global__ void kb_plan(const Params* PP, int R, int cur, Plan plan, int* off) {
+  __shared__ double wsum[2];
+  if (threadIdx.x == 0) {
+    double a = 0.0, d = 0.0;
+    for (int r = 0; r < R; ++r) {
+      const DevState* st = PP[r].st;
+      const int64_t nd = st->ndet[cur];
+      const int64_t na = st->natt > 0 ? st->natt : nd;
+      d += (double)(nd > 0 ? nd : 1);
+      a += (double)(na > 0 ? na : 1);
+    }
+    wsum[0] = d;
+    wsum[1] = a;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < kPlanPhases; p += blockDim.x) {
+    int o = 0;
+    for (int r = 0; r < R; ++r) {
+      const DevState* st = PP[r].st;
+      const int64_t nd = st->ndet[cur];
+      const int64_t na = st->natt > 0 ? st->natt : nd;
+      const double w = (double)(plan.by_attempts[p] ? (na > 0 ? na : 1) : (nd > 0 ? nd : 1));
+      int c = 1 + (int)((double)plan.budget[p] * w / wsum[plan.by_attempts[p] ? 1 : 0]);
+      if (c > plan.cap[p]) c = plan.cap[p];
+      off[p * (R + 1) + r] = o;
+      o += c;
+    }
+    off[p * (R + 1) + R] = o;
+  }
 }
 
 template <int W>
@@ -239,17 +316,17 @@ __device__ T block_scan_excl(T* a, int n, T* wsum) {
 
 __device__ __forceinline__ void set_error(DevState* st, unsigned bit) { atomicOr(&st->error, bit); }
 
-// chunk of a block-partitioned range [0, n)
-__device__ __forceinline__ void block_chunk(int64_t n, int64_t& beg, int64_t& end) {
-  int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  beg = (int64_t)blockIdx.x * per;
+// chunk of a block-partitioned range [0, n) for block vg.b of vg.n
+__device__ __forceinline__ void block_chunk(int64_t n, int64_t& beg, int64_t& end, const VGrid vg) {
+  int64_t per = (n + vg.n - 1) / vg.n;
+  beg = (int64_t)vg.b * per;
   end = beg + per < n ? beg + per : n;
   if (beg > n) beg = n;
 }
 
 // ------------------------------------------------------------------ det pass
 template <int W, int SYS>
-__device__ __forceinline__ void d_det_pass(const Params& P, int cur) {
+__device__ __forceinline__ void d_det_pass(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   __shared__ int64_t sh64[32];
@@ -259,7 +336,7 @@ __device__ __forceinline__ void d_det_pass(const Params& P, int cur) {
   const double S = st->shift;
   const Key<W> d0 = ref_key<W>(P);
   int64_t beg, end;
-  block_chunk(n, beg, end);
+  block_chunk(n, beg, end, vg);
   uint64_t* key = P.key[cur];
   int64_t* pop = P.pop[cur];
   const double* hd = P.hdiag[cur];
@@ -309,20 +386,21 @@ __device__ __forceinline__ void d_det_pass(const Params& P, int cur) {
     attsum += na;
   }
   int64_t a = block_sum<int64_t>(attsum, sh64);
-  if (threadIdx.x == 0) P.part[blockIdx.x] = a;
+  if (threadIdx.x == 0) P.part[vg.b] = a;
   int64_t b = block_sum<int64_t>(nw, sh64);
   if (threadIdx.x == 0 && b) atomicAdd((unsigned long long*)&st->nw_pre, (unsigned long long)b);
   I128 c = block_sum_i128(num, sh128);
   if (threadIdx.x == 0 && (c.lo | (uint64_t)c.hi)) atomic_add_i128(st->num, c);
 }
 template <int W, int SYS>
-__global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) { d_det_pass<W, SYS>(P, cur); }
+__global__ void __launch_bounds__(kScanThreads) k_det_pass(Params P, int cur) { d_det_pass<W, SYS>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W, int SYS>
-__global__ void __launch_bounds__(kScanThreads) kb_det_pass(const Params* PP, int cur) {
+__global__ void __launch_bounds__(kScanThreads) kb_det_pass(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_det_pass<W, SYS>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_det_pass<W, SYS>(sP, cur, vg);
 }
 
 // ------------------------------------------------------------------ generic scans
@@ -423,14 +501,14 @@ __global__ void __launch_bounds__(1024) k_scan_one(const Tin* in, Tout* out, con
 // round takes 4 consecutive values per thread (4 x blockDim per round)
 template <typename T>
 __device__ __forceinline__ void d_scan_apply(const T* in, T* out, const int64_t* n_ptr, const int64_t* part,
-                                             DevState* st) {
+                                             DevState* st, const VGrid vg) {
   if (st->error) return;
   constexpr int kItems = 4;
   __shared__ T wsum[33];
   int64_t beg, end;
-  block_chunk(*n_ptr, beg, end);
+  block_chunk(*n_ptr, beg, end, vg);
   const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5), nw = (int)(blockDim.x >> 5);
-  T carry = (T)part[blockIdx.x];
+  T carry = (T)part[vg.b];
   for (int64_t base = beg; base < end; base += (int64_t)blockDim.x * kItems) {
     const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
     T v[kItems], sum = 0;
@@ -472,7 +550,7 @@ __device__ __forceinline__ void d_scan_apply(const T* in, T* out, const int64_t*
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const T* in, T* out, const int64_t* n_ptr,
                                                              const int64_t* part, DevState* st) {
-  d_scan_apply<T>(in, out, n_ptr, part, st);
+  d_scan_apply<T>(in, out, n_ptr, part, st, VGrid{(int)blockIdx.x, (int)gridDim.x});
 }
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const int64_t* n_ptr, int64_t* part,
@@ -480,7 +558,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const
   if (st->error) return;
   __shared__ int64_t sh[32];
   int64_t beg, end;
-  block_chunk(*n_ptr, beg, end);
+  block_chunk(*n_ptr, beg, end, VGrid{(int)blockIdx.x, (int)gridDim.x});
   int64_t s = 0;
   for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += (int64_t)in[i];
   s = block_sum<int64_t>(s, sh);
@@ -488,13 +566,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, const
 }
 
 // batched forms of the scans, pointers taken from replica blockIdx.y's block
-static __global__ void kb_scan_natt(const Params* PP, int nparts) {
+static __global__ void kb_scan_natt(const Params* PP, const int* off, int R) {
   const Params& P = PP[blockIdx.y];
-  d_scan_partials_i64(P.part, nparts, &P.st->natt, P.st);
+  d_scan_partials_i64(P.part, off[blockIdx.y + 1] - off[blockIdx.y], &P.st->natt, P.st);
 }
-static __global__ void __launch_bounds__(kScanThreads) kb_scan_att(const Params* PP, int cur) {
-  const Params& P = PP[blockIdx.y];
-  d_scan_apply<int64_t>(P.natt, P.att_begin, &P.st->ndet[cur], P.part, P.st);
+static __global__ void __launch_bounds__(kScanThreads) kb_scan_att(const Params* PP, const int* off, int R, int cur) {
+  __shared__ Params sP;
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_scan_apply<int64_t>(sP.natt, sP.att_begin, &sP.st->ndet[cur], sP.part, sP.st, vg);
 }
 static __global__ void __launch_bounds__(1024) kb_scan_buckets(const Params* PP) {
   const Params& P = PP[blockIdx.y];
@@ -511,7 +591,7 @@ static __global__ void __launch_bounds__(1024) kb_scan_kept(const Params* PP, in
 // lies in [key[b*sb], key[(b+1)*sb]); sb is chosen so a bucket expects at most
 // half a tile of spawns (even if every one went to a new determinant).
 template <int W>
-__device__ __forceinline__ void d_split(const Params& P, int cur) {
+__device__ __forceinline__ void d_split(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t n = st->ndet[cur];
@@ -535,7 +615,7 @@ __device__ __forceinline__ void d_split(const Params& P, int cur) {
   if (sb < 1) sb = 1;
   int64_t nb = (n + sb - 1) / sb;
   if (nb < 1) nb = 1;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (vg.b == 0 && threadIdx.x == 0) {
     st->nbuckets = nb;
     st->sb = sb;
     st->nspawn = 0;
@@ -549,7 +629,7 @@ __device__ __forceinline__ void d_split(const Params& P, int cur) {
     if (nb > P.cap) set_error(st, ERR_BUCKET_CAPACITY);
   }
   if (nb > P.cap) return;
-  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t b = vg.b * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)vg.n * blockDim.x) {
     P.bcount[b] = 0;
     P.tile_state[b] = 0ull;
 
@@ -559,13 +639,14 @@ __device__ __forceinline__ void d_split(const Params& P, int cur) {
   }
 }
 template <int W>
-__global__ void k_split(Params P, int cur) { d_split<W>(P, cur); }
+__global__ void k_split(Params P, int cur) { d_split<W>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W>
-__global__ void kb_split(const Params* PP, int cur) {
+__global__ void kb_split(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_split<W>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_split<W>(sP, cur, vg);
 }
 
 // ------------------------------------------------------------------ deterministic space
@@ -931,7 +1012,7 @@ __device__ __forceinline__ void record_sample(const Params& P, int64_t natt, int
 }
 
 template <int W, int SYS>
-__device__ __forceinline__ void d_attempt(const Params& P, int cur) {
+__device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   constexpr int KS = attempt_split_smem<W>();
@@ -985,7 +1066,7 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur) {
   }
   __syncthreads();
   const int lane = (int)warp_lane();
-  const int64_t total_warps = (int64_t)gridDim.x * kAttemptWarps;
+  const int64_t total_warps = (int64_t)vg.n * kAttemptWarps;
   int sq_n = 0, pq_n = 0;   // warp-uniform queue lengths
   // each warp owns one contiguous span of attempts, taken in chunks of 32.
   // Parents are monotone in the attempt index: with base = the parent of a
@@ -994,7 +1075,7 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur) {
   // The offsets att_begin[base .. base + 32] of the next chunk are loaded while
   // the current chunk is processed.
   const int64_t span = (((natt + total_warps - 1) / total_warps) + 31) & ~(int64_t)31;
-  const int64_t gbeg = ((int64_t)blockIdx.x * kAttemptWarps + wid) * span;
+  const int64_t gbeg = ((int64_t)vg.b * kAttemptWarps + wid) * span;
   const int64_t gend = gbeg + span < natt ? gbeg + span : natt;
   int64_t base = 0, av = INT64_MAX, av32_l = INT64_MAX;
   if (gbeg < gend) {
@@ -1090,21 +1171,22 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur) {
   if (pq_n > 0) flush_spawns<W>(P, Q, pq_n, pq_n, sx);
 }
 template <int W, int SYS>
-__global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) { d_attempt<W, SYS>(P, cur); }
+__global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) { d_attempt<W, SYS>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W, int SYS>
-__global__ void __launch_bounds__(kAttemptThreads) kb_attempt(const Params* PP, int cur) {
+__global__ void __launch_bounds__(kAttemptThreads) kb_attempt(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_attempt<W, SYS>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_attempt<W, SYS>(sP, cur, vg);
 }
 
 template <int W>
-__device__ __forceinline__ void d_scatter(const Params& P) {
+__device__ __forceinline__ void d_scatter(const Params& P, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   const int64_t ns = st->nspawn < P.scap ? st->nspawn : P.scap;
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t s = (int64_t)vg.b * blockDim.x + threadIdx.x; s < ns; s += (int64_t)vg.n * blockDim.x) {
     uint64_t m = P.s_meta[s];
     uint32_t b = (uint32_t)(m >> 32);
     uint32_t rank = (uint32_t)(m & 0xffffffffu) >> 1;
@@ -1116,13 +1198,14 @@ __device__ __forceinline__ void d_scatter(const Params& P) {
   }
 }
 template <int W>
-__global__ void __launch_bounds__(256) k_scatter(Params P) { d_scatter<W>(P); }
+__global__ void __launch_bounds__(256) k_scatter(Params P) { d_scatter<W>(P, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W>
-__global__ void __launch_bounds__(256) kb_scatter(const Params* PP) {
+__global__ void __launch_bounds__(256) kb_scatter(const Params* PP, const int* off, int R) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_scatter<W>(sP);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_scatter<W>(sP, vg);
 }
 
 // ------------------------------------------------------------------ merge (annihilation)
@@ -1642,7 +1725,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Params& P, int
 constexpr int kMergeThreads = 256;
 
 template <int W, int SYS>
-__device__ __forceinline__ void d_merge(const Params& P, int cur, int staged) {
+__device__ __forceinline__ void d_merge(const Params& P, int cur, int staged, const VGrid vg) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t wsum[33];
@@ -1964,13 +2047,14 @@ __device__ __forceinline__ void d_merge(const Params& P, int cur, int staged) {
   if (threadIdx.x == 0 && tot) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)tot);
 }
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur, int staged) { d_merge<W, SYS>(P, cur, staged); }
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) k_merge(Params P, int cur, int staged) { d_merge<W, SYS>(P, cur, staged, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) kb_merge(const Params* PP, int cur, int staged) {
+__global__ void __launch_bounds__(kMergeThreads, (W == 8 ? 2 : 4)) kb_merge(const Params* PP, const int* off, int R, int cur, int staged) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_merge<W, SYS>(sP, cur, staged);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_merge<W, SYS>(sP, cur, staged, vg);
 }
 
 // ------------------------------------------------------------------ finalize
@@ -2025,25 +2109,26 @@ static __global__ void kb_finalize(const Params* PP, int cur) {
 
 // diagonal elements of the determinants the merge created (list in natt[])
 template <int W, int SYS>
-__device__ __forceinline__ void d_new_hdiag(const Params& P, int cur) {
+__device__ __forceinline__ void d_new_hdiag(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   const int nxt = cur ^ 1;
   const int64_t nn = st->nnew;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)vg.b * blockDim.x + threadIdx.x; i < nn; i += (int64_t)vg.n * blockDim.x) {
     int64_t o = P.natt[i];
     Key<W> k = load_key<W>(P.key[nxt], P.cap, o);
     P.hdiag[nxt][o] = __dsub_rn(h_diag<W, SYS>(P.sys, k), st->e_ref);
   }
 }
 template <int W, int SYS>
-__global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) { d_new_hdiag<W, SYS>(P, cur); }
+__global__ void __launch_bounds__(256) k_new_hdiag(Params P, int cur) { d_new_hdiag<W, SYS>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W, int SYS>
-__global__ void __launch_bounds__(256) kb_new_hdiag(const Params* PP, int cur) {
+__global__ void __launch_bounds__(256) kb_new_hdiag(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_new_hdiag<W, SYS>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_new_hdiag<W, SYS>(sP, cur, vg);
 }
 
 // ------------------------------------------------------------------ utilities

@@ -195,46 +195,52 @@ void enqueue_iteration(Engine& E, int cur, bool core, cudaStream_t s, cudaEvent_
 }
 
 // One iteration of every replica of a batch group: the same phases and graph
-// branches as enqueue_iteration (captured form), each phase one launch whose
-// grid's y dimension is the replica and x dimension the group's CTAs per
-// replica for that phase; replica r reads its parameter block G.d_params[r].
+// branches as enqueue_iteration (captured form).  A planner kernel first
+// divides each phase's block budget among the replicas in proportion to their
+// work; each phase is then one launch of budget + R blocks in which replica r
+// owns the blocks [off[r], off[r + 1]) and reads its parameter block
+// G.d_params[r].  Single-block steps (scans, shift update) and the
+// deterministic-space kernels run on (blocks, replicas) grids.
 template <int W, int SYS>
 void enqueue_iteration_batch(BatchGroup& G, int cur, cudaStream_t s, cudaStream_t aux, cudaEvent_t fork,
                              cudaEvent_t join) {
   const Params* PP = G.d_params;
-  const unsigned R = (unsigned)G.R;
+  const int R = G.R;
   const Engine& E0 = *G.eng[0];
   const int ncb = (G.max_ncore + 255) / 256;
+  auto off = [&](int p) { return G.d_off + (size_t)p * (R + 1); };
+  auto blocks = [&](int p) { return (unsigned)(G.plan.budget[p] + R); };
+  kb_plan<<<1, 32, 0, s>>>(PP, R, cur, G.plan, G.d_off);
   (void)cudaEventRecord(fork, s);
   (void)cudaStreamWaitEvent(aux, fork, 0);
-  kb_split<W><<<dim3(G.g_scan, R), 256, 0, aux>>>(PP, cur);
+  kb_split<W><<<blocks(0), 256, 0, aux>>>(PP, off(0), R, cur);
   if (G.max_ncore > 0) {
     kb_core_locate<W><<<dim3(ncb, R), 256, 0, aux>>>(PP, cur);
     kb_core_spmv<<<dim3((unsigned)(((int64_t)G.max_ncore * 32 + 255) / 256), R), 256, 0, aux>>>(PP, cur);
   }
   (void)cudaEventRecord(join, aux);
-  kb_det_pass<W, SYS><<<dim3(G.g_scan, R), kScanThreads, 0, s>>>(PP, cur);
-  kb_scan_natt<<<dim3(1, R), 1024, 0, s>>>(PP, G.g_scan);
-  kb_scan_att<<<dim3(G.g_scan, R), kScanThreads, 0, s>>>(PP, cur);
+  kb_det_pass<W, SYS><<<blocks(0), kScanThreads, 0, s>>>(PP, off(0), R, cur);
+  kb_scan_natt<<<dim3(1, R), 1024, 0, s>>>(PP, off(0), R);
+  kb_scan_att<<<blocks(0), kScanThreads, 0, s>>>(PP, off(0), R, cur);
   (void)cudaStreamWaitEvent(s, join, 0);
   if (G.max_ncore > 0) kb_core_apply<<<dim3(ncb, R), 256, 0, s>>>(PP, cur);
-  kb_attempt<W, SYS><<<dim3(G.g_attempt, R), kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(PP, cur);
+  kb_attempt<W, SYS><<<blocks(1), kAttemptThreads, attempt_smem_bytes<W, SYS>(), s>>>(PP, off(1), R, cur);
   kb_scan_buckets<<<dim3(1, R), 1024, 0, s>>>(PP);
-  kb_scatter<W><<<dim3(G.g_scatter, R), 256, 0, s>>>(PP);
+  kb_scatter<W><<<blocks(2), 256, 0, s>>>(PP, off(2), R);
   if (E0.merge_warp) {
     (void)cudaEventRecord(fork, s);
     (void)cudaStreamWaitEvent(aux, fork, 0);
-    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, aux>>>(PP, cur, 2);
+    kb_merge<W, SYS><<<blocks(4), kMergeThreads, E0.merge_smem_bytes, aux>>>(PP, off(4), R, cur, 2);
     (void)cudaEventRecord(join, aux);
-    kb_merge_warp<W, SYS><<<dim3(G.g_mwarp, R), kMwThreads, E0.ops.merge_warp_smem, s>>>(PP, cur);
-    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, cur, 1);
+    kb_merge_warp<W, SYS><<<blocks(3), kMwThreads, E0.ops.merge_warp_smem, s>>>(PP, off(3), R, cur);
+    kb_merge<W, SYS><<<blocks(4), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, off(4), R, cur, 1);
     (void)cudaStreamWaitEvent(s, join, 0);
     kb_scan_kept<<<dim3(1, R), 1024, 0, s>>>(PP, cur);
-    kb_merge_copy<W><<<dim3(G.g_copy, R), 256, 0, s>>>(PP, cur);
+    kb_merge_copy<W><<<blocks(5), 256, 0, s>>>(PP, off(5), R, cur);
   } else {
-    kb_merge<W, SYS><<<dim3(G.g_merge, R), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, cur, 0);
+    kb_merge<W, SYS><<<blocks(4), kMergeThreads, E0.merge_smem_bytes, s>>>(PP, off(4), R, cur, 0);
   }
-  kb_new_hdiag<W, SYS><<<dim3(G.g_hdiag, R), 256, 0, s>>>(PP, cur);
+  kb_new_hdiag<W, SYS><<<blocks(6), 256, 0, s>>>(PP, off(6), R, cur);
   kb_finalize<<<dim3(1, R), 32, 0, s>>>(PP, cur);
 }
 

@@ -354,7 +354,7 @@ __device__ int64_t wt_write(const Params& P, WarpTile<W>& t, int mi, int mh, int
 
 // One warp per bucket, buckets taken from a ticket counter (see the file comment).
 template <int W, int SYS>
-__device__ __forceinline__ void d_merge_warp(const Params& P, int cur) {
+__device__ __forceinline__ void d_merge_warp(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   extern __shared__ __align__(16) unsigned char mw_smem[];
   const int lane = (int)(threadIdx.x & 31), wid = (int)(threadIdx.x >> 5);
@@ -448,13 +448,14 @@ __device__ __forceinline__ void d_merge_warp(const Params& P, int cur) {
   if (lane == 0 && nwsum) atomicAdd((unsigned long long*)&st->nw_post, (unsigned long long)nwsum);
 }
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_warp(Params P, int cur) { d_merge_warp<W, SYS>(P, cur); }
+__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) k_merge_warp(Params P, int cur) { d_merge_warp<W, SYS>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W, int SYS>
-__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) kb_merge_warp(const Params* PP, int cur) {
+__global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) kb_merge_warp(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_merge_warp<W, SYS>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_merge_warp<W, SYS>(sP, cur, vg);
 }
 
 // Compact the staged bucket lists into the new main list (one warp per bucket,
@@ -462,15 +463,15 @@ __global__ void __launch_bounds__(kMwThreads, MwDims<W>::kMinBlocks) kb_merge_wa
 // bucket's packed scan result gives both its output offset (low 32 bits) and
 // its offset in the new-determinant list (high 32 bits).
 template <int W>
-__device__ __forceinline__ void d_merge_copy(const Params& P, int cur) {
+__device__ __forceinline__ void d_merge_copy(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
   const int nxt = cur ^ 1;
   const int64_t nb = st->nbuckets, sb = st->sb;
   const int lane = (int)(threadIdx.x & 31);
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nwarps = ((int64_t)vg.n * blockDim.x) >> 5;
   uint64_t* okey = P.key[nxt];
-  for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
+  for (int64_t b = ((int64_t)vg.b * blockDim.x + threadIdx.x) >> 5; b < nb; b += nwarps) {
     const int64_t src = b * sb + (int64_t)P.boff[b];
     const int64_t dst = (int64_t)(P.tile_inc[b] & 0xffffffffull);   // output offset
     int64_t nslot = (int64_t)(P.tile_inc[b] >> 32);                  // offset in the new-determinant list
@@ -511,13 +512,14 @@ __device__ __forceinline__ void d_merge_copy(const Params& P, int cur) {
   }
 }
 template <int W>
-__global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) { d_merge_copy<W>(P, cur); }
+__global__ void __launch_bounds__(256) k_merge_copy(Params P, int cur) { d_merge_copy<W>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
 template <int W>
-__global__ void __launch_bounds__(256) kb_merge_copy(const Params* PP, int cur) {
+__global__ void __launch_bounds__(256) kb_merge_copy(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
-  load_params(sP, PP);
-  d_merge_copy<W>(sP, cur);
+  __shared__ VGrid vg;
+  if (!batch_block(PP, off, R, sP, vg)) return;
+  d_merge_copy<W>(sP, cur, vg);
 }
 
 }  // namespace hande
