@@ -18,8 +18,9 @@
 // network outputs, because the spawn weight uses the table's exact p_gen.
 //
 // BF16 rounding points (the oracle's FP64 MLP mirrors them): the weights, the
-// hidden activations, and the backward signals of the logits and hidden
-// layers; GEMM outputs, biases, softmax and Adam are FP32.
+// hidden activations (rounded in the GEMM epilogue after bias and ReLU), and
+// the backward signals of the logits and hidden layers; accumulation, biases,
+// logits, softmax and Adam are FP32.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -29,12 +30,16 @@
 
 #include "engine.h"
 #include "host_util.h"
+#include "tc_gemm.cuh"
 
 namespace hande {
 namespace tc {
-// the tensor-core GEMM D = A B^T (tc_gemm.cuh, launched from mlp.cu)
+// the tensor-core GEMM D = A B^T (tc_gemm.cuh, launched from mlp.cu): FP32
+// output, or BF16 act(D + bias) with an optional transposed copy
 bool launch_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* D, int64_t ldd, int M, int N,
                  int K, unsigned* err, cudaStream_t s, const char** why);
+bool launch_gemm_ep(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, const Epilogue& ep, int epi,
+                    int M, int N, int K, unsigned* err, cudaStream_t s, const char** why);
 }
 
 struct Learner {
@@ -49,7 +54,7 @@ struct Learner {
   uint16_t *X = nullptr, *XT = nullptr, *Xtab = nullptr;
   uint16_t *H1 = nullptr, *H2 = nullptr, *H1T = nullptr, *H2T = nullptr;
   uint16_t *G3 = nullptr, *G3T = nullptr, *dZ2 = nullptr, *dZ2T = nullptr, *dZ1 = nullptr, *dZ1T = nullptr;
-  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *dH = nullptr;
+  float *Z3 = nullptr, *dH = nullptr;
   float* wsum = nullptr;
   double* loss = nullptr;
   unsigned* err = nullptr;
@@ -84,27 +89,14 @@ __global__ void k_lr_features(const int32_t* rows, const float* w, int count, in
   }
 }
 
-// Hb = act(Z + b) in BF16 [n][Hd] and its transpose HbT [Hd][ldT] (if given)
-__global__ void k_lr_bias_act(const float* Z, const float* b, int n, int Hd, int relu, uint16_t* Hb, uint16_t* HbT,
-                              int ldT) {
+// dZ = (h > 0) ? dH : 0 in BF16 [n][Hd] and transposed [Hd][ldT], h the layer's
+// BF16 ReLU output (positive exactly where the pre-activation is)
+__global__ void k_lr_relu_back(const float* dH, const uint16_t* Hact, int n, int Hd, uint16_t* dZ, uint16_t* dZT,
+                               int ldT) {
   const int64_t total = (int64_t)n * Hd;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(i / Hd), j = (int)(i % Hd);
-    float v = Z[i] + b[j];
-    if (relu) v = v > 0.0f ? v : 0.0f;
-    const uint16_t h = f2bf(v);
-    Hb[i] = h;
-    if (HbT) HbT[(int64_t)j * ldT + r] = h;
-  }
-}
-
-// dZ = (Z + b > 0) ? dH : 0 in BF16 [n][Hd] and transposed [Hd][ldT]
-__global__ void k_lr_relu_back(const float* dH, const float* Z, const float* b, int n, int Hd, uint16_t* dZ,
-                               uint16_t* dZT, int ldT) {
-  const int64_t total = (int64_t)n * Hd;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / Hd), j = (int)(i % Hd);
-    const uint16_t g = (Z[i] + b[j] > 0.0f) ? f2bf(dH[i]) : (uint16_t)0;
+    const uint16_t g = (Hact[i] != 0 && !(Hact[i] & 0x8000)) ? f2bf(dH[i]) : (uint16_t)0;
     dZ[i] = g;
     dZT[(int64_t)j * ldT + r] = g;
   }
@@ -302,14 +294,26 @@ void gemm(Learner& L, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t
 
 // forward of `nrows` feature rows X [nrows][kin] to the logits Z3 [nrows][M]
 // (activations H1, H2; transposes only for a training batch)
+void gemm_act(Learner& L, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, const float* bias,
+              uint16_t* Hout, uint16_t* HT, int m, int n, int k, cudaStream_t s) {
+  tc::Epilogue ep{};
+  ep.H = Hout;
+  ep.ldh = n;
+  ep.HT = HT;
+  ep.ldt = L.S;
+  ep.bias = bias;
+  ep.relu = 1;
+  const char* why = "";
+  if (!tc::launch_gemm_ep(A, lda, B, ldb, ep, tc::EPI_BF16_BIAS, m, n, k, L.err, s, &why))
+    throw Fail{HANDE_ERR_CUDA, why};
+}
+
+// hidden layers: BF16 relu(x W^T + b) straight from the GEMM epilogue (and
+// their transposes for a training batch); logits in FP32
 void forward(Learner& L, const uint16_t* X, int nrows, bool train, cudaStream_t s) {
   const int H = L.H;
-  gemm(L, X, L.kin, L.W1b, L.kin, L.Z1, H, nrows, H, L.kin, s);
-  k_lr_bias_act<<<grid_for((int64_t)nrows * H), kLt, 0, s>>>(L.Z1, L.param + L.ob1, nrows, H, 1, L.H1,
-                                                             train ? L.H1T : nullptr, L.S);
-  gemm(L, L.H1, H, L.W2b, H, L.Z2, H, nrows, H, H, s);
-  k_lr_bias_act<<<grid_for((int64_t)nrows * H), kLt, 0, s>>>(L.Z2, L.param + L.ob2, nrows, H, 1, L.H2,
-                                                             train ? L.H2T : nullptr, L.S);
+  gemm_act(L, X, L.kin, L.W1b, L.kin, L.param + L.ob1, L.H1, train ? L.H1T : nullptr, nrows, H, L.kin, s);
+  gemm_act(L, L.H1, H, L.W2b, H, L.param + L.ob2, L.H2, train ? L.H2T : nullptr, nrows, H, H, s);
   gemm(L, L.H2, H, L.W3b, H, L.Z3, L.M, nrows, L.M, H, s);
 }
 
@@ -326,11 +330,11 @@ void backward(Engine& E, Learner& L, const int32_t* rows, const int32_t* tgt, co
   gemm(L, L.G3T, S, L.H2T, S, g + L.oW3, H, M, H, S, s);                 // dW3 = G3^T H2
   k_lr_colsum<<<(M + kLt - 1) / kLt, kLt, 0, s>>>(L.G3, S, M, L.M8, g + L.ob3);
   gemm(L, L.G3, L.M8, L.W3bT, L.M8, L.dH, H, S, H, M, s);                // dH2 = G3 W3
-  k_lr_relu_back<<<grid_for((int64_t)S * H), kLt, 0, s>>>(L.dH, L.Z2, L.param + L.ob2, S, H, L.dZ2, L.dZ2T, S);
+  k_lr_relu_back<<<grid_for((int64_t)S * H), kLt, 0, s>>>(L.dH, L.H2, S, H, L.dZ2, L.dZ2T, S);
   k_lr_colsum<<<(H + kLt - 1) / kLt, kLt, 0, s>>>(L.dZ2, S, H, H, g + L.ob2);
   gemm(L, L.dZ2T, S, L.H1T, S, g + L.oW2, H, H, H, S, s);                // dW2 = dZ2^T H1
   gemm(L, L.dZ2, H, L.W2bT, H, L.dH, H, S, H, H, s);                     // dH1 = dZ2 W2
-  k_lr_relu_back<<<grid_for((int64_t)S * H), kLt, 0, s>>>(L.dH, L.Z1, L.param + L.ob1, S, H, L.dZ1, L.dZ1T, S);
+  k_lr_relu_back<<<grid_for((int64_t)S * H), kLt, 0, s>>>(L.dH, L.H1, S, H, L.dZ1, L.dZ1T, S);
   k_lr_colsum<<<(H + kLt - 1) / kLt, kLt, 0, s>>>(L.dZ1, S, H, H, g + L.ob1);
   gemm(L, L.dZ1T, S, L.XT, S, g + L.oW1, L.din, H, L.din, S, s);         // dW1 = dZ1^T X
 }
@@ -480,8 +484,6 @@ void learner_attach(Engine& E, const hande_learning& in) {
   L.dZ2T = dalloc<uint16_t>(E, (size_t)H * L.S);
   L.dZ1 = dalloc<uint16_t>(E, (size_t)L.S * H);
   L.dZ1T = dalloc<uint16_t>(E, (size_t)H * L.S);
-  L.Z1 = dalloc<float>(E, (size_t)L.rows_cap * H);
-  L.Z2 = dalloc<float>(E, (size_t)L.rows_cap * H);
   L.Z3 = dalloc<float>(E, (size_t)L.rows_cap * M);
   L.dH = dalloc<float>(E, (size_t)L.S * H);
   L.wsum = dalloc<float>(E, 1);

@@ -19,7 +19,6 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
-bool g_attr_set[256] = {};
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda)
 EncodeTiledFn encoder() {
@@ -53,14 +52,41 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Validated launch of D = A B^T (see tc_gemm.cuh); false with a message on bad input
-bool launch_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* D, int64_t ldd, int M,
-                 int N, int K, unsigned* err, cudaStream_t s, const char** why) {
-  if (M < 1 || N < 1 || K < 1 || !A || !B || !D || !err) {
+template <int BN, int EPI>
+bool launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep, int M, int N, int K,
+                  unsigned* err, cudaStream_t s, int dev, const char** why) {
+  static bool attr_set[256] = {};
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!attr_set[dev]) {
+      if (cudaFuncSetAttribute(k_gemm_bf16_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Tile<BN>::kSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        *why = "cannot reserve the GEMM's shared memory";
+        return false;
+      }
+      attr_set[dev] = true;
+    }
+  }
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kBM - 1) / kBM));
+  k_gemm_bf16_tn<BN, EPI><<<grid, kThreads, Tile<BN>::kSmemBytes, s>>>(ma, mb, ep, M, N, K, err);
+  if (cudaGetLastError() != cudaSuccess) {
+    *why = "GEMM launch failed";
+    return false;
+  }
+  return true;
+}
+
+// Validated launch of D = A B^T with the given epilogue (see tc_gemm.cuh);
+// 256-column tiles when N > 128; false with a message on bad input
+bool launch_gemm_ep(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, const Epilogue& ep, int epi,
+                    int M, int N, int K, unsigned* err, cudaStream_t s, const char** why) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !err || (epi == EPI_F32 ? !ep.D : (!ep.H || !ep.bias))) {
     *why = "bad GEMM sizes or pointers";
     return false;
   }
-  if (lda < K || ldb < K || ldd < N || (lda & 7) || (ldb & 7) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
+  if (lda < K || ldb < K || (lda & 7) || (ldb & 7) || ((uintptr_t)A & 15) || ((uintptr_t)B & 15) ||
+      (epi == EPI_F32 ? ep.ldd < N : ep.ldh < N)) {
     *why = "GEMM operands need 16-byte aligned rows (leading dimensions multiples of 8, >= K)";
     return false;
   }
@@ -70,31 +96,26 @@ bool launch_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
     *why = "no current CUDA device";
     return false;
   }
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_attr_set[dev]) {
-      if (cudaFuncSetAttribute(k_gemm_bf16_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) !=
-          cudaSuccess) {
-        cudaGetLastError();
-        *why = "cannot reserve the GEMM's shared memory";
-        return false;
-      }
-      g_attr_set[dev] = true;
-    }
-  }
+  const int bn = N > 128 ? 256 : 128;
   CUtensorMap ma, mb;
   if (!make_map(&ma, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kBM) ||
-      !make_map(&mb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, kBN)) {
+      !make_map(&mb, B, (uint64_t)K, (uint64_t)N, (uint64_t)ldb, (uint32_t)bn)) {
     *why = "cuTensorMapEncodeTiled failed";
     return false;
   }
-  dim3 grid((unsigned)((N + kBN - 1) / kBN), (unsigned)((M + kBM - 1) / kBM));
-  k_gemm_bf16_tn<<<grid, kThreads, kSmemBytes, s>>>(ma, mb, D, ldd, M, N, K, err);
-  if (cudaGetLastError() != cudaSuccess) {
-    *why = "GEMM launch failed";
-    return false;
-  }
-  return true;
+  if (epi == EPI_F32)
+    return bn == 256 ? launch_shape<256, EPI_F32>(ma, mb, ep, M, N, K, err, s, dev, why)
+                     : launch_shape<128, EPI_F32>(ma, mb, ep, M, N, K, err, s, dev, why);
+  return bn == 256 ? launch_shape<256, EPI_BF16_BIAS>(ma, mb, ep, M, N, K, err, s, dev, why)
+                   : launch_shape<128, EPI_BF16_BIAS>(ma, mb, ep, M, N, K, err, s, dev, why);
+}
+
+bool launch_gemm(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* D, int64_t ldd, int M,
+                 int N, int K, unsigned* err, cudaStream_t s, const char** why) {
+  Epilogue ep{};
+  ep.D = D;
+  ep.ldd = ldd;
+  return launch_gemm_ep(A, lda, B, ldb, ep, EPI_F32, M, N, K, err, s, why);
 }
 
 namespace {

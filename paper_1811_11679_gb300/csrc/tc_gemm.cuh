@@ -3,14 +3,17 @@
 //   D[m][n] = sum_k A[m][k] B[n][k]        (A: M x K, B: N x K, both K-major
 //                                           BF16 row-major; D: FP32)
 //
-// One CTA computes one 128 x 128 tile of D.  The K dimension is taken in
+// One CTA computes one 128 x BN tile of D (BN = 128, or 256 when N > 128, so
+// that A is read once for N <= 256).  The K dimension is taken in
 // chunks of 64 elements (128 bytes): a TMA tile load brings the A and B chunk
 // of a stage into shared memory in the 128-byte-swizzled K-major layout the
 // tensor core reads, four stages deep; one thread issues the MMAs (four
-// 128 x 128 x 16 tcgen05.mma per chunk, FP32 accumulators in tensor memory) and
+// 128 x BN x 16 tcgen05.mma per chunk, FP32 accumulators in tensor memory) and
 // commits each stage to an mbarrier that frees it for the next TMA load.  When
 // the last MMA has completed, the four warps read the accumulator rows they own
-// (tcgen05.ld, 32 lanes x 32 columns at a time) and store them.  Rows, columns
+// (tcgen05.ld, 32 lanes x 32 columns at a time) and store them as FP32, or as
+// BF16 after adding a bias and a ReLU (with a transposed copy if asked: the
+// learned proposal's hidden layers and their backward operands).  Rows, columns
 // and K beyond the matrix are zero-filled by the TMA and masked in the store,
 // so any M, N, K >= 1 work (leading dimensions: multiples of 8 elements).
 //
@@ -19,6 +22,7 @@
 // frees its tensor memory.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,17 +31,34 @@ namespace hande {
 namespace tc {
 
 constexpr int kBM = 128;        // tile rows (MMA M)
-constexpr int kBN = 128;        // tile columns (MMA N)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = 128 bytes = one swizzle row
 constexpr int kMmaK = 16;       // K of one tcgen05.mma kind::f16
 constexpr int kStages = 4;
 constexpr int kThreads = 128;   // four warps: the 128 TMEM lanes
 constexpr uint32_t kTileABytes = kBM * kBK * 2;
-constexpr uint32_t kTileBBytes = kBN * kBK * 2;
-constexpr uint32_t kTmemCols = kBN;   // FP32 accumulator: one column per output column
 constexpr unsigned ERR_MMA_TIMEOUT = 1u;
-// dynamic shared memory: 1024-byte aligned stages + barriers
-constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kTileABytes + kTileBBytes) + 256;
+// tile columns BN (MMA N, 128 or 256) and what BN needs: B tile bytes, tensor
+// memory columns (one FP32 accumulator column per output column), and the
+// dynamic shared memory (1024-byte aligned stages + barriers)
+template <int BN>
+struct Tile {
+  static constexpr uint32_t kTileBBytes = BN * kBK * 2;
+  static constexpr uint32_t kTmemCols = BN;
+  static constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kTileABytes + kTileBBytes) + 256;
+};
+// epilogues: FP32 D, or BF16 act(D + bias) (ReLU or none) with an optional
+// transposed BF16 copy
+enum { EPI_F32 = 0, EPI_BF16_BIAS = 1 };
+struct Epilogue {
+  float* D;                 // EPI_F32: D[row * ldd + col]
+  int64_t ldd;
+  uint16_t* H;              // EPI_BF16_BIAS: H[row * ldh + col] = bf16(act(D + bias[col]))
+  int64_t ldh;
+  uint16_t* HT;             //   and, if not null, HT[col * ldt + row]
+  int64_t ldt;
+  const float* bias;
+  int relu;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -151,12 +172,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // ------------------------------------------------------------------ the GEMM
-// grid (ceil(N / 128), ceil(M / 128)), kThreads threads, kSmemBytes dynamic
-// shared memory.  tmA: A as a 2D tensor {K, M} (row stride lda * 2 bytes), box
-// {64, 128}; tmB likewise for B {K, N}.  D row stride ldd (FP32).
+// grid (ceil(N / BN), ceil(M / 128)), kThreads threads, Tile<BN>::kSmemBytes
+// dynamic shared memory.  tmA: A as a 2D tensor {K, M} (row stride lda * 2
+// bytes), box {64, 128}; tmB likewise for B {K, N}, box {64, BN}.
+template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* D,
-                   int64_t ldd, int M, int N, int K, unsigned* err) {
+    k_gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const Epilogue ep, int M, int N, int K, unsigned* err) {
+  constexpr uint32_t kTileBBytes = Tile<BN>::kTileBBytes;
+  constexpr uint32_t kTmemCols = Tile<BN>::kTmemCols;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -169,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int s_fail;
 
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int m0 = (int)blockIdx.y * kBM, n0 = (int)blockIdx.x * kBN;
+  const int m0 = (int)blockIdx.y * kBM, n0 = (int)blockIdx.x * BN;
   const int nk = (K + kBK - 1) / kBK;
 
   if (threadIdx.x == 0) {
@@ -189,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+    const uint32_t idesc = idesc_bf16_f32(kBM, BN);
     auto load = [&](int kc, int s) {
       mbar_expect_tx(&full[s], kTileABytes + kTileBBytes);
       tma_load_2d(sA + (size_t)s * kTileABytes, &tmA, &full[s], kc * kBK, m0);
@@ -246,22 +270,56 @@ __global__ void __launch_bounds__(kThreads, 1)
     // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
     const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kBN; c0 += 32) {
+    for (int c0 = 0; c0 < BN; c0 += 32) {
       if (n0 + c0 >= N) break;
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) {
-        float* out = D + (int64_t)row * ldd + n0 + c0;
-        const int nc = N - (n0 + c0) < 32 ? N - (n0 + c0) : 32;
-        if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
+      const int nc = N - (n0 + c0) < 32 ? N - (n0 + c0) : 32;
+      if (EPI == EPI_F32) {
+        if (row < M) {
+          float* out = ep.D + (int64_t)row * ep.ldd + n0 + c0;
+          if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            *reinterpret_cast<float4*>(out + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
-                                                              __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
-        } else {
+            for (int i = 0; i < 32; i += 4)
+              *reinterpret_cast<float4*>(out + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+                                                                __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+          } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (i < nc) out[i] = __uint_as_float(r[i]);
+            for (int i = 0; i < 32; ++i)
+              if (i < nc) out[i] = __uint_as_float(r[i]);
+          }
+        }
+      } else {
+        // bias, activation and BF16 rounding; the row-major copy as packed
+        // pairs, the transposed copy with consecutive lanes on consecutive rows
+        uint32_t h[16];
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+          float v0 = __uint_as_float(r[i]) + (i < nc ? __ldg(&ep.bias[n0 + c0 + i]) : 0.0f);
+          float v1 = __uint_as_float(r[i + 1]) + (i + 1 < nc ? __ldg(&ep.bias[n0 + c0 + i + 1]) : 0.0f);
+          if (ep.relu) {
+            v0 = v0 > 0.0f ? v0 : 0.0f;
+            v1 = v1 > 0.0f ? v1 : 0.0f;
+          }
+          h[i / 2] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v0)) |
+                     ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v1)) << 16);
+        }
+        if (row < M) {
+          uint16_t* out = ep.H + (int64_t)row * ep.ldh + n0 + c0;
+          if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+              *reinterpret_cast<uint4*>(out + 2 * i) = make_uint4(h[i], h[i + 1], h[i + 2], h[i + 3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < nc) out[i] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
+          }
+          if (ep.HT) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < nc) ep.HT[(int64_t)(n0 + c0 + i) * ep.ldt + row] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
+          }
         }
       }
     }
