@@ -326,7 +326,8 @@ const char* hande_last_error(const hande_ctx* ctx);
  * legacy default stream): each phase of a group's iteration is one kernel
  * launch over all its replicas, whose blocks a planner kernel divides among
  * the replicas in proportion to their work (list length, last attempt count),
- * every replica reading its own parameter block; groups run on parallel graph
+ * every replica reading its own parameter block; groups (at most 8 replicas
+ * each unless hande_batch_autotune chose otherwise) run on parallel graph
  * branches.  Each replica also
  * owns a non-blocking stream used by single-replica calls on it (walkers,
  * estimators, hande_iterate of that replica alone), which is ordered with
@@ -355,9 +356,10 @@ hande_status hande_batch_iterate(hande_batch* b, int n_iterations);
  * hande_batch_synchronize returned (-1 if none). */
 int hande_batch_failed_replica(const hande_batch* b);
 
-/* Autotune the batched launch shape: for each candidate block budget (the
- * single run's grid of each phase times a scale in {0.5, 1, 2, 4}), time
- * `iterations` batched iterations and keep the fastest.  The iterations are
+/* Autotune the batched launch shape: for each candidate (replicas per group
+ * at most 4, 8, 16 or unlimited; block budget = the single run's grid of each
+ * phase times 1, 2 or 4), time `iterations` batched iterations and keep the
+ * fastest.  The iterations are
  * real (the replicas advance by (candidates + 1) x iterations); the walker
  * lists do not depend on the shape.  *best_scale and *best_ms (ms per batched
  * iteration) receive the choice (either may be NULL).  HANDE_ERR_STATE if a

@@ -41,7 +41,8 @@ struct hande_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   std::vector<int64_t> sig;            // per replica: epoch and deterministic-space state
-  double scale = 0.0;                  // block budget = single-run grid x scale (0 = 1)
+  double scale = 0.0;                  // block budget = single-run grid x scale (0 = 2)
+  int group_cap = 8;                   // replicas per group at most (0 = no limit)
   int last_failed = -1;
 };
 
@@ -55,24 +56,34 @@ void free_graphs(hande_batch* b) {
     }
 }
 
-void release(hande_batch* b) {
+// the groups' device arrays, streams and events
+void free_groups(hande_batch* b) {
   free_graphs(b);
   if (b->caller) cudaStreamSynchronize(b->caller);
-  for (hande_ctx* c : b->ctx) hande_destroy(c);  // synchronises each replica stream
   for (auto& g : b->groups) {
     if (g.d_params) cudaFree(g.d_params);
     if (g.d_off) cudaFree(g.d_off);
   }
-  for (cudaEvent_t e : b->done)
-    if (e) cudaEventDestroy(e);
   for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin})
     for (cudaEvent_t e : *v)
       if (e) cudaEventDestroy(e);
-  for (cudaStream_t s : b->streams)
-    if (s) cudaStreamDestroy(s);
   for (auto* v : {&b->gs, &b->gaux})
     for (cudaStream_t s : *v)
       if (s) cudaStreamDestroy(s);
+  b->groups.clear();
+  b->group_of.clear();
+  for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin}) v->clear();
+  b->gs.clear();
+  b->gaux.clear();
+}
+
+void release(hande_batch* b) {
+  free_groups(b);
+  for (hande_ctx* c : b->ctx) hande_destroy(c);  // synchronises each replica stream
+  for (cudaEvent_t e : b->done)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
@@ -114,7 +125,7 @@ bool same_group(const Engine& a, const Engine& c) {
 // a replica never gets more than 4 single-run grids, nor more list-pass blocks
 // than its scan partials hold.
 void set_grids(hande_batch* b) {
-  const double f = b->scale > 0.0 ? b->scale : 1.0;
+  const double f = b->scale > 0.0 ? b->scale : 2.0;
   for (auto& G : b->groups) {
     const Engine& E = *G.eng[0];
     const int base[hande::kPlanPhases] = {hande::kScanBlocks, E.attempt_grid, E.attempt_grid * 4,
@@ -129,6 +140,58 @@ void set_grids(hande_batch* b) {
   }
   free_graphs(b);
   b->sig.clear();
+}
+
+// Groups: replicas with the same kernels and launch shapes, at most
+// group_cap per group (each group is one chain of launches; several groups run
+// on parallel graph branches).
+hande_status regroup(hande_batch* b) {
+  free_groups(b);
+  const int n = (int)b->ctx.size();
+  b->group_of.assign((size_t)n, -1);
+  for (int r = 0; r < n; ++r) {
+    Engine& E = b->ctx[r]->E;
+    int g = -1;
+    for (size_t k = 0; k < b->groups.size(); ++k)
+      if (same_group(*b->groups[k].eng[0], E) && (b->group_cap <= 0 || (int)b->groups[k].eng.size() < b->group_cap))
+        g = (int)k;
+    if (g < 0) {
+      b->groups.emplace_back();
+      g = (int)b->groups.size() - 1;
+    }
+    b->groups[g].eng.push_back(&E);
+    b->group_of[r] = g;
+  }
+  const size_t ng = b->groups.size();
+  b->gs.assign(ng, nullptr);
+  b->gaux.assign(ng, nullptr);
+  b->gfork.assign(ng, nullptr);
+  b->gjoin.assign(ng, nullptr);
+  b->efork.assign(ng, nullptr);
+  b->ejoin.assign(ng, nullptr);
+  for (size_t k = 0; k < ng; ++k) {
+    BatchGroup& G = b->groups[k];
+    G.R = (int)G.eng.size();
+    const Engine& E = *G.eng[0];
+    bool good = ok(cudaMalloc(&G.d_params, sizeof(hande::Params) * (size_t)G.R)) &&
+                ok(cudaMalloc(&G.d_off, sizeof(int) * (size_t)hande::kPlanPhases * (G.R + 1))) &&
+                ok(cudaStreamCreateWithFlags(&b->gs[k], cudaStreamNonBlocking)) &&
+                ok(cudaStreamCreateWithFlags(&b->gaux[k], cudaStreamNonBlocking));
+    for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin})
+      good = good && ok(cudaEventCreateWithFlags(&(*v)[k], cudaEventDisableTiming));
+    good = good &&
+           ok(cudaFuncSetAttribute(E.ops.batch_attempt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)E.ops.attempt_smem)) &&
+           ok(cudaFuncSetAttribute(E.ops.batch_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)E.merge_smem_bytes));
+    if (E.merge_warp)
+      good = good && ok(cudaFuncSetAttribute(E.ops.batch_merge_warp_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)E.ops.merge_warp_smem));
+    if (!good) return HANDE_ERR_CUDA;
+  }
+  set_grids(b);
+  return HANDE_OK;
 }
 
 // upload the parameter blocks and capture the batched iteration for both
@@ -277,52 +340,10 @@ hande_status hande_batch_init(const hande_system* sys, const hande_qmc* qmc, int
     }
     b->ctx.push_back(c);
   }
-  // groups of replicas with the same kernels and launch shapes
-  b->group_of.assign((size_t)n, -1);
-  for (int r = 0; r < n; ++r) {
-    Engine& E = b->ctx[r]->E;
-    int g = -1;
-    for (size_t k = 0; k < b->groups.size(); ++k)
-      if (same_group(*b->groups[k].eng[0], E)) g = (int)k;
-    if (g < 0) {
-      b->groups.emplace_back();
-      g = (int)b->groups.size() - 1;
-    }
-    b->groups[g].eng.push_back(&E);
-    b->group_of[r] = g;
+  if (regroup(b) != HANDE_OK) {
+    release(b);
+    return HANDE_ERR_CUDA;
   }
-  const size_t ng = b->groups.size();
-  b->gs.assign(ng, nullptr);
-  b->gaux.assign(ng, nullptr);
-  b->gfork.assign(ng, nullptr);
-  b->gjoin.assign(ng, nullptr);
-  b->efork.assign(ng, nullptr);
-  b->ejoin.assign(ng, nullptr);
-  for (size_t k = 0; k < ng; ++k) {
-    BatchGroup& G = b->groups[k];
-    G.R = (int)G.eng.size();
-    const Engine& E = *G.eng[0];
-    bool good = ok(cudaMalloc(&G.d_params, sizeof(hande::Params) * (size_t)G.R)) &&
-                ok(cudaMalloc(&G.d_off, sizeof(int) * (size_t)hande::kPlanPhases * (G.R + 1))) &&
-                ok(cudaStreamCreateWithFlags(&b->gs[k], cudaStreamNonBlocking)) &&
-                ok(cudaStreamCreateWithFlags(&b->gaux[k], cudaStreamNonBlocking));
-    for (auto* v : {&b->gfork, &b->gjoin, &b->efork, &b->ejoin})
-      good = good && ok(cudaEventCreateWithFlags(&(*v)[k], cudaEventDisableTiming));
-    good = good &&
-           ok(cudaFuncSetAttribute(E.ops.batch_attempt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)E.ops.attempt_smem)) &&
-           ok(cudaFuncSetAttribute(E.ops.batch_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)E.merge_smem_bytes));
-    if (E.merge_warp)
-      good = good && ok(cudaFuncSetAttribute(E.ops.batch_merge_warp_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)E.ops.merge_warp_smem));
-    if (!good) {
-      release(b);
-      return HANDE_ERR_CUDA;
-    }
-  }
-  set_grids(b);
   hande_status st = join(b);
   if (st != HANDE_OK) {
     release(b);
@@ -353,13 +374,27 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
   if (!b || iterations < 1) return HANDE_ERR_INVALID;
   const int n = (int)b->ctx.size();
   (void)n;
-  const std::vector<double> cand = {0.5, 1.0, 2.0, 4.0};
+  struct Cand {
+    int cap;
+    double scale;
+  };
+  std::vector<Cand> cand;
+  for (int cap : {4, 8, 16, 0})
+    for (double f : {1.0, 2.0, 4.0}) cand.push_back({cap, f});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) return HANDE_ERR_CUDA;
-  double best = -1.0, bestf = cand[0];
+  double best = -1.0;
+  Cand bestc = cand[0];
   hande_status st = join(b);
   for (size_t i = 0; i < cand.size() && st == HANDE_OK; ++i) {
-    b->scale = cand[i];
+    b->scale = cand[i].scale;
+    if (b->group_cap != cand[i].cap || b->groups.empty()) {
+      b->group_cap = cand[i].cap;
+      if (regroup(b) != HANDE_OK) {
+        st = HANDE_ERR_CUDA;
+        break;
+      }
+    }
     set_grids(b);
     // one untimed iteration captures the graphs for this shape
     st = batchable(b) ? batched_iteration(b) : HANDE_ERR_STATE;
@@ -373,7 +408,7 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
     const double per = ms / iterations;
     if (best < 0.0 || per < best) {
       best = per;
-      bestf = cand[i];
+      bestc = cand[i];
     }
   }
   cudaEventDestroy(e0);
@@ -381,15 +416,18 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
   if (st == HANDE_ERR_STATE) {
     // a replica needs per-iteration host work: keep the default shape
     b->scale = 0.0;
-    set_grids(b);
+    b->group_cap = 8;
+    hande_status rs = regroup(b);
     fork_all(b);
-    return HANDE_ERR_STATE;
+    return rs != HANDE_OK ? rs : HANDE_ERR_STATE;
   }
-  b->scale = bestf;
-  set_grids(b);
+  b->scale = bestc.scale;
+  b->group_cap = bestc.cap;
+  hande_status rs = regroup(b);
   hande_status fs = fork_all(b);
-  if (best_scale) *best_scale = bestf;
+  if (best_scale) *best_scale = bestc.scale;
   if (best_ms) *best_ms = best;
+  if (rs != HANDE_OK) return rs;
   return st != HANDE_OK ? st : fs;
 }
 

@@ -1173,8 +1173,10 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid 
 template <int W, int SYS>
 __global__ void __launch_bounds__(kAttemptThreads) k_attempt(Params P, int cur) { d_attempt<W, SYS>(P, cur, VGrid{(int)blockIdx.x, (int)gridDim.x}); }
 // the same for replica blockIdx.y of a batch (parameter blocks PP[replica])
+// (two blocks per SM as for the single-run kernel: the shared-memory parameter
+// block would otherwise raise the register count past that)
 template <int W, int SYS>
-__global__ void __launch_bounds__(kAttemptThreads) kb_attempt(const Params* PP, const int* off, int R, int cur) {
+__global__ void __launch_bounds__(kAttemptThreads, 2) kb_attempt(const Params* PP, const int* off, int R, int cur) {
   __shared__ Params sP;
   __shared__ VGrid vg;
   if (!batch_block(PP, off, R, sP, vg)) return;
