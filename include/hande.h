@@ -360,7 +360,7 @@ int hande_batch_failed_replica(const hande_batch* b);
  * at most 4, 8, 16 or unlimited; block budget = the single run's grid of each
  * phase times 1, 2 or 4), time `iterations` batched iterations and keep the
  * fastest.  The iterations are
- * real (the replicas advance by (candidates + 1) x iterations); the walker
+ * real (the replicas advance by 12 x (iterations + 1)); the walker
  * lists do not depend on the shape.  *best_scale and *best_ms (ms per batched
  * iteration) receive the choice (either may be NULL).  HANDE_ERR_STATE if a
  * replica needs per-iteration host work.  Synchronises. */
