@@ -222,6 +222,22 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
 hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
                                int64_t n);
 
+/* Launch and bucket geometry chosen by hande_autotune. */
+typedef struct {
+  int bucket_spawns;      /* expected spawns per annihilation bucket */
+  int bucket_new;         /* expected distinct new determinants per bucket (warp path) */
+  int attempt_blocks;     /* blocks of the spawning kernel */
+  double ms_per_iteration;
+} hande_tuning;
+
+/* Autotune the annihilation bucket size (expected spawns and new determinants
+ * per bucket, 0.5 to 1.25 times the defaults) and the spawning kernel's grid
+ * (one or two blocks per SM): time `iterations` iterations of each candidate
+ * and keep the fastest.  The iterations are real (the run advances by
+ * 16 x (iterations + 1)); the walker lists do not depend on the choice.  *out
+ * (may be NULL) receives it.  Synchronises. */
+hande_status hande_autotune(hande_ctx* ctx, int iterations, hande_tuning* out);
+
 /* Diagnostics of the last iteration (synchronises; usable after an error). */
 typedef struct {
   uint32_t error_bits;        /* device error latch: 1 spawn capacity, 2 walker capacity,

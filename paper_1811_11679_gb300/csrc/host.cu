@@ -1348,6 +1348,65 @@ hande_status hande_learn_refresh(hande_ctx* ctx) {
   });
 }
 
+hande_status hande_autotune(hande_ctx* ctx, int iterations, hande_tuning* out) {
+  if (!ctx || iterations < 1) return HANDE_ERR_INVALID;
+  Engine& E = ctx->E;
+  if (E.failed) return HANDE_ERR_STATE;
+  return run_guarded(&E, [&]() -> hande_status {
+    const int dflt_sp = E.P.bucket_spawns, dflt_new = E.P.bucket_new, dflt_grid = E.attempt_grid;
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, E.device));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    struct Cleanup {
+      cudaEvent_t a, b;
+      ~Cleanup() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+      }
+    } cleanup{e0, e1};
+    hande_tuning best{dflt_sp, dflt_new, dflt_grid, -1.0};
+    for (double fs : {0.5, 0.75, 1.0, 1.25})
+      for (double fn : {0.5, 1.0})
+        for (int per_sm : {1, 2}) {
+          const int grid = std::min(dflt_grid, per_sm * nsm);
+          E.P.bucket_spawns = std::max(1, (int)(dflt_sp * fs));
+          E.P.bucket_new = dflt_new > 0 ? std::max(1, (int)(dflt_new * fn)) : 0;
+          E.attempt_grid = grid;
+          drop_graphs(E, 0);
+          drop_graphs(E, 1);
+          hande_status st = hande_iterate(ctx, 1);   // captures the graphs for this shape
+          if (st == HANDE_OK) {
+            CK(cudaEventRecord(e0, E.stream));
+            st = hande_iterate(ctx, iterations);
+          }
+          if (st != HANDE_OK) {   // back to the defaults (the context may still be usable)
+            E.P.bucket_spawns = dflt_sp;
+            E.P.bucket_new = dflt_new;
+            E.attempt_grid = dflt_grid;
+            drop_graphs(E, 0);
+            drop_graphs(E, 1);
+            return st;
+          }
+          CK(cudaEventRecord(e1, E.stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.0f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          const double per = ms / iterations;
+          if (best.ms_per_iteration < 0.0 || per < best.ms_per_iteration)
+            best = hande_tuning{E.P.bucket_spawns, E.P.bucket_new, grid, per};
+        }
+    E.P.bucket_spawns = best.bucket_spawns;
+    E.P.bucket_new = best.bucket_new;
+    E.attempt_grid = best.attempt_blocks;
+    drop_graphs(E, 0);
+    drop_graphs(E, 1);
+    if (out) *out = best;
+    return map_error(E, read_error(E));
+  });
+}
+
 hande_status hande_diagnostics(hande_ctx* ctx, hande_diag* out) {
   if (!ctx || !out) return HANDE_ERR_INVALID;
   Engine& E = ctx->E;

@@ -769,15 +769,17 @@ static __global__ void kb_core_apply(const Params* PP, int cur) {
 // Attempts are processed 32 per warp.  Lanes diverge on what an attempt
 // produces (nothing, a spawn, a molecular single needing an O(N) matrix
 // element), so the rare outcomes go through per-warp shared-memory queues and
-// are finished 32 at a time by full warps: singles (evaluate H_ia, weight,
-// rounding) and spawns (bucket search, append to the staging arrays).
+// are finished 32 at a time by full warps: singles (select the orbitals,
+// evaluate H_ia, weight, rounding) and spawns (bucket search, append to the
+// staging arrays).  Two CTAs share an SM: the shared memory below stays
+// under half of an SM's 228 KB for every key width and system.
 constexpr int kAttemptThreads = 512;
 constexpr int kAttemptWarps = kAttemptThreads / 32;
 constexpr int kQueue = 64;   // per-warp queue capacity (holds 31 + 32 entries)
 
-template <int W>
+template <int W, int SYS>
 __host__ __device__ constexpr int attempt_split_smem() {
-  return W == 8 ? 256 : (W == 2 ? 2048 : 4096);
+  return W == 8 ? (SYS == SYS_MOLECULE ? 128 : 256) : (W == 2 ? 2048 : 4096);
 }
 // molecular generator tables copied to shared memory for 64-bit keys (at most
 // 64 spin orbitals): the pair records (int4) and the pair unranking table
@@ -786,16 +788,23 @@ template <int W, int SYS>
 __host__ __device__ constexpr size_t attempt_stage_bytes() {
   return (SYS == SYS_MOLECULE && W == 1) ? (size_t)kStagePairs * (16 + 2) : 0;
 }
+// per-warp queue bytes per entry: spawns (key, amount, flag) and, for
+// molecules, singles (parent, words w and z, occupied rank)
+template <int W, int SYS>
+__host__ __device__ constexpr size_t attempt_queue_entry() {
+  return (size_t)(8 * W + 8 + 1) + (SYS == SYS_MOLECULE ? (size_t)(8 + 8 + 8 + 1) : 0);
+}
 template <int W, int SYS>
 __host__ __device__ inline size_t attempt_smem_bytes() {
-  return (size_t)attempt_split_smem<W>() * 8 * W + attempt_stage_bytes<W, SYS>() +
-         (size_t)kAttemptWarps * kQueue * (8 + 8 + 2 + 8 * W + 8 + 1) + 256;
+  return (size_t)attempt_split_smem<W, SYS>() * 8 * W + attempt_stage_bytes<W, SYS>() +
+         (size_t)kAttemptWarps * kQueue * attempt_queue_entry<W, SYS>() + 256;
 }
 
 struct AttemptQueues {
   int64_t* sq_par;     // pending singles: parent index
   uint64_t* sq_word;   // their Philox word w (rounding)
-  uint16_t* sq_ia;     // hole | particle << 8
+  uint64_t* sq_wz;     // word z (empty orbital)
+  uint8_t* sq_ri;      // rank of the occupied orbital, draw_index(w.y, N)
   uint64_t* pq_key;    // finished spawns: key words [W][kQueue]
   int64_t* pq_amt;
   uint8_t* pq_flg;
@@ -913,7 +922,8 @@ __device__ __forceinline__ void push_spawn(const Params& P, const AttemptQueues&
   if (pq_n >= 32) flush_spawns<W>(P, Q, pq_n, 32, sx);
 }
 
-// the top `take` queued molecular singles: H_ia, core test, weight, rounding
+// the top `take` queued molecular singles: orbitals, H_ia, core test, weight,
+// rounding
 template <int W, int SYS>
 __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n, int& pq_n, int take,
                               const uint64_t* key, const uint8_t* fl, const SplitIdx& sx) {
@@ -927,14 +937,15 @@ __device__ void flush_singles(const Params& P, const AttemptQueues& Q, int& sq_n
     const int e = sq_n - take + lane;
     const int64_t par = Q.sq_par[e];
     const uint64_t u = Q.sq_word[e];
-    const int i = Q.sq_ia[e] & 0xff, a = Q.sq_ia[e] >> 8;
     const Key<W> k = load_key<W>(key, P.cap, par);
     const uint8_t f = fl[par];
+    int i = 0, a = 0;
+    const bool drawn = single_orbitals<W>(P.sys, k, Q.sq_ri[e], Q.sq_wz[e], i, a);
     child = k;
     key_flip<W>(child, i);
     key_flip<W>(child, a);
-    const double hij = h_single<W, SYS>(P.sys, k, i, a);
-    if (nonzero(hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
+    const double hij = drawn ? h_single<W, SYS>(P.sys, k, i, a) : 0.0;
+    if (drawn && nonzero(hij) && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, child))) {
       if (P.tau_search) rmax = __dmul_rn(fabs(hij), P.sys.inv_single[i & 1]);
       const uint64_t famt = fixed_amount(abs_bits(hij), dbl_bits(P.sys.c_single[i & 1]), P.sys.half);
       amt = spawn_amount(P, famt, sign_bit(hij), u, f);
@@ -1015,7 +1026,7 @@ template <int W, int SYS>
 __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid vg) {
   DevState* st = P.st;
   if (st->error) return;
-  constexpr int KS = attempt_split_smem<W>();
+  constexpr int KS = attempt_split_smem<W, SYS>();
   extern __shared__ __align__(16) unsigned char att_smem[];
   uint64_t* ssplit = reinterpret_cast<uint64_t*>(att_smem);
   const int wid = threadIdx.x >> 5;
@@ -1023,17 +1034,24 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid 
   {
     unsigned char* p = att_smem + (size_t)KS * 8 * W + attempt_stage_bytes<W, SYS>();
     const size_t per = kQueue;
-    Q.sq_par = reinterpret_cast<int64_t*>(p) + wid * per;
-    p += kAttemptWarps * per * 8;
-    Q.sq_word = reinterpret_cast<uint64_t*>(p) + wid * per;
-    p += kAttemptWarps * per * 8;
     Q.pq_key = reinterpret_cast<uint64_t*>(p) + wid * per * W;
     p += kAttemptWarps * per * 8 * W;
     Q.pq_amt = reinterpret_cast<int64_t*>(p) + wid * per;
     p += kAttemptWarps * per * 8;
-    Q.sq_ia = reinterpret_cast<uint16_t*>(p) + wid * per;
-    p += kAttemptWarps * per * 2;
     Q.pq_flg = reinterpret_cast<uint8_t*>(p) + wid * per;
+    p += kAttemptWarps * per;   // a multiple of 8 bytes
+    Q.sq_par = nullptr;
+    Q.sq_word = Q.sq_wz = nullptr;
+    Q.sq_ri = nullptr;
+    if (SYS == SYS_MOLECULE) {
+      Q.sq_par = reinterpret_cast<int64_t*>(p) + wid * per;
+      p += kAttemptWarps * per * 8;
+      Q.sq_word = reinterpret_cast<uint64_t*>(p) + wid * per;
+      p += kAttemptWarps * per * 8;
+      Q.sq_wz = reinterpret_cast<uint64_t*>(p) + wid * per;
+      p += kAttemptWarps * per * 8;
+      Q.sq_ri = reinterpret_cast<uint8_t*>(p) + wid * per;
+    }
   }
   const int64_t natt = st->natt;
   const int64_t n = st->ndet[cur];
@@ -1128,8 +1146,8 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid 
     Key<W> child;
     int64_t amt = 0;
     uint8_t initf = 0;
-    uint64_t word = 0;
-    uint16_t ia = 0;
+    uint64_t word = 0, wz = 0;
+    uint8_t ri = 0;
     double rmax = 0.0;
     if (g < gend) {
       const uint64_t a = (uint64_t)(g - abeg);
@@ -1141,7 +1159,8 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid 
       if (ex.single) {
         single = true;
         word = w.w;
-        ia = (uint16_t)(ex.si | (ex.sa << 8));
+        wz = w.z;
+        ri = (uint8_t)draw_index(w.y, (uint64_t)P.sys.nel);
       } else if (ex.ok && !((f & F_CORE) && P.ncore > 0 && in_core<W>(P, ex.child))) {
         rmax = fmax(rmax, ex.rval);
         amt = spawn_amount(P, ex.famt, ex.hneg, w.w, f);
@@ -1156,7 +1175,8 @@ __device__ __forceinline__ void d_attempt(const Params& P, int cur, const VGrid 
         const int e = sq_n + __popc(sm & ((1u << lane) - 1u));
         Q.sq_par[e] = par;
         Q.sq_word[e] = word;
-        Q.sq_ia[e] = ia;
+        Q.sq_wz[e] = wz;
+        Q.sq_ri[e] = ri;
       }
       sq_n += __popc(sm);
       __syncwarp();

@@ -248,9 +248,8 @@ __device__ double h_elem(const SysDev& s, const Key<W>& src, const Key<W>& tgt) 
 template <int W>
 struct Excitation {
   bool ok;               // a connected child with H != 0 was drawn
-  bool single;           // a molecular single: selected only (si, sa), evaluated later
+  bool single;           // a molecular single: chosen only, its orbitals and H_ia left to the caller
   bool hneg;             // H_child,parent < 0
-  int si, sa;
   int prow, pA;          // proposal table: the row and particle orbital drawn (prow < 0: none)
   uint32_t pqa, pQ;      //   the drawn weight q_A and the row total Q
   double rval;           // |H| / p_gen = (|H| inv_a) inv_b when the system's want_r is set
@@ -284,6 +283,25 @@ __device__ __forceinline__ Key<W> spin_mask(int spin, int nspin) {
     m.w[j] = x;
   }
   return m;
+}
+
+// orbitals of a molecular single: i the ri-th occupied spin orbital of d
+// (ri = draw_index(w.y, N), uniform), a uniform among the empty orbitals of
+// i's spin by Philox word wz; false when that spin has no empty orbital
+// (nothing is spawned)
+template <int W>
+__device__ __forceinline__ bool single_orbitals(const SysDev& s, const Key<W>& d, int ri, uint64_t wz, int& i,
+                                               int& a) {
+  i = select_bit<W>(d, ri);
+  Key<W> empty = spin_mask<W>(i & 1, s.nspin);
+#pragma unroll
+  for (int j = 0; j < W; ++j) empty.w[j] &= ~d.w[j];
+  int ne = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) ne += __popcll(empty.w[j]);
+  if (ne == 0) return false;
+  a = select_bit<W>(empty, (int)draw_index(wz, (uint64_t)ne));
+  return true;
 }
 
 template <int W>
@@ -386,17 +404,9 @@ __device__ Excitation<W> generate(const SysDev& s, const GenTabs& gt, const Key<
     return e;
   } else {
     if ((uint32_t)(w.x >> 32) < s.psingle_thr) {
-      int i = select_bit<W>(d, (int)draw_index(w.y, (uint64_t)n));
-      Key<W> empty = spin_mask<W>(i & 1, s.nspin);
-#pragma unroll
-      for (int j = 0; j < W; ++j) empty.w[j] &= ~d.w[j];
-      int ne = 0;
-#pragma unroll
-      for (int j = 0; j < W; ++j) ne += __popcll(empty.w[j]);
-      if (ne == 0) return e;
+      // a single: its orbitals (i from w.y, a from w.z) are selected by
+      // single_orbitals when the caller evaluates the queued singles
       e.single = true;
-      e.si = i;
-      e.sa = select_bit<W>(empty, (int)draw_index(w.z, (uint64_t)ne));
       return e;
     }
     uint64_t npairs = (uint64_t)n * (n - 1) / 2;

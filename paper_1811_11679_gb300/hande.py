@@ -75,6 +75,11 @@ class _Learning(C.Structure):
                 ("seed", C.c_uint64)]
 
 
+class _Tuning(C.Structure):
+    _fields_ = [("bucket_spawns", C.c_int), ("bucket_new", C.c_int), ("attempt_blocks", C.c_int),
+                ("ms_per_iteration", C.c_double)]
+
+
 class _State(C.Structure):
     _fields_ = [("iter", C.c_int64), ("shift", C.c_double), ("nw_ref", C.c_int64), ("vary", C.c_int),
                 ("core_active", C.c_int), ("ncore", C.c_int64), ("tau", C.c_double), ("rmax", C.c_double)]
@@ -89,7 +94,7 @@ class _Diag(C.Structure):
 
 # names declared in include/hande.h, in order
 EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_synchronize", "hande_estimators", "hande_get_walkers",
-           "hande_set_walkers", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
+           "hande_set_walkers", "hande_autotune", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
            "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
            "hande_batch_init", "hande_batch_iterate", "hande_batch_failed_replica", "hande_batch_autotune",
            "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize", "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
@@ -135,6 +140,8 @@ def load(build_if_needed: bool = True):
         lib.hande_last_error.restype = C.c_char_p
         lib.hande_diagnostics.argtypes = [P, C.POINTER(_Diag)]
         lib.hande_estimate_noalloc.argtypes = [P, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]
+        lib.hande_autotune.argtypes = [P, C.c_int, C.POINTER(_Tuning)]
+        lib.hande_autotune.restype = C.c_int
         lib.hande_get_state.argtypes = [P, C.POINTER(_State), u64p, C.c_int64]
         lib.hande_set_state.argtypes = [P, C.POINTER(_State), u64p]
         for name in EXPORTS[:12]:
@@ -301,6 +308,13 @@ class Hande:
         d = _Diag()
         self._check(self._lib.hande_diagnostics(self._h, C.byref(d)), "hande_diagnostics")
         return {name: getattr(d, name) for name, _ in _Diag._fields_}
+
+    def autotune(self, iterations: int = 5) -> dict:
+        """Choose bucket sizes and the spawning grid by timing (include/hande.h,
+        hande_autotune); the run advances, its walker lists do not change."""
+        t = _Tuning()
+        self._check(self._lib.hande_autotune(self._h, int(iterations), C.byref(t)), "hande_autotune")
+        return {name: getattr(t, name) for name, _ in _Tuning._fields_}
 
     def launches_per_iteration(self) -> int:
         """Kernels one iteration launches with the current settings."""
