@@ -1806,19 +1806,39 @@ __device__ __forceinline__ void d_merge(const Params& P, int cur, int staged, co
   c.staged = staged;
   const uint64_t* key = P.key[cur];
   int64_t nwsum = 0;
+  // large-bucket pass: blocks claim chunks of blockDim.x buckets (one ticket
+  // each) and list the chunk's large buckets (more spawns than a warp takes)
+  __shared__ int s_big[kMergeThreads];
+  __shared__ int s_nbig, s_pbig;
+  __shared__ int64_t s_chunk;
+  if (threadIdx.x == 0) s_nbig = s_pbig = 0;
+  __syncthreads();
   for (;;) {
+    if (staged == 2) {
+      const int64_t lim = 8 * (int64_t)P.warp_cap;
+      for (;;) {
+        if (s_pbig < s_nbig) break;   // block-uniform (read after a barrier)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          s_nbig = s_pbig = 0;
+          s_chunk = st->error ? nb : (int64_t)atomicAdd(&st->big_ticket, (unsigned)blockDim.x);
+        }
+        __syncthreads();
+        const int64_t c0 = s_chunk;
+        if (c0 >= nb) break;
+        const int64_t bb = c0 + threadIdx.x;
+        if (bb < nb && (int64_t)P.bcount[bb] > lim) s_big[atomicAdd(&s_nbig, 1)] = (int)bb;
+        __syncthreads();
+      }
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       s_abort = 0;
       if (st->error) {
         tile_id = -1;
-      } else if (staged == 2) {   // the large buckets (more spawns than a warp takes)
-        const int64_t lim = 8 * (int64_t)P.warp_cap;
-        int64_t tk;
-        do {
-          tk = (int64_t)atomicAdd(&st->big_ticket, 1u);
-        } while (tk < st->nbuckets && (int64_t)P.bcount[tk] <= lim);
-        tile_id = tk < st->nbuckets ? (int)tk : -1;
-        if (tk < st->nbuckets) atomicAdd((unsigned long long*)&st->nbig, 1ull);
+      } else if (staged == 2) {
+        tile_id = s_pbig < s_nbig ? s_big[s_pbig++] : -1;
+        if (tile_id >= 0) atomicAdd((unsigned long long*)&st->nbig, 1ull);
       } else if (staged) {        // the buckets the warp kernel deferred
         const int64_t tk = (int64_t)atomicAdd(&st->defer_ticket, 1u);
         tile_id = tk < st->ndefer ? (int)P.att_begin[tk] : -1;
