@@ -476,6 +476,7 @@ def batched_leg(dev, replicas=64, grow=300, steps=50):
 
     ms_b = timed(lambda: b.iterate(steps))
     att_b = float(sum(v.estimators()["natt"].sum() for v in b.replicas))
+    groups, cap = b.layout()
 
     def plain():
         for _ in range(steps):
@@ -489,7 +490,7 @@ def batched_leg(dev, replicas=64, grow=300, steps=50):
     b.close()
     return {"replicas": replicas, "steps": steps, "grow_iterations": grow,
             "batched": {"attempts_per_s": att_b / (ms_b / 1e3), "ms_per_step": ms_b / steps,
-                        "autotuned_scale": scale},
+                        "autotuned_scale": scale, "launch_groups": groups, "replicas_per_group_max": cap},
             "plain_back_to_back": {"attempts_per_s": att_p / (ms_p / 1e3), "ms_per_step": ms_p / steps,
                                    "kernel_launches_per_step": launches},
             "speedup": (att_b / ms_b) / (att_p / ms_p),
@@ -627,6 +628,36 @@ def run_profile_case(args):
     eng.close()
 
 
+def run_profile_batched(args):
+    """Launch-list case of the batched form: the batched leg's replicas grown
+    300 iterations and autotuned, then 3 batched iterations and 3 iterations of
+    every replica on the plain path inside one profiler range."""
+    import torch
+
+    from paper_1811_11679_gb300 import hande, inputs
+    torch.cuda.set_device(0)
+    systems, qmcs = inputs.batched_replicas(args.profile_batched)
+    b = hande.HandeBatch(systems, qmcs)
+    b.iterate(300)
+    scale, ms = b.autotune(iterations=3)
+    groups, cap = b.layout()
+    b.synchronize()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    b.iterate(3)
+    torch.cuda.synchronize()
+    for _ in range(3):
+        for v in b.replicas:
+            v.iterate(1)
+    for v in b.replicas:
+        v.synchronize()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_batched": True, "replicas": len(b), "autotuned_scale": scale,
+                      "launch_groups": groups, "replicas_per_group_max": cap, "tuned_ms_per_iteration": ms}))
+    b.close()
+
+
 def run_batched(args):
     """Batched replicas (inputs.batched_replicas: UEG 14e in 38/66 orbitals, four
     r_s, targets log-uniform in [1e4, 1e6]) advanced together through
@@ -699,6 +730,11 @@ def main():
     ap.add_argument("--no-configs", action="store_true", help="skip the Hubbard and UEG lines")
     ap.add_argument("--profile-case", action="store_true",
                     help="small synthetic-start case for ncu captures (no timing output)")
+    ap.add_argument("--profile-gemm", action="store_true",
+                    help="the tensor-core GEMM shapes alone, two timed calls each (for ncu captures)")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="this many batched UEG replicas: 3 batched then 3 plain iterations inside a "
+                         "profiler range (ncu --profile-from-start off)")
     ap.add_argument("--batched", type=int, default=0,
                     help="time this many batched UEG replicas instead of the molecule workload")
     ap.add_argument("--batched-grow", type=int, default=600,
@@ -709,6 +745,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_batched > 0:
+        run_profile_batched(args)
+        return
+    if args.profile_gemm:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"profile_gemm": True, **tensor_core_leg(torch.cuda.current_device(), calls=2)}))
         return
     if args.batched > 0:
         print(json.dumps(run_batched(args)), flush=True)

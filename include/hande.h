@@ -374,9 +374,9 @@ int hande_batch_failed_replica(const hande_batch* b);
 
 /* Autotune the batched launch shape: for each candidate (replicas per group
  * at most 4, 8, 16 or unlimited; block budget = the single run's grid of each
- * phase times 1, 2 or 4), time `iterations` batched iterations and keep the
- * fastest.  The iterations are
- * real (the replicas advance by 12 x (iterations + 1)); the walker
+ * phase times 1, 2, 4 or 8), time `iterations` batched iterations and keep
+ * the fastest.  The iterations are
+ * real (the replicas advance by 16 x (iterations + 1)); the walker
  * lists do not depend on the shape.  *best_scale and *best_ms (ms per batched
  * iteration) receive the choice (either may be NULL).  HANDE_ERR_STATE if a
  * replica needs per-iteration host work.  Synchronises. */
@@ -384,6 +384,12 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
 
 /* Number of replicas (0 for NULL). */
 int hande_batch_size(const hande_batch* b);
+
+/* Launch layout in use: *groups (may be NULL) receives the number of launch
+ * groups of a batched iteration (0 before the first batched iteration) and
+ * *group_cap (may be NULL) the most replicas a group takes (0 = no limit).
+ * HANDE_ERR_INVALID for NULL b. */
+hande_status hande_batch_layout(const hande_batch* b, int* groups, int* group_cap);
 
 /* Context of replica r, owned by the batch (NULL when r is out of range).  All
  * single-context calls apply to it; hande_iterate on it advances that replica

@@ -380,7 +380,7 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
   };
   std::vector<Cand> cand;
   for (int cap : {4, 8, 16, 0})
-    for (double f : {1.0, 2.0, 4.0}) cand.push_back({cap, f});
+    for (double f : {1.0, 2.0, 4.0, 8.0}) cand.push_back({cap, f});
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!ok(cudaEventCreate(&e0)) || !ok(cudaEventCreate(&e1))) return HANDE_ERR_CUDA;
   double best = -1.0;
@@ -432,6 +432,13 @@ hande_status hande_batch_autotune(hande_batch* b, int iterations, double* best_s
 }
 
 int hande_batch_size(const hande_batch* b) { return b ? (int)b->ctx.size() : 0; }
+
+hande_status hande_batch_layout(const hande_batch* b, int* groups, int* group_cap) {
+  if (!b) return HANDE_ERR_INVALID;
+  if (groups) *groups = (int)b->groups.size();
+  if (group_cap) *group_cap = b->group_cap;
+  return HANDE_OK;
+}
 
 hande_ctx* hande_batch_replica(hande_batch* b, int r) {
   if (!b || r < 0 || r >= (int)b->ctx.size()) return nullptr;

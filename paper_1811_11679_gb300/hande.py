@@ -97,7 +97,7 @@ EXPORTS = ["hande_init_system", "hande_iterate", "hande_iterate_timed", "hande_s
            "hande_set_walkers", "hande_autotune", "hande_diagnostics", "hande_estimate_noalloc", "hande_get_state", "hande_set_state",
            "hande_reference", "hande_iterations", "hande_destroy", "hande_last_error",
            "hande_batch_init", "hande_batch_iterate", "hande_batch_failed_replica", "hande_batch_autotune",
-           "hande_batch_size", "hande_batch_replica", "hande_batch_synchronize", "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
+           "hande_batch_size", "hande_batch_layout", "hande_batch_replica", "hande_batch_synchronize", "hande_batch_destroy", "hande_set_proposal", "hande_get_proposal", "hande_learn_proposal",
            "hande_learn_params", "hande_learn_gradients", "hande_learn_probabilities", "hande_learn_refresh",
            "hande_gemm_bf16"]
 
@@ -150,6 +150,8 @@ def load(build_if_needed: bool = True):
                                          C.POINTER(P), C.POINTER(C.c_int)]
         lib.hande_batch_iterate.argtypes = [P, C.c_int]
         lib.hande_batch_size.argtypes = [P]
+        lib.hande_batch_layout.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        lib.hande_batch_layout.restype = C.c_int
         lib.hande_batch_replica.argtypes = [P, C.c_int]
         lib.hande_batch_replica.restype = P
         lib.hande_batch_synchronize.argtypes = [P]
@@ -578,6 +580,15 @@ class HandeBatch:
         if rc != 0:
             self._raise(rc, "hande_batch_autotune")
         return f.value, ms.value
+
+    def layout(self):
+        """(launch groups of a batched iteration, most replicas per group; 0 =
+        no limit) as now in use (include/hande.h, hande_batch_layout)."""
+        g, cap = C.c_int(), C.c_int()
+        rc = self._lib.hande_batch_layout(self._h, C.byref(g), C.byref(cap))
+        if rc != 0:
+            self._raise(rc, "hande_batch_layout")
+        return g.value, cap.value
 
     def close(self) -> None:
         if self._h:

@@ -70,6 +70,7 @@ def test_batch_arguments_rejected_before_any_device_call():
     assert lib.hande_batch_iterate(None, 1) == -1
     assert lib.hande_batch_synchronize(None) == -1
     assert lib.hande_batch_size(None) == 0
+    assert lib.hande_batch_layout(None, None, None) == -1
     assert lib.hande_batch_replica(None, 0) is None
     lib.hande_batch_destroy(None)
 

@@ -133,7 +133,9 @@ def test_autotune_keeps_the_walker_lists():
     a.iterate(20)
     b.iterate(20)
     scale, ms = a.autotune(iterations=3)
-    assert 0.0 < scale <= 1.0 and ms > 0.0
+    assert scale in (1.0, 2.0, 4.0, 8.0) and ms > 0.0
+    groups, cap = a.layout()
+    assert cap in (0, 4, 8, 16) and 1 <= groups <= len(runs)
     done = a.replicas[0].iterations
     b.iterate(done - 20)
     a.iterate(10)
