@@ -153,8 +153,8 @@ def _phase_bytes(rec, W):
 # kernel on the profile case (profiles/kernels_molecule28_profile_case.md);
 # the peak is 4 warp instructions per cycle per SM (one per sub-partition) on
 # 152 SMs at the maximum SM clock.
-ATTEMPT_INST_PER_ATTEMPT = 246563229 / 7571203
-ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.644800e6 + 7.361024e6) / 7571203
+ATTEMPT_INST_PER_ATTEMPT = 235755617 / 7571203
+ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.771008e6 + 7.630336e6) / 7571203
 N_SM = 152
 
 
@@ -503,11 +503,14 @@ def tensor_core_leg(dev, calls=20):
     """The tensor-core GEMM alone (tcgen05 MMAs, TMA tiles, TMEM accumulators)
     at the learned proposal's shapes: the table refresh of a 246-orbital basis
     (2 x 246^2 rows, first layer K = 512 and hidden layer K = 256) and a
-    4096-sample training batch; FLOP/s against the measured BF16 burst peak."""
+    4096-sample training batch; FLOP/s against the measured BF16 burst peak
+    and, since these shapes sit below the ridge point, algorithmic bytes/s
+    against the measured copy bandwidth."""
     import torch
 
     from paper_1811_11679_gb300 import hande
     peak = _bf16_peak()
+    hbm = _peaks()
     stream = torch.cuda.current_stream(dev)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     rows = []
@@ -529,12 +532,17 @@ def tensor_core_leg(dev, calls=20):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / calls
         tf = 2.0 * m * n * k / (ms / 1e3) / 1e12
+        # algorithmic bytes: A and B read once (BF16), D written once (FP32)
+        byt = 2.0 * (m * k + n * k) + 4.0 * m * n
+        gbs = byt / (ms / 1e3) / 1e9
         rows.append({"shape": what, "m": m, "n": n, "k": k, "us_per_launch": ms * 1e3, "tflops": tf,
-                     "frac": tf / peak[0]})
+                     "frac": tf / peak[0], "bytes": int(byt), "hbm_gbs": gbs, "hbm_frac": gbs / hbm[0]})
     assert int(status.item()) == 0, "tensor-core GEMM wait timed out"
     best = max(rows, key=lambda x: x["tflops"])
     return {"bound": "tensor", "achieved": round(best["tflops"], 1), "peak": peak[0], "unit": "TFLOP/s",
             "frac": round(best["frac"], 4), "traffic": None, "peak_source": peak[1], "kernel": "k_gemm_bf16_tn",
+            "hbm": {"achieved": round(best["hbm_gbs"], 1), "peak": hbm[0], "unit": "GB/s",
+                    "frac": round(best["hbm_frac"], 4), "peak_source": hbm[1]},
             "shapes": rows}
 
 
