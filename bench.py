@@ -156,6 +156,17 @@ def _phase_bytes(rec, W):
 ATTEMPT_INST_PER_ATTEMPT = 235755617 / 7571203
 ATTEMPT_DRAM_BYTES_PER_ATTEMPT = (89.771008e6 + 7.630336e6) / 7571203
 N_SM = 152
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of each phase's
+# kernels in the profile case's 4th iteration, and that iteration's counts
+# (profiles/traffic_molecule28_profile_case.md).  A phase's `traffic` in the
+# bench line is its ratio of these bytes to its algorithmic bytes times the
+# bench's own algorithmic bytes: both grow with the list and the spawns.
+PROFILE_CASE_REC = {"nspawn": 892485, "ndet_pre": 4040607, "ndet": 4031282}
+PROFILE_CASE_DRAM = {"det_pass": 101613056 + 22525952,
+                     "scatter": 23025408 + 1524736,
+                     "merge": (118296320 + 54569472) + (1056000 + 330240) + (109726464 + 49445888),
+                     "annihilation": 92928 + (23025408 + 1524736) + (118296320 + 54569472)
+                                     + (1056000 + 330240) + (109726464 + 49445888)}
 
 
 def _issue_peak():
@@ -230,20 +241,26 @@ def run_ours(args, rank, world):
     t_phase = {k: ph[k] / args.steps for k in ph}
     t_phase["annihilation"] = t_phase["bucket_scan"] + t_phase["scatter"] + t_phase["merge"]
     t_phase["iteration"] = t_max / args.steps
+    byt_pc = _phase_bytes(PROFILE_CASE_REC, W)
     for k in ("annihilation", "merge", "scatter", "det_pass", "iteration"):
         t_s = t_phase[k] / 1e3
         ach = byt[k] / t_s / 1e9
+        ratio = PROFILE_CASE_DRAM[k] / byt_pc[k] if k in PROFILE_CASE_DRAM else None
         roof[k] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                   "frac": round(ach / peak, 4), "traffic": None, "bytes_per_launch": int(byt[k]),
-                   "ms_per_launch": round(t_phase[k], 4), "peak_source": peak_kind}
+                   "frac": round(ach / peak, 4), "traffic": int(ratio * byt[k]) if ratio else None,
+                   "traffic_over_algorithmic": round(ratio, 3) if ratio else None,
+                   "bytes_per_launch": int(byt[k]), "ms_per_launch": round(t_phase[k], 4), "peak_source": peak_kind}
     ipeak, imhz = _issue_peak()
     att_launch = attempts / args.steps / world
     t_att = ph["attempt"] / args.steps / 1e3
     ach_i = ATTEMPT_INST_PER_ATTEMPT * att_launch / t_att / 1e9
+    spawns_launch = float(rec["nspawn"].sum()) / args.steps / world
     roof_attempt = {"bound": "alu", "achieved": round(ach_i, 1), "peak": round(ipeak, 1),
                     "unit": "G warp-instructions/s", "frac": round(ach_i / ipeak, 4),
                     "traffic": int(ATTEMPT_DRAM_BYTES_PER_ATTEMPT * att_launch),
                     "ms_per_launch": round(ph["attempt"] / args.steps, 4),
+                    "attempts_per_s": att_launch / t_att, "spawns_per_attempt": spawns_launch / att_launch,
+                    "warp_instructions_per_spawn": ATTEMPT_INST_PER_ATTEMPT * att_launch / spawns_launch,
                     "kernel": "k_attempt (spawning: Philox draw, excitation, spawn amount, bucket)",
                     "per_unit": f"{ATTEMPT_INST_PER_ATTEMPT:.1f} warp instructions per attempt (ncu)",
                     "peak_source": f"4 warp instructions/cycle/SM x {N_SM} SMs x {imhz:.0f} MHz"}
@@ -632,7 +649,8 @@ def run_profile_case(args):
     eng.synchronize()
     r = eng.estimators()
     print(json.dumps({"profile_case": True, "ndet": int(r["ndet"][-1]), "natt": int(r["natt"][-1]),
-                      "nspawn": int(r["nspawn"][-1])}))
+                      "nspawn": int(r["nspawn"][-1]), "ndet_per_iteration": [int(x) for x in r["ndet"]],
+                      "nspawn_per_iteration": [int(x) for x in r["nspawn"]]}))
     eng.close()
 
 
