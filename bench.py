@@ -313,8 +313,10 @@ def run_ours(args, rank, world):
         out["cpu_baseline"] = cpu_baseline(sysd, q, k_h, p_h)
     eng.close()
     if rank == 0 and not args.no_configs:
+        small = lambda d: batched_leg(d, replicas=256, lo=2e3, hi=2e4)   # noqa: E731
         for key, leg in (("configs", config_lines), ("learned_proposal", learned_leg),
-                         ("batched_replicas", batched_leg), ("tensor_core_gemm", tensor_core_leg)):
+                         ("batched_replicas", batched_leg), ("batched_small_replicas", small),
+                         ("tensor_core_gemm", tensor_core_leg)):
             try:
                 out[key] = leg(dev)
             except Exception as exc:   # one failing extra leg must not lose the headline line
@@ -462,9 +464,10 @@ def learned_leg(dev, iterations=4000):
     return out
 
 
-def batched_leg(dev, replicas=64, grow=300, steps=50):
+def batched_leg(dev, replicas=64, grow=300, steps=50, lo=1e4, hi=1e6):
     """Batched replicas (inputs.batched_replicas: UEG 14 electrons in 38 or 66
-    orbitals, four r_s, uneven targets 1e4-1e6) advanced by the batched graphs
+    orbitals, four r_s, uneven targets log-uniform in [lo, hi]; the default
+    line runs 64 replicas of 1e4-1e6 walkers and 256 of 2e3-2e4) advanced by the batched graphs
     (one launch per phase per key-width group, launch shape autotuned) against
     the same replicas advanced back to back on the plain path (each replica's
     own captured iteration graph on its own stream, no host synchronisation),
@@ -475,7 +478,7 @@ def batched_leg(dev, replicas=64, grow=300, steps=50):
 
     from paper_1811_11679_gb300 import hande, inputs
     stream = torch.cuda.current_stream(dev)
-    systems, qmcs = inputs.batched_replicas(replicas)
+    systems, qmcs = inputs.batched_replicas(replicas, lo=lo, hi=hi)
     b = hande.HandeBatch(systems, qmcs)
     b.iterate(grow)
     scale, tuned_ms = b.autotune(iterations=3)
@@ -512,8 +515,8 @@ def batched_leg(dev, replicas=64, grow=300, steps=50):
                                    "kernel_launches_per_step": launches},
             "speedup": (att_b / ms_b) / (att_p / ms_p),
             "workload": f"{replicas} UEG replicas: 14 electrons in 38 or 66 spatial orbitals (128- or 512-bit "
-                        "keys), r_s 0.5/1/2/5, targets log-uniform in [1e4, 1e6], initiator, real weights, "
-                        "tau=0.002"}
+                        f"keys), r_s 0.5/1/2/5, targets log-uniform in [{lo:.0e}, {hi:.0e}], initiator, real "
+                        "weights, tau=0.002"}
 
 
 def tensor_core_leg(dev, calls=20):

@@ -126,16 +126,16 @@ WORKLOADS = {
 }
 
 
-def batched_replicas(n: int = 256, seed: int = 13):
+def batched_replicas(n: int = 256, seed: int = 13, lo: float = 1e4, hi: float = 1e6):
     """(systems, qmcs) of n independent replicas: UEG 14 electrons in 38 or 66
     spatial orbitals (128- or 512-bit keys), r_s in {0.5, 1, 2, 5}, 32 seeds per
     (basis, r_s) pair for n = 256, cycled for other n; initiator real-weight
-    FCIQMC at tau = 0.002; target populations log-uniform in [1e4, 1e6] drawn
-    from numpy's Philox generator with the given seed.  Each replica starts
-    with half its target on the reference determinant, so the population
-    reaches the target within a few hundred iterations."""
+    FCIQMC at tau = 0.002; target populations log-uniform in [lo, hi] (default
+    [1e4, 1e6]) drawn from numpy's Philox generator with the given seed.  Each
+    replica starts with half its target on the reference determinant, so the
+    population reaches the target within a few hundred iterations."""
     rng = np.random.Generator(np.random.Philox(seed))
-    targets = np.exp(rng.uniform(np.log(1e4), np.log(1e6), n))
+    targets = np.exp(rng.uniform(np.log(lo), np.log(hi), n))
     systems, qmcs = [], []
     for r in range(n):
         norb = (38, 66)[r % 2]
