@@ -266,10 +266,14 @@ def run_ours(args, rank, world):
                     "peak_source": f"4 warp instructions/cycle/SM x {N_SM} SMs x {imhz:.0f} MHz"}
 
     # end to end through the C ABI with host buffers: upload, iterate, download
-    e2e_steps = min(args.steps, 3)
+    e2e_steps = min(args.steps, 10)
     nd_now = int(eng.diagnostics()["ndet"])
     bufs = eng.host_buffers(int(nd_now * 1.5) + 1024)   # page-locked, reused every step
     k_h, p_h, h_h, _ = eng.walkers(out=bufs)
+    eng.set_walkers(k_h, p_h, h_h)                       # one untimed step of the same form
+    eng.iterate(1)
+    k_h, p_h, h_h, _ = eng.walkers(out=bufs)
+    eng.estimators()
     h2d = d2h = 0
     att_e2e = 0.0
     t0 = time.perf_counter()

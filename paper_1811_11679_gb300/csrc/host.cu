@@ -517,6 +517,13 @@ void scan_natt(Engine& E, int cur) {
   CK(cudaGetLastError());
 }
 
+// the core bit of every list flag (the iteration's other bits dropped), for
+// hande_get_walkers
+__global__ void k_core_flags(const uint8_t* in, uint8_t* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] & F_CORE;
+}
+
 int64_t read_i64(Engine& E, size_t off) {
   int64_t v = 0;
   CK(cudaMemcpyAsync(&v, (char*)E.P.st + off, 8, cudaMemcpyDeviceToHost, E.stream));
@@ -1037,9 +1044,14 @@ hande_status hande_estimators(hande_ctx* ctx, hande_estimate* out, int max, int*
     int64_t avail = E.host_iter - E.fetched;
     int64_t m = std::min<int64_t>(avail, max);
     std::vector<Record> tmp((size_t)m);
-    for (int64_t i = 0; i < m; ++i) {
-      int64_t slot = (E.fetched + i) % E.P.rec_cap;
-      CK(cudaMemcpyAsync(&tmp[(size_t)i], E.P.rec + slot, sizeof(Record), cudaMemcpyDeviceToHost, E.stream));
+    if (m > 0) {   // the ring's slots from the first unread one: at most two contiguous runs
+      const int64_t first = E.fetched % E.P.rec_cap;
+      const int64_t run = std::min<int64_t>(m, E.P.rec_cap - first);
+      CK(cudaMemcpyAsync(tmp.data(), E.P.rec + first, (size_t)run * sizeof(Record), cudaMemcpyDeviceToHost,
+                         E.stream));
+      if (m > run)
+        CK(cudaMemcpyAsync(tmp.data() + run, E.P.rec, (size_t)(m - run) * sizeof(Record), cudaMemcpyDeviceToHost,
+                           E.stream));
     }
     CK(cudaStreamSynchronize(E.stream));
     for (int64_t i = 0; i < m; ++i) {
@@ -1091,10 +1103,14 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
     CK(cudaMemcpyAsync(keys, stage, (size_t)nd * W * 8, cudaMemcpyDeviceToHost, E.stream));
     CK(cudaMemcpyAsync(pops, E.P.pop[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
     if (hdiag) CK(cudaMemcpyAsync(hdiag, E.P.hdiag[cur], nd * 8, cudaMemcpyDeviceToHost, E.stream));
-    if (flags) CK(cudaMemcpyAsync(flags, E.P.flags[cur], nd, cudaMemcpyDeviceToHost, E.stream));
+    if (flags) {   // masked into the other list's flag buffer (free between iterations)
+      uint8_t* fstage = E.P.flags[cur ^ 1];
+      const int blocks = (int)std::min<int64_t>((nd + 255) / 256, 4096);
+      k_core_flags<<<blocks, 256, 0, E.stream>>>(E.P.flags[cur], fstage, nd);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(flags, fstage, nd, cudaMemcpyDeviceToHost, E.stream));
+    }
     CK(cudaStreamSynchronize(E.stream));
-    if (flags)
-      for (int64_t i = 0; i < nd; ++i) flags[i] &= F_CORE;
     return HANDE_OK;
   });
 }

@@ -337,10 +337,21 @@ class Hande:
         return e.value, k
 
     def estimators(self, max_records: int = 1 << 20) -> dict:
-        buf = (_Estimate * max_records)()
-        n = C.c_int()
-        self._check(self._lib.hande_estimators(self._h, buf, max_records, C.byref(n)), "hande_estimators")
-        arr = np.ctypeslib.as_array(buf)[: n.value]
+        """Records of the iterations since the last call (at most max_records),
+        fetched through one reused 4096-record buffer."""
+        if getattr(self, "_est_buf", None) is None:
+            self._est_buf = (_Estimate * 4096)()
+        buf, parts, left = self._est_buf, [], int(max_records)
+        while left > 0:
+            n = C.c_int()
+            want = min(left, len(buf))
+            self._check(self._lib.hande_estimators(self._h, buf, want, C.byref(n)), "hande_estimators")
+            if n.value:
+                parts.append(np.ctypeslib.as_array(buf)[: n.value].copy())
+            left -= n.value
+            if n.value < want:
+                break
+        arr = np.concatenate(parts) if parts else np.ctypeslib.as_array(buf)[:0]
         return {name: np.array(arr[name]) for name, _ in _Estimate._fields_}
 
     def host_buffers(self, capacity: int, pinned: bool = True):
