@@ -180,7 +180,15 @@ typedef struct hande_ctx hande_ctx;
 hande_status hande_init_system(const hande_system* sys, const hande_qmc* qmc, const hande_allocator* allocator,
                                void* cuda_stream, hande_ctx** out);
 
-/* Advance n >= 0 iterations (asynchronous; one CUDA-graph launch per iteration). */
+/* Advance n >= 0 iterations (asynchronous; one CUDA-graph launch per iteration).
+ * Errors of an iteration surface at the next synchronising call.  Annihilation
+ * buckets are sized from the previous iteration's spawn and new-key counts; a
+ * bucket that still receives more spawns than one warp takes is split into at
+ * most 256 key sub-ranges of about a quarter tile each (splitters sampled from
+ * its spawns), so one list entry whose spawns in a single iteration exceed
+ * about 256 x tile_capacity / 4 mostly distinct new keys (16 384 at the 512-bit
+ * default tile, 32 768 otherwise) can end the run with HANDE_ERR_CAPACITY
+ * (annihilation tile); start such runs from a smaller init_pop. */
 hande_status hande_iterate(hande_ctx* ctx, int n);
 
 /* Number of phases reported by hande_iterate_timed, in order: determinant pass
@@ -218,7 +226,9 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
  * from this list; an active deterministic space is kept (its matrix is not
  * rebuilt) and must lie in the new list (else HANDE_ERR_INVALID and the space
  * is off; hande_set_state installs a different one).  The iteration counter is
- * kept.  Synchronises. */
+ * kept.  The next iteration sizes its annihilation buckets as if every one of
+ * the list's attempts (sum of ceil |N_i|) spawned a new determinant.
+ * Synchronises. */
 hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
                                int64_t n);
 

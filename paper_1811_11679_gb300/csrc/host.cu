@@ -524,6 +524,31 @@ __global__ void k_core_flags(const uint8_t* in, uint8_t* out, int64_t n) {
     out[i] = in[i] & F_CORE;
 }
 
+// Bucket-sizing statistics for the first iteration on a list set from the
+// host: both "previous iteration" counts (spawns, distinct new keys) become the
+// list's attempt bound, sum of ceil(|N_i|) walkers, so the buckets are sized
+// as if every attempt spawned onto a new determinant.
+__global__ void k_attempt_bound(const int64_t* pop, int64_t n, DevState* st) {
+  __shared__ unsigned long long part[32];
+  unsigned long long s = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = pop[i];
+    const uint64_t m = (uint64_t)(p < 0 ? -p : p);
+    s += (m + 0xffffffffull) >> 32;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0ull;
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0 && s) {
+      atomicAdd((unsigned long long*)&st->nspawn_prev, s);
+      atomicAdd((unsigned long long*)&st->nuniq_prev, s);
+    }
+  }
+}
+
 int64_t read_i64(Engine& E, size_t off) {
   int64_t v = 0;
   CK(cudaMemcpyAsync(&v, (char*)E.P.st + off, 8, cudaMemcpyDeviceToHost, E.stream));
@@ -1141,6 +1166,10 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     E.ops.keys_to_soa(E, stage, E.P.key[cur], n, E.P.cap, E.stream);
     CK(cudaMemcpyAsync(E.P.pop[cur], pops, n * 8, cudaMemcpyHostToDevice, E.stream));
     CK(cudaMemsetAsync(E.P.flags[cur], 0, n, E.stream));
+    CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nspawn_prev), 0, 8, E.stream));
+    CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nuniq_prev), 0, 8, E.stream));
+    k_attempt_bound<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, E.stream>>>(E.P.pop[cur], n, E.P.st);
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync((char*)E.P.st + offsetof(DevState, ndet) + 8 * cur, &n, 8, cudaMemcpyHostToDevice, E.stream));
     if (hdiag) CK(cudaMemcpyAsync(E.P.hdiag[cur], hdiag, n * 8, cudaMemcpyHostToDevice, E.stream));
     else E.ops.hdiag(E, cur, n, E.stream);
