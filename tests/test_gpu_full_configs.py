@@ -148,3 +148,36 @@ def test_all_256_batched_replicas_sampled_against_the_oracle():
         _same_records(b.replicas[r], cs[r])
     assert all(v.iterations == 4 for v in b.replicas)
     b.close()
+
+
+def test_benchmark_state_two_iterations_against_the_oracle():
+    """The headline workload as the bench times it (28-orbital molecule, 1e7
+    target walkers, deterministic space of 1e4 chosen at iteration 2000, the
+    bench's capacities and launch configuration): grown on the GPU to iteration
+    2060, its list and run state handed to the oracle (all host cores), then two
+    more iterations on both sides compared element by element."""
+    import os
+    sysd, q = inputs.workload("molecule28", target_population=1e7, semi_stoch_size=10000, semi_stoch_start=2000,
+                              state_capacity=16_000_000, spawn_capacity=32_000_000)
+    g = hande.Hande(sysd, q)
+    while g.iterations < 2060:
+        g.iterate(min(250, 2060 - g.iterations))
+    keys, pops, _, _ = g.walkers()
+    state, core = g.state()
+    assert len(pops) > 2_000_000 and state["core_active"] == 1 and len(core) == 10000
+    assert g.diagnostics()["nbuckets"] > 4096
+    g.estimators()
+    c = oracle.Oracle(sysd, q, threads=os.cpu_count())
+    c.set_walkers(keys, pops)
+    c.set_state(state, core)
+    for it in range(2):
+        g.iterate(1)
+        c.iterate(1)
+        _same_lists(g, c, 2061 + it)
+    rg, rc = g.estimators(), c.records()
+    n = len(rc["iter"])
+    assert n == 2 and len(rg["iter"]) == 2
+    for k in ("iter", "nw_pre", "n0", "num_hi", "num_lo", "nw_post", "ndet", "natt", "nspawn"):
+        assert np.array_equal(rg[k], rc[k][-n:]), k
+    assert np.array_equal(rg["shift"].view(np.int64), rc["shift"][-n:].view(np.int64))
+    g.close()
