@@ -319,6 +319,7 @@ def run_ours(args, rank, world):
     if rank == 0 and not args.no_configs:
         small = lambda d: batched_leg(d, replicas=256, lo=2e3, hi=2e4)   # noqa: E731
         for key, leg in (("configs", config_lines), ("learned_proposal", learned_leg),
+                         ("learned_proposal_full_basis", learned_full_basis_leg),
                          ("batched_replicas", batched_leg), ("batched_small_replicas", small),
                          ("tensor_core_gemm", tensor_core_leg)):
             try:
@@ -418,7 +419,7 @@ def config_lines(dev):
     return out
 
 
-def learned_leg(dev, iterations=4000):
+def learned_leg(dev, iterations=4000, nel=14, norb=38, tau=0.002, target=2e5, equil=500, grow_blocks=80):
     """The learned excitation proposal against the uniform generator on the
     same UEG run (14 electrons in 38 plane waves, r_s=1, initiator, real
     weights, tau=0.002, target 2e5 walkers): each grown until the shift varies,
@@ -431,16 +432,20 @@ def learned_leg(dev, iterations=4000):
     stream = torch.cuda.current_stream(dev)
     out = {}
     for name in ("uniform", "learned"):
-        sysd, q = inputs.workload("ueg14", target_population=2e5, init_pop=2e4, state_capacity=1_500_000,
-                                  spawn_capacity=3_000_000, excit_gen=1 if name == "learned" else 0)
+        sysd = inputs.ueg_system(nel, norb, 1.0)
+        q = inputs.qmc_params(tau=tau, target_population=target, init_pop=target / 10, initiator=1,
+                              real_amplitudes=1, spawn_cutoff=0.1, seed=7,
+                              state_capacity=int(12 * target) + (1 << 16),
+                              spawn_capacity=int(24 * target) + (1 << 17),
+                              excit_gen=1 if name == "learned" else 0)
         eng = hande.Hande(sysd, q)
         if name == "learned":
             eng.learn_proposal(width=256, batch=4096, period=10, learning_rate=2e-3, seed=1)
-        for _ in range(80):
+        for _ in range(grow_blocks):
             eng.iterate(250)
             if eng.estimators()["shift"][-1] != 0.0:
                 break
-        eng.iterate(500)
+        eng.iterate(equil)
         eng.synchronize()
         eng.estimators()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -462,9 +467,77 @@ def learned_leg(dev, iterations=4000):
     u, l = out["uniform"], out["learned"]
     out["efficiency_gain"] = u["cost_error2_x_seconds"] / l["cost_error2_x_seconds"]
     out["agreement_sigma"] = abs(u["E_proj"] - l["E_proj"]) / float(np.hypot(u["error"], l["error"]))
-    out["workload"] = ("UEG 14e in 38 plane waves, r_s=1, initiator n_a=3, real weights, tau=0.002, target 2e5; "
-                       f"{iterations} timed iterations each; learned = MLP 3 layers width 256 (BF16 tensor cores), "
-                       "Adam every 10 iterations on 4096 recorded attempts")
+    out["workload"] = (f"UEG {nel}e in {norb} plane waves, r_s=1, initiator n_a=3, real weights, tau={tau}, "
+                       f"target {target:.0e}; {iterations} timed iterations each; learned = MLP 3 layers width 256 "
+                       "(BF16 tensor cores), Adam every 10 iterations on 4096 recorded attempts")
+    return out
+
+
+def learned_full_basis_leg(dev, target=1e5, pretrain=2000, taus=(5e-5, 1e-3), iterations=(40000, 8000)):
+    """The learned proposal at the full basis of its configuration (UEG 54
+    electrons in 246 plane waves, 512-bit keys, r_s = 1, initiator, real
+    weights; 1e5 target walkers instead of 1e8) against the uniform generator,
+    each at its own stable time step: the uniform generator at the time-step
+    search's value for it (5e-5; at 1e-3 its spawns of up to ~18 walkers per
+    attempt make the population explode), the learned one at 1e-3.  The network
+    is warm-started from a 2000-iteration run at tau = 2e-4 and keeps training
+    every 10 iterations.  Each arm: grown from a tenth of the target until the
+    shift varies, 3000 iterations of equilibration, then the timed iterations
+    (CUDA events).  Cost = (reblocked error of E_proj)^2 x time."""
+    import torch
+
+    from paper_1811_11679_gb300 import analysis, hande, inputs
+    stream = torch.cuda.current_stream(dev)
+    sysd = inputs.ueg_system(54, 246, 1.0)
+
+    def qmc(gen, tau):
+        return inputs.qmc_params(tau=tau, target_population=target, init_pop=target / 10, initiator=1,
+                                 real_amplitudes=1, spawn_cutoff=0.1, seed=7,
+                                 state_capacity=int(20 * target) + (1 << 20),
+                                 spawn_capacity=int(40 * target) + (1 << 21), excit_gen=gen)
+
+    pre = hande.Hande(sysd, qmc(1, 2e-4))
+    pre.learn_proposal(width=256, batch=4096, period=10, learning_rate=2e-3, seed=1)
+    pre.iterate(pretrain)
+    params = pre.learn_params()
+    pre.close()
+    out = {}
+    for name, tau, iters in (("uniform", taus[0], iterations[0]), ("learned", taus[1], iterations[1])):
+        eng = hande.Hande(sysd, qmc(1 if name == "learned" else 0, tau))
+        if name == "learned":
+            eng.learn_proposal(width=256, batch=4096, period=10, learning_rate=2e-3, seed=1)
+            eng.learn_params(params)
+            eng.learn_refresh()
+        for _ in range(200):
+            eng.iterate(100)
+            if eng.estimators()["shift"][-1] != 0.0:
+                break
+        eng.iterate(3000)
+        eng.synchronize()
+        eng.estimators()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        eng.iterate(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        r = eng.estimators()
+        e_ref, _ = eng.reference()
+        E, err = analysis.projected_energy(r, e_ref)
+        eng.close()
+        out[name] = {"tau": tau, "iterations": iters, "E_proj": E, "error": err, "ms_per_iteration": ms / iters,
+                     "attempts_per_s": float(r["natt"].sum()) / (ms / 1e3),
+                     "spawns_per_attempt": float(r["nspawn"].sum()) / max(float(r["natt"].sum()), 1.0),
+                     "mean_walkers": float(r["nw_post"].mean()) / 2 ** 32,
+                     "cost_error2_x_seconds": err * err * ms / 1e3}
+    u, l = out["uniform"], out["learned"]
+    out["efficiency_gain"] = u["cost_error2_x_seconds"] / l["cost_error2_x_seconds"]
+    out["agreement_sigma"] = abs(u["E_proj"] - l["E_proj"]) / float(np.hypot(u["error"], l["error"]))
+    out["workload"] = (f"UEG 54e in 246 plane waves (512-bit keys), r_s=1, initiator n_a=3, real weights, target "
+                       f"{target:.0e}; uniform at tau={taus[0]} ({iterations[0]} timed iterations), learned at "
+                       f"tau={taus[1]} ({iterations[1]}), network warm-started from {pretrain} iterations at "
+                       "tau=2e-4, Adam every 10 iterations on 4096 recorded attempts")
     return out
 
 
