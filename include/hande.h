@@ -226,9 +226,10 @@ hande_status hande_get_walkers(hande_ctx* ctx, uint64_t* keys, int64_t* pops, do
  * from this list; an active deterministic space is kept (its matrix is not
  * rebuilt) and must lie in the new list (else HANDE_ERR_INVALID and the space
  * is off; hande_set_state installs a different one).  The iteration counter is
- * kept.  The next iteration sizes its annihilation buckets as if every one of
- * the list's attempts (sum of ceil |N_i|) spawned a new determinant.
- * Synchronises. */
+ * kept.  In a context that has not iterated yet, the first iteration sizes
+ * its annihilation buckets as if every one of the list's attempts (sum of
+ * ceil |N_i|) spawned a new determinant; later lists keep the sizing from the
+ * previous iteration's counts.  Synchronises. */
 hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64_t* pops, const double* hdiag,
                                int64_t n);
 

@@ -1166,10 +1166,12 @@ hande_status hande_set_walkers(hande_ctx* ctx, const uint64_t* keys, const int64
     E.ops.keys_to_soa(E, stage, E.P.key[cur], n, E.P.cap, E.stream);
     CK(cudaMemcpyAsync(E.P.pop[cur], pops, n * 8, cudaMemcpyHostToDevice, E.stream));
     CK(cudaMemsetAsync(E.P.flags[cur], 0, n, E.stream));
-    CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nspawn_prev), 0, 8, E.stream));
-    CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nuniq_prev), 0, 8, E.stream));
-    k_attempt_bound<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, E.stream>>>(E.P.pop[cur], n, E.P.st);
-    CK(cudaGetLastError());
+    if (E.host_iter == 0) {   // no previous iteration's counts to size the buckets with
+      CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nspawn_prev), 0, 8, E.stream));
+      CK(cudaMemsetAsync((char*)E.P.st + offsetof(DevState, nuniq_prev), 0, 8, E.stream));
+      k_attempt_bound<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, E.stream>>>(E.P.pop[cur], n, E.P.st);
+      CK(cudaGetLastError());
+    }
     CK(cudaMemcpyAsync((char*)E.P.st + offsetof(DevState, ndet) + 8 * cur, &n, 8, cudaMemcpyHostToDevice, E.stream));
     if (hdiag) CK(cudaMemcpyAsync(E.P.hdiag[cur], hdiag, n * 8, cudaMemcpyHostToDevice, E.stream));
     else E.ops.hdiag(E, cur, n, E.stream);
