@@ -637,7 +637,7 @@ def tensor_core_leg(dev, calls=20):
     assert int(status.item()) == 0, "tensor-core GEMM wait timed out"
     best = max(rows, key=lambda x: x["tflops"])
     return {"bound": "tensor", "achieved": round(best["tflops"], 1), "peak": peak[0], "unit": "TFLOP/s",
-            "frac": round(best["frac"], 4), "traffic": None, "peak_source": peak[1], "kernel": "k_gemm_bf16_tn",
+            "frac": round(best["frac"], 4), "traffic": None, "peak_source": peak[1], "kernel": "k_gemm_bf16_tn_p (persistent, two TMEM accumulators)",
             "hbm": {"achieved": round(best["hbm_gbs"], 1), "peak": hbm[0], "unit": "GB/s",
                     "frac": round(best["hbm_frac"], 4), "peak_source": hbm[1]},
             "shapes": rows}

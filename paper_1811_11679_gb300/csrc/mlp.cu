@@ -52,15 +52,18 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// persistent launch: one CTA per SM (at most one per output tile)
 template <int BN, int EPI>
 bool launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& ep, int M, int N, int K,
                   unsigned* err, cudaStream_t s, int dev, const char** why) {
   static bool attr_set[256] = {};
+  static int nsm[256] = {};
   {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!attr_set[dev]) {
-      if (cudaFuncSetAttribute(k_gemm_bf16_tn<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)Tile<BN>::kSmemBytes) != cudaSuccess) {
+      if (cudaFuncSetAttribute(k_gemm_bf16_tn_p<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)PTile<BN>::kSmemBytes) != cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         *why = "cannot reserve the GEMM's shared memory";
         return false;
@@ -68,8 +71,9 @@ bool launch_shape(const CUtensorMap& ma, const CUtensorMap& mb, const Epilogue& 
       attr_set[dev] = true;
     }
   }
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + kBM - 1) / kBM));
-  k_gemm_bf16_tn<BN, EPI><<<grid, kThreads, Tile<BN>::kSmemBytes, s>>>(ma, mb, ep, M, N, K, err);
+  const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + kBM - 1) / kBM);
+  const unsigned grid = (unsigned)(tiles < nsm[dev] ? tiles : nsm[dev]);
+  k_gemm_bf16_tn_p<BN, EPI><<<grid, kPThreads, PTile<BN>::kSmemBytes, s>>>(ma, mb, ep, M, N, K, err);
   if (cudaGetLastError() != cudaSuccess) {
     *why = "GEMM launch failed";
     return false;

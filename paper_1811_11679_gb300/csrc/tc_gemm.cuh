@@ -3,23 +3,24 @@
 //   D[m][n] = sum_k A[m][k] B[n][k]        (A: M x K, B: N x K, both K-major
 //                                           BF16 row-major; D: FP32)
 //
-// One CTA computes one 128 x BN tile of D (BN = 128, or 256 when N > 128, so
-// that A is read once for N <= 256).  The K dimension is taken in
-// chunks of 64 elements (128 bytes): a TMA tile load brings the A and B chunk
-// of a stage into shared memory in the 128-byte-swizzled K-major layout the
-// tensor core reads, four stages deep; one thread issues the MMAs (four
-// 128 x BN x 16 tcgen05.mma per chunk, FP32 accumulators in tensor memory) and
-// commits each stage to an mbarrier that frees it for the next TMA load.  When
-// the last MMA has completed, the four warps read the accumulator rows they own
-// (tcgen05.ld, 32 lanes x 32 columns at a time) and store them as FP32, or as
-// BF16 after adding a bias and a ReLU (with a transposed copy if asked: the
-// learned proposal's hidden layers and their backward operands).  Rows, columns
-// and K beyond the matrix are zero-filled by the TMA and masked in the store,
-// so any M, N, K >= 1 work (leading dimensions: multiples of 8 elements).
+// Output tiles of 128 x BN (BN = 128, or 256 when N > 128, so that A is read
+// once for N <= 256), walked by one persistent CTA per SM (see
+// k_gemm_bf16_tn_p below).  The K dimension is taken in chunks of 64 elements
+// (128 bytes): a TMA tile load brings the A and B chunk of a stage into shared
+// memory in the 128-byte-swizzled K-major layout the tensor core reads, four
+// stages deep; one thread issues the MMAs (four 128 x BN x 16 tcgen05.mma per
+// chunk, FP32 accumulators in tensor memory) and commits each stage to an
+// mbarrier that frees it for the next TMA load.  Four warps read the
+// accumulator rows they own (tcgen05.ld, 32 lanes x 32 columns at a time) and
+// store them as FP32, or as BF16 after adding a bias and a ReLU (with a
+// transposed copy if asked: the learned proposal's hidden layers and their
+// backward operands).  Rows, columns and K beyond the matrix are zero-filled by
+// the TMA and masked in the store, so any M, N, K >= 1 work (leading
+// dimensions: multiples of 8 elements).
 //
 // Every wait is bounded: a wait that gives up sets bit ERR_MMA_TIMEOUT of *err,
-// the kernel skips its remaining work, waits (bounded) for its own MMAs and
-// frees its tensor memory.
+// the kernel skips its remaining work, waits (bounded) for its own loads and
+// MMAs and frees its tensor memory.
 #pragma once
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -34,17 +35,12 @@ constexpr int kBM = 128;        // tile rows (MMA M)
 constexpr int kBK = 64;         // K per stage: 64 BF16 = 128 bytes = one swizzle row
 constexpr int kMmaK = 16;       // K of one tcgen05.mma kind::f16
 constexpr int kStages = 4;
-constexpr int kThreads = 128;   // four warps: the 128 TMEM lanes
 constexpr uint32_t kTileABytes = kBM * kBK * 2;
 constexpr unsigned ERR_MMA_TIMEOUT = 1u;
-// tile columns BN (MMA N, 128 or 256) and what BN needs: B tile bytes, tensor
-// memory columns (one FP32 accumulator column per output column), and the
-// dynamic shared memory (1024-byte aligned stages + barriers)
+// tile columns BN (MMA N, 128 or 256): the bytes of a B chunk
 template <int BN>
 struct Tile {
   static constexpr uint32_t kTileBBytes = BN * kBK * 2;
-  static constexpr uint32_t kTmemCols = BN;
-  static constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kTileABytes + kTileBBytes) + 256;
 };
 // epilogues: FP32 D, or BF16 act(D + bias) (ReLU or none) with an optional
 // transposed BF16 copy
@@ -171,162 +167,217 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// ------------------------------------------------------------------ the GEMM
-// grid (ceil(N / BN), ceil(M / 128)), kThreads threads, Tile<BN>::kSmemBytes
-// dynamic shared memory.  tmA: A as a 2D tensor {K, M} (row stride lda * 2
-// bytes), box {64, 128}; tmB likewise for B {K, N}, box {64, BN}.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Epilogue of 32 accumulator columns c0 .. c0 + 31 of tile column n0 for the
+// calling lane's row (r: the lane's 32 FP32 values from tcgen05.ld): FP32
+// store, or BF16 act(D + bias) with the optional transposed copy.
+template <int EPI>
+__device__ __forceinline__ void epi_store(const Epilogue& ep, const uint32_t (&r)[32], int row, int n0, int c0,
+                                          int M, int N) {
+  const int nc = N - (n0 + c0) < 32 ? N - (n0 + c0) : 32;
+  if (EPI == EPI_F32) {
+    if (row < M) {
+      float* out = ep.D + (int64_t)row * ep.ldd + n0 + c0;
+      if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
+#pragma unroll
+        for (int i = 0; i < 32; i += 4)
+          *reinterpret_cast<float4*>(out + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
+                                                            __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < nc) out[i] = __uint_as_float(r[i]);
+      }
+    }
+  } else {
+    uint32_t h[16];
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) {
+      float v0 = __uint_as_float(r[i]) + (i < nc ? __ldg(&ep.bias[n0 + c0 + i]) : 0.0f);
+      float v1 = __uint_as_float(r[i + 1]) + (i + 1 < nc ? __ldg(&ep.bias[n0 + c0 + i + 1]) : 0.0f);
+      if (ep.relu) {
+        v0 = v0 > 0.0f ? v0 : 0.0f;
+        v1 = v1 > 0.0f ? v1 : 0.0f;
+      }
+      h[i / 2] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v0)) |
+                 ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v1)) << 16);
+    }
+    if (row < M) {
+      uint16_t* out = ep.H + (int64_t)row * ep.ldh + n0 + c0;
+      if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+          *reinterpret_cast<uint4*>(out + 2 * i) = make_uint4(h[i], h[i + 1], h[i + 2], h[i + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < nc) out[i] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
+      }
+      if (ep.HT) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (i < nc) ep.HT[(int64_t)(n0 + c0 + i) * ep.ldt + row] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ persistent form
+// One CTA per SM walks the output tiles t = blockIdx.x, + gridDim.x, ... with
+// six warps: warp 4 (one thread) issues the TMA loads of every tile's K chunks
+// into the stage ring, warp 5 (one thread) issues the MMAs into one of two
+// tensor-memory accumulators (2 x BN columns) and owns the tensor memory, and
+// warps 0-3 (accumulator lanes 32w .. 32w + 31) run the epilogue of the other
+// accumulator, so one tile's stores overlap the next tile's loads and MMAs.
+// Barriers: full/empty per stage (TMA bytes / MMA commit), acc_full per
+// accumulator (MMA commit) and acc_empty (one arrival per epilogue warp).
+// Every wait is bounded; a wait that gives up sets ERR_MMA_TIMEOUT and a
+// shared flag that stops all roles, which then drain their own loads and MMAs
+// (bounded) before the tensor memory is freed.
+constexpr int kPThreads = 192;
+// tensor-memory columns (two FP32 accumulators of BN columns: 512 at BN = 256)
+// and dynamic shared memory (1024-byte aligned stages + barriers)
+template <int BN>
+struct PTile {
+  static constexpr uint32_t kTmemCols = 2 * BN;
+  static constexpr size_t kSmemBytes = 1024 + (size_t)kStages * (kTileABytes + Tile<BN>::kTileBBytes) + 256;
+};
+
 template <int BN, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_bf16_tn(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const Epilogue ep, int M, int N, int K, unsigned* err) {
+__global__ void __launch_bounds__(kPThreads, 1)
+    k_gemm_bf16_tn_p(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const Epilogue ep, int M, int N, int K, unsigned* err) {
   constexpr uint32_t kTileBBytes = Tile<BN>::kTileBBytes;
-  constexpr uint32_t kTmemCols = Tile<BN>::kTmemCols;
-  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  constexpr uint32_t kTmemCols = PTile<BN>::kTmemCols;
+  extern __shared__ __align__(16) unsigned char tcp_smem_raw[];
   unsigned char* base =
-      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tcp_smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;
   unsigned char* sB = base + (size_t)kStages * kTileABytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + (size_t)kStages * kTileBBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* done = empty + kStages;
+  uint64_t* acc_full = empty + kStages;      // [2]
+  uint64_t* acc_empty = acc_full + 2;        // [2]
+  uint64_t* done = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
 
   const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-  const int m0 = (int)blockIdx.y * kBM, n0 = (int)blockIdx.x * BN;
   const int nk = (K + kBK - 1) / kBK;
+  const int tn_count = (N + BN - 1) / BN, tm_count = (M + kBM - 1) / kBM;
+  const int ntiles = tn_count * tm_count;
 
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 5) tmem_alloc(tmem_slot, kTmemCols);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  auto fail = [&]() {
+    s_fail = 1;
+    atomicOr(err, ERR_MMA_TIMEOUT);
+  };
 
-  if (threadIdx.x == 0) {
-    const uint32_t idesc = idesc_bf16_f32(kBM, BN);
-    auto load = [&](int kc, int s) {
-      mbar_expect_tx(&full[s], kTileABytes + kTileBBytes);
-      tma_load_2d(sA + (size_t)s * kTileABytes, &tmA, &full[s], kc * kBK, m0);
-      tma_load_2d(sB + (size_t)s * kTileBBytes, &tmB, &full[s], kc * kBK, n0);
-    };
-    const int pre = nk < kStages ? nk : kStages;
-    for (int kc = 0; kc < pre; ++kc) load(kc, kc);
-    int issued = pre, consumed = 0;
-    bool ok = true;
-    for (int kc = 0; kc < nk && ok; ++kc) {
-      const int s = kc % kStages;
-      if (!mbar_wait(&full[s], (uint32_t)((kc / kStages) & 1))) {
-        ok = false;
-        break;
+  if (warp == 4) {
+    if (lane == 0) {   // producer
+      int64_t fill = 0;   // chunk loads issued over all tiles
+      int64_t landed = 0;
+      for (int t = (int)blockIdx.x; t < ntiles && !s_fail; t += (int)gridDim.x) {
+        const int m0 = (t / tn_count) * kBM, n0 = (t % tn_count) * BN;
+        for (int kc = 0; kc < nk && !s_fail; ++kc, ++fill) {
+          const int st = (int)(fill % kStages);
+          const uint32_t ph = (uint32_t)((fill / kStages) & 1);
+          if (!mbar_wait(&empty[st], ph ^ 1u)) {
+            fail();
+            break;
+          }
+          mbar_expect_tx(&full[st], kTileABytes + kTileBBytes);
+          tma_load_2d(sA + (size_t)st * kTileABytes, &tmA, &full[st], kc * kBK, m0);
+          tma_load_2d(sB + (size_t)st * kTileBBytes, &tmB, &full[st], kc * kBK, n0);
+        }
       }
-      consumed = kc + 1;
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + (size_t)s * kTileABytes);
-      const uint32_t b0 = smem_u32(sB + (size_t)s * kTileBBytes);
-#pragma unroll
-      for (int j = 0; j < kBK / kMmaK; ++j) {
-        // K step j: 16 BF16 = 32 bytes further along each 128-byte row
-        tc_mma(tmem, sw128_kmajor_desc(a0 + 32u * j), sw128_kmajor_desc(b0 + 32u * j), idesc,
-               (kc > 0 || j > 0) ? 1u : 0u);
+      if (s_fail) {   // let this thread's loads in flight land before the CTA exits (bounded)
+        for (landed = fill - kStages > 0 ? fill - kStages : 0; landed < fill; ++landed)
+          mbar_wait(&full[landed % kStages], (uint32_t)((landed / kStages) & 1));
       }
-      tc_commit(&empty[s]);
-      // refill the stage the previous chunk used once its MMAs have read it
-      const int kp = kc - 1;
-      if (kp >= 0 && kp + kStages < nk) {
-        const int sp = kp % kStages;
-        if (!mbar_wait(&empty[sp], (uint32_t)((kp / kStages) & 1))) {
-          ok = false;
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {   // MMA issuer
+      const uint32_t idesc = idesc_bf16_f32(kBM, BN);
+      int64_t use = 0;   // chunk consumptions over all tiles
+      int i = 0;         // tiles of this CTA
+      for (int t = (int)blockIdx.x; t < ntiles && !s_fail; t += (int)gridDim.x, ++i) {
+        const int a = i & 1;
+        if (!mbar_wait(&acc_empty[a], (uint32_t)(((i >> 1) & 1) ^ 1))) {
+          fail();
           break;
         }
-        load(kp + kStages, sp);
-        issued = kp + kStages + 1;
+        tc_fence_after();
+        const uint32_t dcol = tmem + (uint32_t)(a * BN);
+        for (int kc = 0; kc < nk; ++kc, ++use) {
+          const int st = (int)(use % kStages);
+          if (!mbar_wait(&full[st], (uint32_t)((use / kStages) & 1))) {
+            fail();
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + (size_t)st * kTileABytes);
+          const uint32_t b0 = smem_u32(sB + (size_t)st * kTileBBytes);
+#pragma unroll
+          for (int j = 0; j < kBK / kMmaK; ++j)
+            tc_mma(dcol, sw128_kmajor_desc(a0 + 32u * j), sw128_kmajor_desc(b0 + 32u * j), idesc,
+                   (kc > 0 || j > 0) ? 1u : 0u);
+          tc_commit(&empty[st]);
+        }
+        if (s_fail) break;
+        tc_commit(&acc_full[a]);
       }
+      tc_commit(done);   // completes once every MMA issued above has completed
+      if (!mbar_wait(done, 0)) fail();
     }
-    if (!ok) {
-      s_fail = 1;
-      atomicOr(err, ERR_MMA_TIMEOUT);
-      // let the tile loads still in flight land before the CTA exits (bounded)
-      for (int kc = consumed; kc < issued; ++kc) mbar_wait(&full[kc % kStages], (uint32_t)((kc / kStages) & 1));
-    }
-    tc_commit(done);   // completes when every MMA issued above has completed
-  }
-  __syncwarp();
-  // uniform over the CTA (the accumulator reads below are warp-collective)
-  const bool finished = __syncthreads_and(mbar_wait(done, 0) ? 1 : 0) != 0;
-  tc_fence_after();
-  if (!finished) {
-    if (threadIdx.x == 0) atomicOr(err, ERR_MMA_TIMEOUT);
-  } else if (!s_fail) {
-    // epilogue: warp w owns accumulator lanes (rows) 32w .. 32w + 31
-    const int row = m0 + warp * 32 + lane;
+  } else {   // epilogue warps 0-3
+    const int lrow = warp * 32 + lane;
+    int i = 0;
+    for (int t = (int)blockIdx.x; t < ntiles && !s_fail; t += (int)gridDim.x, ++i) {
+      const int m0 = (t / tn_count) * kBM, n0 = (t % tn_count) * BN;
+      const int a = i & 1;
+      const bool ok = mbar_wait(&acc_full[a], (uint32_t)((i >> 1) & 1));
+      if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform (the accumulator reads are warp-collective)
+        if (lane == 0) fail();
+        break;
+      }
+      tc_fence_after();
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      if (n0 + c0 >= N) break;
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      const int nc = N - (n0 + c0) < 32 ? N - (n0 + c0) : 32;
-      if (EPI == EPI_F32) {
-        if (row < M) {
-          float* out = ep.D + (int64_t)row * ep.ldd + n0 + c0;
-          if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-              *reinterpret_cast<float4*>(out + i) = make_float4(__uint_as_float(r[i]), __uint_as_float(r[i + 1]),
-                                                                __uint_as_float(r[i + 2]), __uint_as_float(r[i + 3]));
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < nc) out[i] = __uint_as_float(r[i]);
-          }
-        }
-      } else {
-        // bias, activation and BF16 rounding; the row-major copy as packed
-        // pairs, the transposed copy with consecutive lanes on consecutive rows
-        uint32_t h[16];
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-          float v0 = __uint_as_float(r[i]) + (i < nc ? __ldg(&ep.bias[n0 + c0 + i]) : 0.0f);
-          float v1 = __uint_as_float(r[i + 1]) + (i + 1 < nc ? __ldg(&ep.bias[n0 + c0 + i + 1]) : 0.0f);
-          if (ep.relu) {
-            v0 = v0 > 0.0f ? v0 : 0.0f;
-            v1 = v1 > 0.0f ? v1 : 0.0f;
-          }
-          h[i / 2] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v0)) |
-                     ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v1)) << 16);
-        }
-        if (row < M) {
-          uint16_t* out = ep.H + (int64_t)row * ep.ldh + n0 + c0;
-          if (nc == 32 && (((uintptr_t)out & 15) == 0)) {
-#pragma unroll
-            for (int i = 0; i < 16; i += 4)
-              *reinterpret_cast<uint4*>(out + 2 * i) = make_uint4(h[i], h[i + 1], h[i + 2], h[i + 3]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < nc) out[i] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
-          }
-          if (ep.HT) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < nc) ep.HT[(int64_t)(n0 + c0 + i) * ep.ldt + row] = (uint16_t)(h[i / 2] >> (16 * (i & 1)));
-          }
-        }
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= N) break;
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * BN + c0), r);
+        epi_store<EPI>(ep, r, m0 + lrow, n0, c0, M, N);
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[a]);
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_free(tmem, kTmemCols);
+  if (warp == 5) tmem_free(tmem, kTmemCols);
 }
 
 }  // namespace tc
